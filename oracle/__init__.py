@@ -1,0 +1,215 @@
+"""Oracle for the RaFI work-forwarding hot path (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never does: it shares no code with the oracle.
+
+The arithmetic lives in ``oracle.c`` (plain single-threaded C, built without
+FMA contraction); this module only builds it and marshals numpy arrays.
+Every function cites the passage of the paper it restates.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+UNIFORM, ZIPF, NBR6 = 0, 1, 2
+RETIRE_THRESHOLD = 429496730  # ceil(0.1 * 2**32)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, no FMA contraction)."""
+    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            u32, i32, u64, f64 = ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+            lib.or_philox_batch.argtypes = [u64, P, P, P]
+            lib.or_philox_batch.restype = None
+            lib.or_partition.argtypes = [P, P, u64, u32, i32, P, P, P, P]
+            lib.or_partition.restype = u64
+            lib.or_zipf_thresholds.argtypes = [i32, f64, P]
+            lib.or_zipf_thresholds.restype = None
+            lib.or_c1_choose_dest.argtypes = [i32, i32, u32, i32, P, P]
+            lib.or_c1_choose_dest.restype = i32
+            lib.or_c1_walk.argtypes = [P, u64, i32, u32, i32, P, P, u32, P, P, P]
+            lib.or_c1_walk.restype = u64
+            lib.or_c1_rounds.argtypes = [P, u64, i32, u32, i32, P, P, u32, P, P, P, i32, P, P]
+            lib.or_c1_rounds.restype = i32
+            lib.or_c0_primary.argtypes = [P, i32, i32, i32, P, P, P]
+            lib.or_c0_primary.restype = i32
+            lib.or_c0_render.argtypes = [P, i32, i32, P, i32, i32, P, P, P, P, i32, P]
+            lib.or_c0_render.restype = None
+            lib.or_c0_sigma.argtypes = [P, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+            lib.or_c0_sigma.restype = ctypes.c_float
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11)
+# --------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of counters ``ctr`` (n x 4 uint32) under keys ``key`` (n x 2)."""
+    ctr = _c(np.atleast_2d(ctr), np.uint32)
+    key = _c(np.broadcast_to(np.atleast_2d(key), (ctr.shape[0], 2)), np.uint32)
+    out = np.empty_like(ctr)
+    _load().or_philox_batch(ctr.shape[0], _p(ctr), _p(key), _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Exchange: stable partition by destination (Sec. 4.2.1-4.2.3)
+# --------------------------------------------------------------------------
+def partition(items: np.ndarray, dest: np.ndarray, num_ranks: int):
+    """Stable partition of ``items`` (n x itemBytes uint8) by ``dest``.
+
+    Returns (out, offset[R+1], bad, holes): ``out[offset[r]:offset[r+1]]`` is
+    rank r's next incoming queue, in emission order (Sec. 4.2.1's radix sort
+    on (dest << 32 | i) followed by the gather).
+    """
+    items = _c(items, np.uint8)
+    dest = _c(dest, np.int32)
+    n = dest.shape[0]
+    item_bytes = items.shape[1] if n else (items.shape[1] if items.ndim == 2 else 0)
+    out = np.zeros((n, item_bytes), np.uint8)
+    off = np.zeros(num_ranks + 1, np.uint64)
+    bad = np.zeros(1, np.uint64)
+    holes = np.zeros(1, np.uint64)
+    total = _load().or_partition(_p(items), _p(dest), n, item_bytes, num_ranks, _p(out), _p(off),
+                                 _p(bad), _p(holes))
+    return out[:total], off, int(bad[0]), int(holes[0])
+
+
+# --------------------------------------------------------------------------
+# Forwarding microbenchmark
+# --------------------------------------------------------------------------
+def zipf_thresholds(num_ranks: int, s: float = 1.1) -> np.ndarray:
+    thr = np.zeros(max(num_ranks - 1, 1), np.uint32)
+    _load().or_zipf_thresholds(num_ranks, s, _p(thr))
+    return thr[: max(num_ranks - 1, 0)]
+
+
+def _grid_of(num_ranks: int, grid):
+    if grid is None:
+        return np.array([num_ranks, 1, 1], np.int32)
+    return _c(grid, np.int32)
+
+
+def choose_dest(mode: int, src: int, r1: int, num_ranks: int, grid=None, thr=None) -> int:
+    g = _grid_of(num_ranks, grid)
+    t = zipf_thresholds(num_ranks) if thr is None else _c(thr, np.uint32)
+    t = t if t.size else np.zeros(1, np.uint32)
+    return int(_load().or_c1_choose_dest(mode, src, r1, num_ranks, _p(g), _p(t)))
+
+
+def c1_walk(items: np.ndarray, num_ranks: int, seed: int, mode: int, grid=None, thr=None,
+            max_hops: int = 100000, record_visits: bool = False):
+    """Walk each item until it retires.  Returns (final n x 16, hops n, unfinished, visits)."""
+    items = _c(items, np.uint32).reshape(-1, 16)
+    n = items.shape[0]
+    g = _grid_of(num_ranks, grid)
+    t = zipf_thresholds(num_ranks) if thr is None else _c(thr, np.uint32)
+    t = t if t.size else np.zeros(1, np.uint32)
+    final = np.empty_like(items)
+    hops = np.empty(n, np.uint32)
+    visits = np.full((n, max_hops), -1, np.int32) if record_visits else None
+    unfinished = _load().or_c1_walk(_p(items), n, num_ranks, seed, mode, _p(g), _p(t), max_hops,
+                                    _p(final), _p(hops), _p(visits))
+    return final, hops, int(unfinished), visits
+
+
+def c1_rounds(items: np.ndarray, num_ranks: int, seed: int, mode: int, grid=None, thr=None,
+              max_rounds: int = 100000, dump_round: int = -1):
+    """Round-by-round queue simulation.
+
+    Returns dict(rounds, active[rounds+1], retired[rounds], retired_items,
+    dump_items, dump_offsets).
+    """
+    items = _c(items, np.uint32).reshape(-1, 16)
+    n = items.shape[0]
+    g = _grid_of(num_ranks, grid)
+    t = zipf_thresholds(num_ranks) if thr is None else _c(thr, np.uint32)
+    t = t if t.size else np.zeros(1, np.uint32)
+    active = np.zeros(max_rounds + 2, np.uint64)
+    retired = np.zeros(max_rounds + 2, np.uint64)
+    retired_items = np.zeros((max(n, 1), 16), np.uint32)
+    dump_items = np.zeros((max(n, 1), 16), np.uint32) if dump_round >= 0 else None
+    dump_off = np.zeros(num_ranks + 1, np.uint64) if dump_round >= 0 else None
+    rounds = _load().or_c1_rounds(_p(items), n, num_ranks, seed, mode, _p(g), _p(t), max_rounds,
+                                  _p(active), _p(retired), _p(retired_items), dump_round,
+                                  _p(dump_items), _p(dump_off))
+    if rounds < 0:
+        raise RuntimeError("oracle: max_rounds reached")
+    res = dict(rounds=rounds, active=active[: rounds + 1].copy(), retired=retired[:rounds].copy(),
+               retired_items=retired_items[:n])
+    if dump_round >= 0:
+        cnt = int(dump_off[-1]) if dump_round <= rounds else 0
+        res["dump_items"] = dump_items[:cnt]
+        res["dump_offsets"] = dump_off
+    return res
+
+
+# --------------------------------------------------------------------------
+# Absorption marching (Sec. 5.1 trace step, absorption only)
+# --------------------------------------------------------------------------
+def c0_primary(cam: np.ndarray, n: int, x: int, y: int):
+    cam = _c(cam, np.float32)
+    d = np.zeros(3, np.float32)
+    t0 = np.zeros(1, np.float32)
+    t1 = np.zeros(1, np.float32)
+    hit = _load().or_c0_primary(_p(cam), n, x, y, _p(d), _p(t0), _p(t1))
+    return bool(hit), d, float(t0[0]), float(t1[0])
+
+
+def c0_render(vol: np.ndarray, cam: np.ndarray, width: int, height: int, brick: int | None = None,
+              max_hops: int = 16):
+    """Render through the unpartitioned volume.  Returns dict(T, tau, nsamp, hops, hop_count)."""
+    vol = _c(vol, np.float32)
+    n = vol.shape[0]
+    b = n if brick is None else brick
+    cam = _c(cam, np.float32)
+    npx = width * height
+    T = np.zeros(npx, np.float32)
+    tau = np.zeros(npx, np.float32)
+    ns = np.zeros(npx, np.int32)
+    hop = np.full((npx, max_hops), -1, np.int32)
+    hc = np.zeros(npx, np.int32)
+    _load().or_c0_render(_p(vol), n, b, _p(cam), width, height, _p(T), _p(tau), _p(ns), _p(hop),
+                         max_hops, _p(hc))
+    return dict(T=T, tau=tau, nsamp=ns, hops=hop, hop_count=hc)
+
+
+def c0_sigma(vol: np.ndarray, p) -> float:
+    vol = _c(vol, np.float32)
+    return float(_load().or_c0_sigma(_p(vol), vol.shape[0], float(p[0]), float(p[1]), float(p[2])))

@@ -1,0 +1,423 @@
+/*
+ * Oracle for the RaFI work-forwarding hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product (the CUDA library, its
+ * Python binding) may link, load or call this file; only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark do.  It is a plain,
+ * slow, single-threaded restatement of what the method computes, written
+ * from the paper and the workload definitions, and it shares no code with
+ * the GPU path.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared  (no FMA
+ * contraction: float results of the marching workload must follow the
+ * written operation order exactly).
+ *
+ * Contents
+ *   or_philox4x32_10   counter-based generator (Salmon et al., SC'11, "Parallel
+ *                      random numbers: as easy as 1, 2, 3", Philox-4x32, 10 rounds)
+ *   or_partition       forwardRays' exchange result (Sec. 4.2.1 + 4.2.2): a
+ *                      stable partition of the emitted items by destination
+ *   or_zipf_thresholds Zipf(s) destination table for the microbenchmark
+ *   or_c1_*            the forwarding microbenchmark (hop simulator)
+ *   or_c0_*            absorption marching through a density grid (the VoPaT
+ *                      style trace kernel of Sec. 5.1, absorption only)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10.  One round maps counter (c0,c1,c2,c3) with key (k0,k1) to */
+/* (hi(M1*c2)^c1^k0, lo(M1*c2), hi(M0*c0)^c3^k1, lo(M0*c0)); the key is     */
+/* bumped by the Weyl constants between rounds.                             */
+/* ------------------------------------------------------------------------ */
+#define OR_PHILOX_M0 0xD2511F53u
+#define OR_PHILOX_M1 0xCD9E8D57u
+#define OR_PHILOX_W0 0x9E3779B9u
+#define OR_PHILOX_W1 0xBB67AE85u
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += OR_PHILOX_W0;
+            k1 += OR_PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)OR_PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)OR_PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* n independent evaluations: ctr is n x 4, key is n x 2, out is n x 4. */
+void or_philox_batch(uint64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    for (uint64_t i = 0; i < n; ++i)
+        or_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exchange (Sec. 4.2.1 "Sorting by Destination", Sec. 4.2.2 "Exchanging    */
+/* Rays", Sec. 4.2.3 "Wrap-up").                                            */
+/*                                                                          */
+/* The paper radix-sorts 64-bit keys (dest << 32 | i) and gathers the items */
+/* in key order, so items end up grouped by destination and, within one     */
+/* destination, in emission order: a stable partition by destination.  The */
+/* per-destination begin/end scan and the Alltoall/Alltoallv steps then     */
+/* hand rank r the block of items addressed to it.  On one device the       */
+/* concatenation of those blocks, in rank order, is the next round's input  */
+/* queue; rank r's incoming segment is [offset[r], offset[r+1]).  The total */
+/* is the reduce-add of received counts (Sec. 4.2.3).                       */
+/*                                                                          */
+/* Written out as a counting sort.  dest == -1 marks an empty slot (the     */
+/* paper's first single-array design, Sec. 3.2) and is skipped; any other   */
+/* destination outside [0, R) is not a valid rank (Sec. 3.3) and is counted */
+/* in *bad and dropped.                                                     */
+/* Returns the number of items delivered (offset[R]).                       */
+/* ------------------------------------------------------------------------ */
+uint64_t or_partition(const void *items, const int32_t *dest, uint64_t n, uint32_t itemBytes,
+                      int32_t R, void *out, uint64_t *offset, uint64_t *bad, uint64_t *holes)
+{
+    uint64_t *count = (uint64_t *)calloc((size_t)R, sizeof(uint64_t));
+    uint64_t nbad = 0, nholes = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        int32_t d = dest[i];
+        if (d == -1) nholes++;
+        else if (d < 0 || d >= R) nbad++;
+        else count[d]++;
+    }
+    /* exclusive scan of the per-destination counts */
+    uint64_t run = 0;
+    for (int32_t d = 0; d < R; ++d) {
+        offset[d] = run;
+        run += count[d];
+    }
+    offset[R] = run;
+    /* stable placement, in emission order */
+    uint64_t *next = (uint64_t *)malloc((size_t)R * sizeof(uint64_t));
+    for (int32_t d = 0; d < R; ++d) next[d] = offset[d];
+    const unsigned char *src = (const unsigned char *)items;
+    unsigned char *dst = (unsigned char *)out;
+    for (uint64_t i = 0; i < n; ++i) {
+        int32_t d = dest[i];
+        if (d < 0 || d >= R) continue;
+        memcpy(dst + next[d] * itemBytes, src + i * itemBytes, itemBytes);
+        next[d]++;
+    }
+    free(next);
+    free(count);
+    if (bad) *bad = nbad;
+    if (holes) *holes = nholes;
+    return run;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forwarding microbenchmark (the synthetic 64-byte work item workload).    */
+/*                                                                          */
+/* Item: 16 uint32 words w[0..15].  Round k (k = number of hops made so     */
+/* far) draws  r = Philox4x32-10(key = {seed, 1}, ctr = {w0, w1, w15, k}).  */
+/*   r0 < RETIRE_THRESHOLD (= ceil(0.1 * 2^32)): the item retires as is.   */
+/*   otherwise it picks a destination d from r1 (uniform, Zipf or one of    */
+/*   the 6 torus neighbours of its current rank), then sets w14 = d,        */
+/*   w13 ^= r2, w15 += 1 and is forwarded to rank d.                        */
+/* Item i starts on rank i mod R.                                           */
+/* ------------------------------------------------------------------------ */
+#define OR_C1_RETIRE_THRESHOLD 429496730u
+enum { OR_C1_UNIFORM = 0, OR_C1_ZIPF = 1, OR_C1_NBR6 = 2 };
+
+/* thr[k] = floor(2^32 * P(rank <= k)) for k = 0 .. R-2, where rank k has
+ * weight (k+1)^-s.  Sums run in double, in increasing j. */
+void or_zipf_thresholds(int32_t R, double s, uint32_t *thr)
+{
+    double total = 0.0;
+    for (int32_t j = 1; j <= R; ++j) total += pow((double)j, -s);
+    double partial = 0.0;
+    for (int32_t k = 0; k + 1 < R; ++k) {
+        partial += pow((double)(k + 1), -s);
+        double cdf = partial / total;
+        thr[k] = (uint32_t)floor(cdf * 4294967296.0);
+    }
+}
+
+int32_t or_c1_choose_dest(int32_t mode, int32_t src, uint32_t r1, int32_t R, const int32_t *grid,
+                          const uint32_t *thr)
+{
+    if (mode == OR_C1_UNIFORM) {
+        return (int32_t)(((uint64_t)r1 * (uint64_t)R) >> 32);
+    }
+    if (mode == OR_C1_ZIPF) {
+        for (int32_t k = 0; k + 1 < R; ++k)
+            if (r1 < thr[k]) return k;
+        return R - 1;
+    }
+    /* 6-neighbour torus: rank = x + gx*(y + gy*z) */
+    int32_t gx = grid[0], gy = grid[1], gz = grid[2];
+    int32_t x = src % gx, y = (src / gx) % gy, z = src / (gx * gy);
+    int32_t k = (int32_t)(((uint64_t)r1 * 6u) >> 32);
+    switch (k) {
+    case 0: x = (x + 1) % gx; break;
+    case 1: x = (x + gx - 1) % gx; break;
+    case 2: y = (y + 1) % gy; break;
+    case 3: y = (y + gy - 1) % gy; break;
+    case 4: z = (z + 1) % gz; break;
+    default: z = (z + gz - 1) % gz; break;
+    }
+    return x + gx * (y + gy * z);
+}
+
+/* One hop of one item.  Returns 1 when the item retires (w unchanged),
+ * 0 when it is forwarded (w updated, *dst set). */
+int32_t or_c1_hop(uint32_t *w, uint32_t seed, uint32_t hop, int32_t src, int32_t mode, int32_t R,
+                  const int32_t *grid, const uint32_t *thr, int32_t *dst)
+{
+    uint32_t ctr[4] = {w[0], w[1], w[15], hop};
+    uint32_t key[2] = {seed, 1u};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    if (r[0] < OR_C1_RETIRE_THRESHOLD) return 1;
+    int32_t d = or_c1_choose_dest(mode, src, r[1], R, grid, thr);
+    w[14] = (uint32_t)d;
+    w[13] ^= r[2];
+    w[15] += 1u;
+    *dst = d;
+    return 0;
+}
+
+/* Walk every item independently until it retires (or maxHops hops).
+ * final[i] = item i's payload at retirement, hops[i] = hops it made,
+ * visits (optional, n x maxHops) = ranks it was forwarded to.
+ * Returns the number of items that hit maxHops without retiring. */
+uint64_t or_c1_walk(const uint32_t *items, uint64_t n, int32_t R, uint32_t seed, int32_t mode,
+                    const int32_t *grid, const uint32_t *thr, uint32_t maxHops, uint32_t *final,
+                    uint32_t *hops, int32_t *visits)
+{
+    uint64_t unfinished = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t w[16];
+        memcpy(w, items + 16 * i, sizeof w);
+        int32_t rank = (int32_t)(i % (uint64_t)R);
+        uint32_t h = 0;
+        for (;;) {
+            if (h >= maxHops) { unfinished++; break; }
+            int32_t d = -1;
+            if (or_c1_hop(w, seed, h, rank, mode, R, grid, thr, &d)) break;
+            if (visits) visits[i * maxHops + h] = d;
+            rank = d;
+            h++;
+        }
+        memcpy(final + 16 * i, w, sizeof w);
+        hops[i] = h;
+    }
+    return unfinished;
+}
+
+/* The same workload run round by round through per-rank queues, the way
+ * the forwarding layer runs it: seed (item i forwarded to rank i mod R),
+ * exchange, then { every rank processes its incoming segment in order,
+ * emitting in that order; exchange } until nothing is active.
+ *
+ * active[k]  = items in the incoming queues of round k (k = 0 .. rounds-1),
+ *              active[rounds] = 0,
+ * retired[k] = items that retired in round k,
+ * retiredOut = payloads in retirement order (n x 16),
+ * dumpItems/dumpOffsets (optional) = the incoming queue and segment offsets
+ *              at the start of round dumpRound.
+ * Returns the number of rounds run, or -1 if maxRounds was reached. */
+int32_t or_c1_rounds(const uint32_t *items, uint64_t n, int32_t R, uint32_t seed, int32_t mode,
+                     const int32_t *grid, const uint32_t *thr, uint32_t maxRounds, uint64_t *active,
+                     uint64_t *retired, uint32_t *retiredOut, int32_t dumpRound, uint32_t *dumpItems,
+                     uint64_t *dumpOffsets)
+{
+    const uint32_t itemBytes = 64;
+    uint32_t *outq = (uint32_t *)malloc((size_t)(n ? n : 1) * itemBytes);
+    uint32_t *inq = (uint32_t *)malloc((size_t)(n ? n : 1) * itemBytes);
+    int32_t *dest = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    uint64_t *off = (uint64_t *)malloc((size_t)(R + 1) * sizeof(uint64_t));
+    uint64_t nret = 0;
+
+    /* seed round */
+    memcpy(outq, items, (size_t)n * itemBytes);
+    for (uint64_t i = 0; i < n; ++i) dest[i] = (int32_t)(i % (uint64_t)R);
+    uint64_t nin = or_partition(outq, dest, n, itemBytes, R, inq, off, NULL, NULL);
+
+    int32_t round = 0;
+    for (;;) {
+        if (round == dumpRound && dumpItems) {
+            memcpy(dumpItems, inq, (size_t)nin * itemBytes);
+            memcpy(dumpOffsets, off, (size_t)(R + 1) * sizeof(uint64_t));
+        }
+        if (nin == 0) {
+            active[round] = 0;
+            break;
+        }
+        if ((uint32_t)round >= maxRounds) {
+            round = -1;
+            break;
+        }
+        active[round] = nin;
+        uint64_t nout = 0, nr = 0;
+        for (int32_t r = 0; r < R; ++r) {
+            for (uint64_t i = off[r]; i < off[r + 1]; ++i) {
+                uint32_t w[16];
+                memcpy(w, inq + 16 * i, sizeof w);
+                int32_t d = -1;
+                if (or_c1_hop(w, seed, (uint32_t)round, r, mode, R, grid, thr, &d)) {
+                    memcpy(retiredOut + 16 * nret, w, sizeof w);
+                    nret++;
+                    nr++;
+                } else {
+                    memcpy(outq + 16 * nout, w, sizeof w);
+                    dest[nout] = d;
+                    nout++;
+                }
+            }
+        }
+        retired[round] = nr;
+        nin = or_partition(outq, dest, nout, itemBytes, R, inq, off, NULL, NULL);
+        round++;
+    }
+    free(outq);
+    free(inq);
+    free(dest);
+    free(off);
+    return round;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Absorption marching through a float density grid (the trace step of     */
+/* Sec. 5.1 / Fig. 1, absorption only, fixed step).                         */
+/*                                                                          */
+/* Volume: N^3 floats, voxel v has centre v + 0.5, stored x fastest.        */
+/* sigma(p): trilinear over voxel centres, clamp to edge.                   */
+/* Camera: cam = {eye[3], corner[3], du[3], dv[3]}; the unnormalised        */
+/* direction of pixel (x, y) is corner + du*(x+0.5) + dv*(y+0.5), then      */
+/* divided by its length.                                                   */
+/* Ray/box: slab test against [0, N]^3 gives [t0, t1].  Samples at          */
+/* t_k = t0 + (k + 0.5) * 0.5 while t_k < t1, position p_k = eye + dir*t_k. */
+/* tau = sum_k sigma(p_k) * 0.5 in k order; T = expf(-tau).                 */
+/* A ray with no sample (no hit, or t_0 >= t1) has T = 1.                   */
+/*                                                                          */
+/* The owner of p is the brick (floor(p/B) clamped to the brick grid), with */
+/* rank = bx + nb*(by + nb*bz).  The hop sequence of a ray is the sequence  */
+/* of owners of p_0, p_1, ... with repeats collapsed: the ranks a ray must  */
+/* visit when each rank holds one brick.                                    */
+/* All float arithmetic is written in evaluation order, no contraction.     */
+/* ------------------------------------------------------------------------ */
+static float or_c0_sample(const float *vol, int32_t N, float px, float py, float pz)
+{
+    float u[3] = {px - 0.5f, py - 0.5f, pz - 0.5f};
+    int32_t i0[3], i1[3];
+    float f[3];
+    for (int a = 0; a < 3; ++a) {
+        float fl = floorf(u[a]);
+        f[a] = u[a] - fl;
+        int32_t lo = (int32_t)fl;
+        int32_t hi = lo + 1;
+        i0[a] = lo < 0 ? 0 : (lo > N - 1 ? N - 1 : lo);
+        i1[a] = hi < 0 ? 0 : (hi > N - 1 ? N - 1 : hi);
+    }
+#define V(x, y, z) vol[((size_t)(z) * (size_t)N + (size_t)(y)) * (size_t)N + (size_t)(x)]
+    float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
+    float c00 = V(i0[0], i0[1], i0[2]) * gx + V(i1[0], i0[1], i0[2]) * f[0];
+    float c10 = V(i0[0], i1[1], i0[2]) * gx + V(i1[0], i1[1], i0[2]) * f[0];
+    float c01 = V(i0[0], i0[1], i1[2]) * gx + V(i1[0], i0[1], i1[2]) * f[0];
+    float c11 = V(i0[0], i1[1], i1[2]) * gx + V(i1[0], i1[1], i1[2]) * f[0];
+#undef V
+    float c0 = c00 * gy + c10 * f[1];
+    float c1 = c01 * gy + c11 * f[1];
+    return c0 * gz + c1 * f[2];
+}
+
+static int32_t or_c0_owner(float px, float py, float pz, int32_t B, int32_t nb)
+{
+    float p[3] = {px, py, pz};
+    int32_t b[3];
+    for (int a = 0; a < 3; ++a) {
+        int32_t v = (int32_t)floorf(p[a] / (float)B);
+        b[a] = v < 0 ? 0 : (v > nb - 1 ? nb - 1 : v);
+    }
+    return b[0] + nb * (b[1] + nb * b[2]);
+}
+
+/* Primary ray of pixel (x, y): direction and [t0, t1].  Returns 1 if the
+ * ray has at least one sample (t_0 < t1). */
+int32_t or_c0_primary(const float *cam, int32_t N, int32_t x, int32_t y, float *dir, float *t0out,
+                      float *t1out)
+{
+    float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    float d[3];
+    for (int a = 0; a < 3; ++a) d[a] = cam[3 + a] + cam[6 + a] * px + cam[9 + a] * py;
+    float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; ++a) d[a] = d[a] / len;
+    float tn[3], tf[3];
+    for (int a = 0; a < 3; ++a) {
+        float ta = (0.0f - cam[a]) / d[a];
+        float tb = ((float)N - cam[a]) / d[a];
+        tn[a] = fminf(ta, tb);
+        tf[a] = fmaxf(ta, tb);
+    }
+    float t0 = fmaxf(fmaxf(fmaxf(tn[0], tn[1]), tn[2]), 0.0f);
+    float t1 = fminf(fminf(tf[0], tf[1]), tf[2]);
+    for (int a = 0; a < 3; ++a) dir[a] = d[a];
+    *t0out = t0;
+    *t1out = t1;
+    float tk = t0 + (0.0f + 0.5f) * 0.5f;
+    return tk < t1 ? 1 : 0;
+}
+
+/* Render W x H pixels through the unpartitioned volume.
+ * T[pix], tau[pix], nsamp[pix]; hop sequences for brick size B (N % B == 0)
+ * into hopSeq[pix * maxHops + j], hopCount[pix] (may exceed maxHops; only
+ * the first maxHops entries are stored). */
+void or_c0_render(const float *vol, int32_t N, int32_t B, const float *cam, int32_t W, int32_t H,
+                  float *T, float *tau, int32_t *nsamp, int32_t *hopSeq, int32_t maxHops,
+                  int32_t *hopCount)
+{
+    int32_t nb = N / B;
+    for (int32_t y = 0; y < H; ++y) {
+        for (int32_t x = 0; x < W; ++x) {
+            int32_t pix = y * W + x;
+            float dir[3], t0, t1;
+            int32_t hit = or_c0_primary(cam, N, x, y, dir, &t0, &t1);
+            float acc = 0.0f;
+            int32_t k = 0, hops = 0, last = -1;
+            if (hit) {
+                for (;;) {
+                    float tk = t0 + ((float)k + 0.5f) * 0.5f;
+                    if (!(tk < t1)) break;
+                    float px = cam[0] + dir[0] * tk;
+                    float py = cam[1] + dir[1] * tk;
+                    float pz = cam[2] + dir[2] * tk;
+                    int32_t own = or_c0_owner(px, py, pz, B, nb);
+                    if (own != last) {
+                        if (hopSeq && hops < maxHops) hopSeq[(size_t)pix * maxHops + hops] = own;
+                        hops++;
+                        last = own;
+                    }
+                    acc = acc + or_c0_sample(vol, N, px, py, pz) * 0.5f;
+                    k++;
+                }
+            }
+            tau[pix] = acc;
+            T[pix] = expf(-acc);
+            nsamp[pix] = k;
+            if (hopCount) hopCount[pix] = hops;
+        }
+    }
+}
+
+/* Single-point access to sigma(p), for tests. */
+float or_c0_sigma(const float *vol, int32_t N, float px, float py, float pz)
+{
+    return or_c0_sample(vol, N, px, py, pz);
+}
