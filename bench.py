@@ -1,0 +1,370 @@
+"""Benchmark: device-local work forwarding on one GB300.
+
+One step = the forwarding microbenchmark run to termination three times
+(destinations uniform, Zipf s=1.1, 6-neighbour on a 4x4x4 torus): 2^24
+64-byte items over 64 logical ranks, seed, exchange, then {work; exchange}
+rounds until no item is active.  ``value`` counts items delivered by the
+exchanges of work rounds (the seed exchange is timed but not counted) per
+second of device time; inputs are resident in HBM before timing, and the
+1 GiB queues are larger than L2.
+
+Also reported on the same line: the scatter kernel's roofline (algorithmic
+bytes 2 x 64 B per delivered item over its CUDA-event time), the same run end
+to end through rf_c1_run with host buffers, rays/s of the 64^3 marching
+workload, the oracle timed on a bounded sample (cpu_baseline), SM clocks
+sampled during the timed region and the number of kernels launched.
+
+``--impl reference`` times the oracle (the CPU reference of this method) on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "forwarded items/s and rays/s on 1 GB300; forwarding HBM GB/s as % of peak"
+N_ITEMS = 1 << 24
+RANKS = 64
+GRID = (4, 4, 4)
+SEED = 1
+ITEM_BYTES = 64
+MODES = (0, 1, 2)  # uniform, Zipf 1.1, 6-neighbour torus
+WORKLOAD = ("forwarding microbenchmark: 2^24 x 64-byte items (Philox payloads), 64 logical ranks, "
+            "destinations uniform / Zipf s=1.1 / 6-neighbour 4x4x4 torus, retire p=0.1, seed 1; "
+            "one step = the three runs, each seeded and run to zero active items")
+SAMPLE_ITEMS = 1 << 18  # oracle sample per destination law, per reference-arm step
+BASELINE_ITEMS = 1 << 22  # oracle sample per destination law for cpu_baseline (about 10 s)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.reader.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample_step(sample_items):
+    import oracle
+
+    fwd = 0
+    for mode in MODES:
+        res = oracle.c1_rounds(sample_items, RANKS, SEED, mode, grid=GRID)
+        fwd += int(res["active"][1:].sum())
+    return fwd
+
+
+def oracle_baseline(steps=1):
+    from paper_2605_30294_gb300 import inputs
+
+    items = inputs.c1_items(BASELINE_ITEMS, seed=SEED)
+    t0 = time.perf_counter()
+    fwd = 0
+    for _ in range(steps):
+        fwd += oracle_sample_step(items)
+    dt = time.perf_counter() - t0
+    return fwd / dt, fwd, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2605_30294_gb300 import inputs
+
+    items = inputs.c1_items(SAMPLE_ITEMS, seed=SEED)
+    for _ in range(args.warmup):
+        oracle_sample_step(items)
+    t0 = time.perf_counter()
+    fwd = 0
+    for _ in range(args.steps):
+        fwd += oracle_sample_step(items)
+    dt = time.perf_counter() - t0
+    v = fwd / dt
+    sample = (f"{SAMPLE_ITEMS} of the 2^24 items per destination law (same seed, ranks and laws), "
+              f"run round by round through the oracle's queues")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "items/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "items/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "items/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU path
+# ---------------------------------------------------------------------------
+def traffic_for_scatter():
+    """DRAM bytes per scatter launch from a committed ncu summary, if it matches the current kernel."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "scatter_traffic.json")
+    src = os.path.join(ROOT, "paper_2605_30294_gb300", "csrc", "exchange.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("exchange_cu_sha256") != h:
+        return None
+    return d.get("bytes_per_full_size_launch")
+
+
+def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
+    n, w, h, brick = 64, 128, 128, 32
+    vol = inputs.c0_volume(n)
+    cam = inputs.c0_camera(n, w, h)
+    dvol = torch.from_numpy(vol.reshape(-1)).cuda()
+    bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+    rafi.rf_c0_make_bricks(dvol, n, brick, bricks, s)
+    image = torch.zeros(w * h, dtype=torch.float32, device="cuda")
+    with rafi.Context(8, 48, w * h) as ctx:
+        for _ in range(3):
+            rafi.rf_c0_render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            rafi.rf_c0_render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    return w * h / (ms * 1e-3), ms
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2605_30294_gb300 import build, inputs, rafi
+
+    world, rank, local = dist_env()
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    n = args.items
+    items = inputs.c1_items(n, seed=SEED)
+    d_items = torch.from_numpy(items.view(np.int32)).to(dev)
+    retired = torch.zeros((n, 16), dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    ctx = rafi.Context(RANKS, ITEM_BYTES, n)
+
+    def step():
+        fwd = 0
+        for mode in MODES:
+            st, cnt, rounds, f = rafi.rf_c1_run(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired, stream=s)
+            if cnt != n:
+                raise RuntimeError(f"mode {mode}: {cnt} of {n} items retired")
+            fwd += f
+        return fwd
+
+    for _ in range(args.warmup):
+        step()
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = None
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        gpu_id = "GPU-" + str(uuid) if not str(uuid).startswith("GPU-") else str(uuid)
+    rafi.rf_set_timing(ctx.handle, True)
+    rafi.rf_get_timing(ctx.handle, reset=True)
+    barrier()
+    launches0 = rafi.rf_launch_count()
+    with ClockSampler(gpu_id) as clocks:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fwd = 0
+        for _ in range(args.steps):
+            fwd += step()
+        e1.record(s)
+        barrier()
+    launches = rafi.rf_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    t = rafi.rf_get_timing(ctx.handle, reset=True)
+    rafi.rf_set_timing(ctx.handle, False)
+
+    # end to end through the public call with host buffers (H2D + D2H inside)
+    h_items = torch.from_numpy(items.view(np.int32)).pin_memory()
+    h_ret = torch.zeros((n, 16), dtype=torch.int32).pin_memory()
+
+    def e2e_step():
+        f = 0
+        for mode in MODES:
+            st, cnt, rounds, ff = rafi.rf_c1_run(ctx.handle, h_items.data_ptr(), n, SEED, mode, 1.1, GRID,
+                                                 h_ret.data_ptr(), host_memory=True, stream=s)
+            f += ff
+        return f
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_fwd = 0
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        e2e_fwd += e2e_step()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+
+    rays_s, c0_ms = c0_rays_per_s(torch, rafi, inputs, s)
+    ctx.close()
+
+    # max over ranks of the timed region
+    sec = ms / 1e3
+    total_fwd = fwd
+    if pg:
+        tt = torch.tensor([sec, float(fwd), e2e_s, float(e2e_fwd)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        sm = tt.clone()
+        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
+        sec, e2e_s = float(mx[0]), float(mx[2])
+        total_fwd, e2e_fwd = int(sm[1]), int(sm[3])
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = peaks()
+    bytes_alg = t.scatterItems * 2 * ITEM_BYTES
+    achieved = bytes_alg / (t.scatterMs * 1e-3) / 1e9 if t.scatterMs > 0 else 0.0
+    achieved_large = (t.scatterItemsLarge * 2 * ITEM_BYTES / (t.scatterMsLarge * 1e-3) / 1e9
+                      if t.scatterMsLarge > 0 else 0.0)
+    traffic = traffic_for_scatter()
+    cpu_v, cpu_fwd, cpu_dt = oracle_baseline()
+    line = {
+        "metric": METRIC, "value": total_fwd / sec, "unit": "items/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "items": n, "item_bytes": ITEM_BYTES, "ranks": RANKS,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "no flush: the 1 GiB item queues exceed the 129 MB L2"},
+        "roofline": {"bound": "hbm", "kernel": "scatter_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind,
+                     "achieved_rounds_ge_2^20": achieved_large, "frac_rounds_ge_2^20": achieved_large / peak,
+                     "launches": t.scatterLaunches, "launches_ge_2^20": t.scatterLaunchesLarge,
+                     "ms_total": t.scatterMs},
+        "phase_ms": {"work": t.workMs, "count": t.countMs, "scan": t.scanMs, "scatter": t.scatterMs},
+        "e2e": {"value": e2e_fwd / e2e_s, "unit": "items/s",
+                "h2d_bytes_per_step": len(MODES) * n * ITEM_BYTES,
+                "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8)},
+        "rays_per_s": {"value": rays_s, "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
+                       "ms_per_frame": c0_ms},
+        "cpu_baseline": {"value": cpu_v, "unit": "items/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{BASELINE_ITEMS} items per destination law, round-by-round oracle, "
+                                   f"{cpu_dt:.1f} s"},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--items", type=int, default=N_ITEMS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * rafi.h -- C ABI of librafi_gb.so: device-local work forwarding between
+ * logical ranks on one GB300 (sm_103a).
+ *
+ * The paper's host context (Sec. 3.4) is created over a GPU and an MPI
+ * communicator and offers three calls: resizeRayQueues(N),
+ * getDeviceInterface() and forwardRays().  Here the communicator is replaced
+ * by a count of logical ranks that all live in this GPU's memory: each rank
+ * owns one contiguous segment of a shared incoming queue, and forwardRays()
+ * (rf_exchange) is a device-side count / scan / stable scatter instead of a
+ * sort plus MPI_Alltoall(v) (Sec. 4.2).
+ *
+ * Conventions for every entry point
+ *   - Return an rf_status; nothing crosses the ABI as an exception.  On error
+ *     rf_last_error() describes the most recent failure of the calling thread.
+ *   - "device" pointers are CUDA global-memory pointers of the device that was
+ *     current when the context was created; "host" pointers are ordinary
+ *     (preferably pinned) host memory.  The caller keeps ownership of every
+ *     pointer it passes; the context owns the queues it allocates.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  All work is stream-ordered on it; the collective barrier of
+ *     forwardRays (Sec. 3.4) is plain stream order here.
+ *   - Item sizes are multiples of 16 bytes (16-byte vector copies), at most
+ *     RF_MAX_ITEM_BYTES.  Counts and offsets are below 2^31.
+ */
+#ifndef RAFI_H
+#define RAFI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RF_MAX_ITEM_BYTES 512u
+#define RF_MAX_RANKS 1024
+#define RF_MAX_CAPACITY 0x7FFFFFFFull
+
+typedef struct rf_ctx rf_ctx;
+
+typedef enum rf_status {
+    RF_OK = 0,
+    RF_ERR_ARG = 1,        /* an argument is out of range or NULL where not allowed */
+    RF_ERR_OOM = 2,        /* device or pinned host allocation failed */
+    RF_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    RF_ERR_OVERFLOW = 4,   /* emits past capacity were dropped (Sec. 3.3); results valid */
+    RF_ERR_BAD_DEST = 5,   /* items addressed to a rank outside [0, numRanks) were dropped */
+    RF_ERR_MAX_ROUNDS = 6, /* a round loop hit its round limit with items still active */
+    RF_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up; the kernel returned early */
+    RF_ERR_STATE = 8       /* call not valid in the context's current state */
+} rf_status;
+
+/*
+ * Device interface (Sec. 3.3, "DeviceInterface<T>"): a trivially copyable
+ * struct that kernels receive by value.  Device-side helpers that read and
+ * write it live in rafi_device.cuh (numIncoming, getIncoming, rankOf,
+ * forward / emitOutgoing).
+ *
+ *   in        incoming items of all ranks, rank r's at [inOffset[r], inOffset[r+1])
+ *   out       outgoing append queue (capacity items)
+ *   dest      destination rank of each outgoing slot; -1 = empty slot (skipped)
+ *   outCount  atomic append counter; it may run past capacity, and every emit
+ *             at or past capacity is dropped (Sec. 3.3)
+ *   inOffset  numRanks + 1 offsets; inOffset[numRanks] = items incoming in total
+ */
+typedef struct rf_device_queues {
+    void *in;
+    void *out;
+    int32_t *dest;
+    unsigned long long *outCount;
+    const uint32_t *inOffset;
+    uint64_t capacity;
+    uint32_t itemBytes;
+    int32_t numRanks;
+} rf_device_queues;
+
+/* What the most recent exchange saw, plus running totals since create. */
+typedef struct rf_round_stats {
+    uint64_t numActive;      /* items delivered (Sec. 4.2.3's reduce-add of received counts) */
+    uint64_t emitted;        /* valid slots the out-queue held: min(outCount, capacity) */
+    uint64_t dropped;        /* emits past capacity */
+    uint64_t badDest;        /* slots whose destination was not -1 and outside [0, numRanks) */
+    uint64_t holes;          /* slots with destination -1 */
+    uint64_t exchanges;      /* exchanges since create */
+    uint64_t totalDelivered; /* items delivered, summed over exchanges */
+    uint64_t totalDropped;   /* dropped + badDest, summed over exchanges */
+} rf_round_stats;
+
+/* Accumulated device time per phase (CUDA events on the launching stream),
+ * collected only while rf_set_timing(ctx, 1) is in effect. */
+typedef struct rf_phase_times {
+    double countMs, scanMs, scatterMs, workMs;
+    uint64_t countLaunches, scanLaunches, scatterLaunches, workLaunches;
+    uint64_t scatterItems;      /* items the timed scatter launches delivered */
+    double scatterMsLarge;      /* the same, restricted to exchanges of >= 2^20 items */
+    uint64_t scatterItemsLarge;
+    uint64_t scatterLaunchesLarge;
+} rf_phase_times;
+
+/* --- host context (Sec. 3.4) ------------------------------------------- */
+
+/* Create a context on the current CUDA device: numRanks logical ranks
+ * (1..RF_MAX_RANKS), items of itemBytes bytes (multiple of 16, <=
+ * RF_MAX_ITEM_BYTES), queues of capacity items in total over all ranks
+ * (1..RF_MAX_CAPACITY; Sec. 3.4 resizeRayQueues).  Allocates the in/out
+ * queues, destinations, counters and exchange scratch on the device.
+ * *out is set on success and must be released with rf_destroy. */
+rf_status rf_create(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, rf_ctx **out);
+
+/* Release every allocation of the context (synchronises the device). NULL is a no-op. */
+rf_status rf_destroy(rf_ctx *ctx);
+
+/* resizeRayQueues(N) (Sec. 3.4): reallocate for a new total capacity.
+ * Queue contents are discarded; the context is left empty. */
+rf_status rf_resize(rf_ctx *ctx, uint64_t capacity);
+
+/* getDeviceInterface() (Sec. 3.4): fill *out with the device pointers kernels use. */
+rf_status rf_get_device_queues(rf_ctx *ctx, rf_device_queues *out);
+
+/* forwardRays() (Sec. 3.4, Sec. 4.2): deliver every item in the out-queue to
+ * its destination rank's incoming segment, stably (items keep their emission
+ * order within a destination), reset the append counter, and compute the
+ * number of items now active.  Kernels: count per destination, exclusive
+ * scan, shared-memory-bucketed scatter, wrap-up.
+ * numActiveOut != NULL: waits for the stream and returns the count, with
+ *   RF_ERR_OVERFLOW / RF_ERR_BAD_DEST if items were dropped (the count is
+ *   still valid).
+ * numActiveOut == NULL: returns without waiting; errors surface on the next
+ *   rf_num_active / rf_stats. */
+rf_status rf_exchange(rf_ctx *ctx, void *stream, uint64_t *numActiveOut);
+
+/* Total of the most recent exchange (numIncoming over all ranks, Sec. 3.3);
+ * waits for that exchange's stream. */
+rf_status rf_num_active(rf_ctx *ctx, uint64_t *out);
+
+/* numIncoming for one rank (Sec. 3.3), on the host: its segment [offset, offset + count). */
+rf_status rf_segment(rf_ctx *ctx, int32_t rank, uint64_t *offset, uint64_t *count);
+
+/* Statistics of the most recent exchange and running totals (waits for the stream). */
+rf_status rf_stats(rf_ctx *ctx, rf_round_stats *out);
+
+/* emitOutgoing from the host (Sec. 3.3): append n items with destinations to
+ * the out-queue.  items (n x itemBytes) and dest (n int32) are host memory
+ * when hostMemory != 0, device memory otherwise.  Items past capacity are
+ * dropped and reported by the next exchange. */
+rf_status rf_push(rf_ctx *ctx, const void *items, const int32_t *dest, uint64_t n, int32_t hostMemory,
+                  void *stream);
+
+/* Checkpoint: copy the incoming queue (rf_num_active items) and its numRanks+1
+ * offsets out of the context.  Device pointers; itemsOut holds capacity items. */
+rf_status rf_snapshot(rf_ctx *ctx, void *itemsOut, uint32_t *offsetsOut, void *stream);
+
+/* Resume: replace the incoming queue with n items (device) whose segments are
+ * given by numRanks+1 offsets (device, offsets[numRanks] == n). */
+rf_status rf_restore(rf_ctx *ctx, const void *items, const uint32_t *offsets, uint64_t n, void *stream);
+
+/* Per-phase CUDA-event timing on/off; read and clear the accumulated times. */
+rf_status rf_set_timing(rf_ctx *ctx, int32_t enable);
+rf_status rf_get_timing(rf_ctx *ctx, rf_phase_times *out, int32_t reset);
+
+/* Kernels this library launched in this process so far (all contexts). */
+uint64_t rf_launch_count(void);
+
+/* Message of the calling thread's most recent error ("" if none). */
+const char *rf_last_error(void);
+
+/* --- forwarding microbenchmark (64-byte items) --------------------------- */
+
+/* Destination laws of the microbenchmark work kernel. */
+#define RF_C1_UNIFORM 0
+#define RF_C1_ZIPF 1
+#define RF_C1_NBR6 2
+
+/* Zipf table for numRanks ranks and exponent s, on the host: thr[k] =
+ * floor(2^32 * P(rank <= k)), rank k weighted (k+1)^-s, k = 0 .. numRanks-2;
+ * sums in double, in increasing k. */
+rf_status rf_c1_zipf_thresholds(int32_t numRanks, double s, uint32_t *thrHost);
+
+/* Seed (the raygen step of Sec. 5.1): emit item i of items (device, n x 64
+ * bytes) to rank i mod numRanks.  Follow with rf_exchange. */
+rf_status rf_c1_seed(rf_ctx *ctx, const void *items, uint64_t n, void *stream);
+
+/* One round of the per-rank work kernel over the incoming queue (64-byte
+ * items, words w0..w15).  Each item draws r = Philox4x32-10(key {seed, 1},
+ * counter {w0, w1, w15, hop}) (Salmon et al., SC'11).  r0 < ceil(0.1 * 2^32):
+ * the item retires unchanged into retired (device, retiredCapacity items) at
+ * index atomicAdd(retiredCount, 1) (device counter).  Otherwise r1 picks a
+ * destination d by mode: RF_C1_UNIFORM floor(r1 * numRanks / 2^32);
+ * RF_C1_ZIPF the first k with r1 < thr[k] of rf_c1_zipf_thresholds(numRanks,
+ * zipfS), else numRanks - 1; RF_C1_NBR6 direction floor(r1 * 6 / 2^32) =
+ * +x,-x,+y,-y,+z,-z from the item's rank on the torus gx x gy x gz (rank = x +
+ * gx*(y + gy*z), wrapping).  The item becomes w14 = d, w13 ^= r2, w15 += 1 and
+ * is forwarded to d.
+ * deterministic != 0: out slot i holds incoming item i (destination -1 when it
+ * retired), so queue order does not depend on scheduling; the out-queue must
+ * be empty before the call. */
+rf_status rf_c1_work(rf_ctx *ctx, uint32_t seed, uint32_t hop, int32_t mode, double zipfS, int32_t gx,
+                     int32_t gy, int32_t gz, void *retired, unsigned long long *retiredCount,
+                     uint64_t retiredCapacity, int32_t deterministic, void *stream);
+
+/* The whole microbenchmark: seed, exchange, then { work (hop = round); exchange }
+ * until no item is active (RF_ERR_MAX_ROUNDS after maxRounds rounds).
+ * hostMemory == 0: items and retired are device buffers of n x 64 bytes.
+ * hostMemory != 0: they are host buffers (pinned for speed); the items are
+ *   copied into the empty out-queue and the retired items back, inside the call.
+ * *retiredCountOut (host) = items retired; *rounds = work rounds run;
+ * *forwarded = items delivered by the exchanges after work rounds (the seed
+ * exchange excluded).  Waits for the stream before returning. */
+rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
+                    int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,
+                    int32_t deterministic, int32_t hostMemory, uint32_t maxRounds, void *stream,
+                    uint64_t *rounds, uint64_t *forwarded);
+
+/* --- absorption marching through bricks (48-byte rays) ------------------- */
+
+/* Cut an N^3 float volume (device, x fastest) into (N/B)^3 bricks of
+ * (B+2)^3 floats with a one-voxel halo, clamp-to-edge at the volume border;
+ * brick of rank r = bx + nb*(by + nb*bz) at bricks + r*(B+2)^3. */
+rf_status rf_c0_make_bricks(const float *volume, int32_t N, int32_t B, float *bricks, void *stream);
+
+/* Raygen (Sec. 5.1 step 2): one primary ray per pixel of a W x H pinhole
+ * camera cam (host, 12 floats: eye, corner, du, dv); a ray with a sample in
+ * [0,N]^3 is forwarded to the brick holding its first sample, any other ray
+ * writes T = 1 to image (device, W*H floats).  Follow with rf_exchange. */
+rf_status rf_c0_raygen(rf_ctx *ctx, const float *cam, int32_t N, int32_t B, int32_t W, int32_t H,
+                       float *image, void *stream);
+
+/* Trace (Sec. 5.1 step 3, absorption only): every rank marches its incoming
+ * rays through its brick at step 0.5 (tau += sigma * 0.5), forwarding a ray
+ * to the next brick when a sample leaves its own, and writing T = expf(-tau)
+ * to image[pixel] when the ray leaves the volume.  hopLog (device, W*H x
+ * maxHops, nullable) records the ranks each pixel's ray visited, hopCount
+ * (device, W*H) how many. */
+rf_status rf_c0_march(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, float *image,
+                      int32_t *hopLog, int32_t maxHops, int32_t *hopCount, void *stream);
+
+/* The whole render: raygen, exchange, then { march; exchange } until no ray
+ * is active (at most maxRounds rounds).  *rounds = march rounds run. */
+rf_status rf_c0_render(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B,
+                       int32_t W, int32_t H, float *image, int32_t *hopLog, int32_t maxHops,
+                       int32_t *hopCount, uint32_t maxRounds, void *stream, uint64_t *rounds);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAFI_H */

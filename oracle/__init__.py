@@ -54,7 +54,7 @@ def _load():
             lib.or_zipf_thresholds.restype = None
             lib.or_c1_choose_dest.argtypes = [i32, i32, u32, i32, P, P]
             lib.or_c1_choose_dest.restype = i32
-            lib.or_c1_walk.argtypes = [P, u64, i32, u32, i32, P, P, u32, P, P, P]
+            lib.or_c1_walk.argtypes = [P, u64, i32, u32, i32, P, P, u32, P, P, P, P]
             lib.or_c1_walk.restype = u64
             lib.or_c1_rounds.argtypes = [P, u64, i32, u32, i32, P, P, u32, P, P, P, i32, P, P]
             lib.or_c1_rounds.restype = i32
@@ -134,17 +134,21 @@ def choose_dest(mode: int, src: int, r1: int, num_ranks: int, grid=None, thr=Non
 
 
 def c1_walk(items: np.ndarray, num_ranks: int, seed: int, mode: int, grid=None, thr=None,
-            max_hops: int = 100000, record_visits: bool = False):
-    """Walk each item until it retires.  Returns (final n x 16, hops n, unfinished, visits)."""
+            max_hops: int = 100000, record_visits: bool = False, start_ranks=None):
+    """Walk each item until it retires (item i starts on start_ranks[i], default i mod R).
+
+    Returns (final n x 16, hops n, unfinished, visits).
+    """
     items = _c(items, np.uint32).reshape(-1, 16)
     n = items.shape[0]
+    sr = None if start_ranks is None else _c(start_ranks, np.int32)
     g = _grid_of(num_ranks, grid)
     t = zipf_thresholds(num_ranks) if thr is None else _c(thr, np.uint32)
     t = t if t.size else np.zeros(1, np.uint32)
     final = np.empty_like(items)
     hops = np.empty(n, np.uint32)
     visits = np.full((n, max_hops), -1, np.int32) if record_visits else None
-    unfinished = _load().or_c1_walk(_p(items), n, num_ranks, seed, mode, _p(g), _p(t), max_hops,
+    unfinished = _load().or_c1_walk(_p(items), n, num_ranks, seed, mode, _p(g), _p(t), max_hops, _p(sr),
                                     _p(final), _p(hops), _p(visits))
     return final, hops, int(unfinished), visits
 

@@ -194,18 +194,19 @@ int32_t or_c1_hop(uint32_t *w, uint32_t seed, uint32_t hop, int32_t src, int32_t
 }
 
 /* Walk every item independently until it retires (or maxHops hops).
+ * Item i starts on startRank[i], or on rank i mod R when startRank is NULL.
  * final[i] = item i's payload at retirement, hops[i] = hops it made,
  * visits (optional, n x maxHops) = ranks it was forwarded to.
  * Returns the number of items that hit maxHops without retiring. */
 uint64_t or_c1_walk(const uint32_t *items, uint64_t n, int32_t R, uint32_t seed, int32_t mode,
-                    const int32_t *grid, const uint32_t *thr, uint32_t maxHops, uint32_t *final,
-                    uint32_t *hops, int32_t *visits)
+                    const int32_t *grid, const uint32_t *thr, uint32_t maxHops, const int32_t *startRank,
+                    uint32_t *final, uint32_t *hops, int32_t *visits)
 {
     uint64_t unfinished = 0;
     for (uint64_t i = 0; i < n; ++i) {
         uint32_t w[16];
         memcpy(w, items + 16 * i, sizeof w);
-        int32_t rank = (int32_t)(i % (uint64_t)R);
+        int32_t rank = startRank ? startRank[i] : (int32_t)(i % (uint64_t)R);
         uint32_t h = 0;
         for (;;) {
             if (h >= maxHops) { unfinished++; break; }

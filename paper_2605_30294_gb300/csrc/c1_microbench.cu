@@ -1,0 +1,364 @@
+// Forwarding microbenchmark: 64-byte work items that hop between logical
+// ranks until they retire.  This is the synthetic stand-in for the paper's
+// forwarding-only bandwidth benchmark (Sec. 6.1), driven through the same
+// interface an application uses (Sec. 3.3, 3.4): a seed kernel emits the
+// initial items (the raygen step of Sec. 5.1), a per-rank work kernel reads
+// its incoming segment and forwards or retires each item, and rf_exchange
+// delivers the forwarded items, round after round, until none is active.
+//
+// Hop rule (item words w0..w15): r = Philox4x32-10(key {seed, 1}, counter
+// {w0, w1, w15, hop}); r0 < ceil(0.1 * 2^32) retires the item, otherwise r1
+// picks the destination d (uniform, Zipf table, or one of the 6 torus
+// neighbours of the item's rank) and the item becomes w14 = d, w13 ^= r2,
+// w15 += 1.  Philox4x32-10 follows Salmon et al., SC'11.
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+#include "rafi_device.cuh"
+
+namespace rfi {
+
+rf_status configure_exchange(rf_ctx *ctx);
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr uint32_t kRetire = 429496730u;  // ceil(0.1 * 2^32)
+
+// One Philox4x32 round and the 10-round generator (Salmon et al., SC'11).
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint2 k)
+{
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    return make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    c = philox_round(c, k);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+        c = philox_round(c, k);
+    }
+    return c;
+}
+
+struct WorkArgs {
+    rf_device_queues q;
+    const uint32_t *zipfThr;
+    uint4 *retired;
+    unsigned long long *retiredCount;
+    unsigned long long retiredCap;
+    uint32_t seed, hop;
+    int32_t mode, gx, gy, gz;
+};
+
+__device__ __forceinline__ int32_t choose_dest(int32_t mode, int32_t src, uint32_t r1, int32_t R,
+                                               const uint32_t *thr, int32_t gx, int32_t gy, int32_t gz)
+{
+    if (mode == RF_C1_UNIFORM) return (int32_t)(((unsigned long long)r1 * (unsigned)R) >> 32);
+    if (mode == RF_C1_ZIPF) {
+        // first k with r1 < thr[k] (thresholds ascending); R - 1 if none
+        int32_t lo = 0, hi = R - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (r1 < thr[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        return lo;
+    }
+    int32_t x = src % gx, y = (src / gx) % gy, z = src / (gx * gy);
+    const int32_t k = (int32_t)(((unsigned long long)r1 * 6u) >> 32);
+    if (k == 0) x = (x + 1) % gx;
+    else if (k == 1) x = (x + gx - 1) % gx;
+    else if (k == 2) y = (y + 1) % gy;
+    else if (k == 3) y = (y + gy - 1) % gy;
+    else if (k == 4) z = (z + 1) % gz;
+    else z = (z + gz - 1) % gz;
+    return x + gx * (y + gy * z);
+}
+
+// Per-rank work kernel: one thread per incoming item; the owning rank comes
+// from the segment offsets.  DET: out slot = incoming index (retired slots
+// get destination -1), otherwise a block-aggregated append.
+template <bool DET>
+__global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
+{
+    __shared__ uint32_t sOff[RF_MAX_RANKS + 1];
+    __shared__ uint32_t sThr[RF_MAX_RANKS];
+    __shared__ typename rf::BlockAppend<kBlock>::Storage sFwd, sRet;
+    const int R = a.q.numRanks;
+    for (int e = threadIdx.x; e <= R; e += kBlock) sOff[e] = a.q.inOffset[e];
+    if (a.mode == RF_C1_ZIPF)
+        for (int e = threadIdx.x; e < R - 1; e += kBlock) sThr[e] = a.zipfThr[e];
+    __syncthreads();
+    const uint32_t n = sOff[R];
+    if (DET && blockIdx.x == 0 && threadIdx.x == 0) *a.q.outCount = n;
+
+    const uint4 *inq = static_cast<const uint4 *>(a.q.in);
+    uint4 *outq = static_cast<uint4 *>(a.q.out);
+    for (uint32_t base = blockIdx.x * kBlock; base < n; base += gridDim.x * kBlock) {
+        const uint32_t i = base + threadIdx.x;
+        const bool active = i < n;
+        uint4 w0 = {}, w1 = {}, w2 = {}, w3 = {};
+        bool retire = false;
+        int32_t d = -1;
+        if (active) {
+            const uint4 *p = inq + (size_t)i * 4;
+            w0 = __ldg(p);
+            w1 = __ldg(p + 1);
+            w2 = __ldg(p + 2);
+            w3 = __ldg(p + 3);
+            const uint4 r = philox4x32_10(make_uint4(w0.x, w0.y, w3.w, a.hop), make_uint2(a.seed, 1u));
+            if (r.x < kRetire) {
+                retire = true;
+            } else {
+                const int32_t src = rf::rankOf(sOff, R, i);
+                d = choose_dest(a.mode, src, r.y, R, sThr, a.gx, a.gy, a.gz);
+                w3.z = (uint32_t)d;
+                w3.y ^= r.z;
+                w3.w += 1u;
+            }
+        }
+        const bool fwd = active && !retire;
+        if (DET) {
+            if (fwd) {
+                uint4 *o = outq + (size_t)i * 4;
+                o[0] = w0;
+                o[1] = w1;
+                o[2] = w2;
+                o[3] = w3;
+            }
+            if (active) a.q.dest[i] = fwd ? d : -1;
+        } else {
+            const unsigned long long slot = rf::BlockAppend<kBlock>::reserve(sFwd, a.q.outCount, fwd);
+            if (fwd && slot < a.q.capacity) {
+                uint4 *o = outq + (size_t)slot * 4;
+                o[0] = w0;
+                o[1] = w1;
+                o[2] = w2;
+                o[3] = w3;
+                a.q.dest[slot] = d;
+            }
+        }
+        const bool ret = active && retire;
+        const unsigned long long rs = rf::BlockAppend<kBlock>::reserve(sRet, a.retiredCount, ret);
+        if (ret && rs < a.retiredCap) {
+            uint4 *o = a.retired + (size_t)rs * 4;
+            o[0] = w0;
+            o[1] = w1;
+            o[2] = w2;
+            o[3] = w3;
+        }
+    }
+}
+
+// Seed: emit item i to rank i mod R at out slot base + i, where base was
+// reserved on the append counter by reserve_kernel.
+__global__ void __launch_bounds__(kBlock) seed_kernel(const uint4 *items, uint32_t n, rf_device_queues q,
+                                                      const unsigned long long *base)
+{
+    const unsigned long long b = *base;
+    uint4 *outq = static_cast<uint4 *>(q.out);
+    const uint64_t vecs = (uint64_t)n * 4u;
+    for (uint64_t v = blockIdx.x * (uint64_t)kBlock + threadIdx.x; v < vecs; v += (uint64_t)gridDim.x * kBlock) {
+        const uint32_t i = (uint32_t)(v >> 2);
+        if (b + i < q.capacity) {
+            outq[(b + i) * 4 + (v & 3u)] = __ldg(items + v);
+            if ((v & 3u) == 0) q.dest[b + i] = (int32_t)(i % (uint32_t)q.numRanks);
+        }
+    }
+}
+
+// Seed for items already copied into out slots [0, n): destinations only.
+__global__ void __launch_bounds__(kBlock) seed_dest_kernel(uint32_t n, rf_device_queues q)
+{
+    for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
+        q.dest[i] = (int32_t)(i % (uint32_t)q.numRanks);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *q.outCount = n;
+}
+
+__global__ void reserve_kernel(unsigned long long *counter, unsigned long long n, unsigned long long *base)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *base = atomicAdd(counter, n);
+}
+
+rf_status check_c1(rf_ctx *ctx, const char *fn)
+{
+    if (!ctx) {
+        set_error("%s: NULL context", fn);
+        return RF_ERR_ARG;
+    }
+    if (ctx->itemBytes != 64) {
+        set_error("%s: the microbenchmark moves 64-byte items (context has %u)", fn, ctx->itemBytes);
+        return RF_ERR_ARG;
+    }
+    return RF_OK;
+}
+
+rf_status ensure_zipf(rf_ctx *ctx, double s)
+{
+    if (ctx->zipfS == s) return RF_OK;
+    std::vector<uint32_t> thr((size_t)ctx->numRanks, 0u);
+    rf_status st = rf_c1_zipf_thresholds(ctx->numRanks, s, thr.data());
+    if (st != RF_OK) return st;
+    RF_CUDA(cudaMemcpy(ctx->zipfThr, thr.data(), thr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    ctx->zipfS = s;
+    return RF_OK;
+}
+
+int grid_for(rf_ctx *ctx, uint64_t work, int perSM)
+{
+    const uint64_t want = (work + kBlock - 1) / kBlock;
+    const uint64_t cap = (uint64_t)ctx->numSMs * (uint64_t)perSM;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+}  // namespace
+}  // namespace rfi
+
+using namespace rfi;
+
+extern "C" {
+
+rf_status rf_c1_zipf_thresholds(int32_t numRanks, double s, uint32_t *thrHost)
+{
+    if (numRanks < 1 || numRanks > RF_MAX_RANKS || !thrHost || !(s > 0.0)) {
+        set_error("rf_c1_zipf_thresholds: bad arguments");
+        return RF_ERR_ARG;
+    }
+    double total = 0.0;
+    for (int32_t j = 1; j <= numRanks; ++j) total += std::pow((double)j, -s);
+    double partial = 0.0;
+    for (int32_t k = 0; k + 1 < numRanks; ++k) {
+        partial += std::pow((double)(k + 1), -s);
+        thrHost[k] = (uint32_t)std::floor(partial / total * 4294967296.0);
+    }
+    return RF_OK;
+}
+
+rf_status rf_c1_seed(rf_ctx *ctx, const void *items, uint64_t n, void *stream)
+{
+    if (rf_status st = check_c1(ctx, "rf_c1_seed")) return st;
+    if (n > ctx->capacity || (n && !items)) {
+        set_error("rf_c1_seed: n %llu above capacity or NULL items", (unsigned long long)n);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rf_device_queues q;
+    rf_get_device_queues(ctx, &q);
+    reserve_kernel<<<1, 32, 0, s>>>(q.outCount, n, &ctx->dev->scratch);
+    RF_LAUNCHED("reserve_kernel");
+    if (n) {
+        seed_kernel<<<grid_for(ctx, n * 4, 8), kBlock, 0, s>>>(static_cast<const uint4 *>(items), (uint32_t)n, q,
+                                                              &ctx->dev->scratch);
+        RF_LAUNCHED("seed_kernel");
+    }
+    return RF_OK;
+}
+
+rf_status rf_c1_work(rf_ctx *ctx, uint32_t seed, uint32_t hop, int32_t mode, double zipfS, int32_t gx, int32_t gy,
+                     int32_t gz, void *retired, unsigned long long *retiredCount, uint64_t retiredCapacity,
+                     int32_t deterministic, void *stream)
+{
+    if (rf_status st = check_c1(ctx, "rf_c1_work")) return st;
+    if (mode < RF_C1_UNIFORM || mode > RF_C1_NBR6 || !retired || !retiredCount) {
+        set_error("rf_c1_work: bad mode or NULL retired buffer");
+        return RF_ERR_ARG;
+    }
+    if (mode == RF_C1_NBR6 && (gx < 1 || gy < 1 || gz < 1 || gx * gy * gz != ctx->numRanks)) {
+        set_error("rf_c1_work: torus %dx%dx%d does not have %d ranks", gx, gy, gz, ctx->numRanks);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (mode == RF_C1_ZIPF)
+        if (rf_status st = ensure_zipf(ctx, zipfS)) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WorkArgs a;
+    rf_get_device_queues(ctx, &a.q);
+    a.zipfThr = ctx->zipfThr;
+    a.retired = static_cast<uint4 *>(retired);
+    a.retiredCount = retiredCount;
+    a.retiredCap = retiredCapacity;
+    a.seed = seed;
+    a.hop = hop;
+    a.mode = mode;
+    a.gx = gx;
+    a.gy = gy;
+    a.gz = gz;
+    // the incoming count is only known on the device: size the grid for the
+    // capacity, up to 8 resident blocks per SM, and loop
+    const int grid = grid_for(ctx, ctx->capacity, 8);
+    time_begin(ctx, kTimeWork, s);
+    if (deterministic) work_kernel<true><<<grid, kBlock, 0, s>>>(a);
+    else work_kernel<false><<<grid, kBlock, 0, s>>>(a);
+    RF_LAUNCHED("work_kernel");
+    time_end(ctx, kTimeWork, s);
+    return RF_OK;
+}
+
+rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
+                    int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,
+                    int32_t deterministic, int32_t hostMemory, uint32_t maxRounds, void *stream,
+                    uint64_t *rounds, uint64_t *forwarded)
+{
+    if (rf_status st = check_c1(ctx, "rf_c1_run")) return st;
+    if (n > ctx->capacity || (n && (!items || !retired)) || !retiredCountOut) {
+        set_error("rf_c1_run: n %llu above capacity or NULL buffer", (unsigned long long)n);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *devRetired = retired;
+    if (hostMemory) {
+        if (rf_status st = ensure_staging(ctx)) return st;
+        devRetired = ctx->staging;
+    }
+    RF_CUDA(cudaMemsetAsync(ctx->stagingCount, 0, sizeof(unsigned long long), s));
+
+    uint64_t active = 0, fwd = 0, r = 0;
+    rf_status st;
+    if (hostMemory) {
+        // host items land straight in the (empty) out-queue, then get their destinations
+        rf_device_queues q;
+        rf_get_device_queues(ctx, &q);
+        if (n) RF_CUDA(cudaMemcpyAsync(q.out, items, (size_t)n * 64u, cudaMemcpyHostToDevice, s));
+        seed_dest_kernel<<<grid_for(ctx, n, 8), kBlock, 0, s>>>((uint32_t)n, q);
+        RF_LAUNCHED("seed_dest_kernel");
+    } else {
+        st = rf_c1_seed(ctx, items, n, stream);
+        if (st != RF_OK) return st;
+    }
+    st = rf_exchange(ctx, stream, &active);
+    if (st != RF_OK) return st;
+    while (active > 0) {
+        if (r >= maxRounds) {
+            set_error("rf_c1_run: %llu items still active after %u rounds", (unsigned long long)active, maxRounds);
+            st = RF_ERR_MAX_ROUNDS;
+            break;
+        }
+        st = rf_c1_work(ctx, seed, (uint32_t)r, mode, zipfS, gx, gy, gz, devRetired, ctx->stagingCount, n,
+                        deterministic, stream);
+        if (st != RF_OK) return st;
+        st = rf_exchange(ctx, stream, &active);
+        if (st != RF_OK) return st;
+        fwd += active;
+        ++r;
+    }
+    unsigned long long cnt = 0;
+    RF_CUDA(cudaMemcpyAsync(&cnt, ctx->stagingCount, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    RF_CUDA(cudaStreamSynchronize(s));
+    if (hostMemory && cnt)
+        RF_CUDA(cudaMemcpyAsync(retired, ctx->staging, (size_t)(cnt < n ? cnt : n) * 64u, cudaMemcpyDeviceToHost, s));
+    if (hostMemory) RF_CUDA(cudaStreamSynchronize(s));
+    *retiredCountOut = cnt;
+    if (rounds) *rounds = r;
+    if (forwarded) *forwarded = fwd;
+    return st == RF_ERR_MAX_ROUNDS ? st : RF_OK;
+}
+
+}  // extern "C"

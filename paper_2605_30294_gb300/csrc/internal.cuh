@@ -1,0 +1,195 @@
+// Internal declarations shared by the librafi_gb.so translation units:
+// the context layout, error and launch bookkeeping, and thin inline-PTX
+// wrappers (mbarrier, bulk async copy) used by the exchange kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "rafi.h"
+
+namespace rfi {
+
+// Device-resident state of one context.  The exchange's wrap-up kernel
+// copies the per-exchange counters into the last* fields and clears the
+// accumulators; the host reads the struct back after each exchange.
+struct DevState {
+    unsigned long long outCount;   // append counter of the out-queue
+    unsigned long long bad;        // slots with an invalid destination (this exchange)
+    unsigned long long holes;      // slots with destination -1 (this exchange)
+    unsigned long long numActive;  // items delivered by the last exchange
+    unsigned long long lastEmitted, lastDropped, lastBad, lastHoles;
+    unsigned long long exchanges, totalDelivered, totalDropped;
+    unsigned long long scratch;    // one-word scratch (append reservations)
+    unsigned int status;           // RF_DEV_* bits, sticky until the host reads them
+    unsigned int pad;
+};
+
+enum : unsigned int { RF_DEV_TIMEOUT = 1u };
+
+// Upper bound on any spin-wait, in SM clock cycles (about half a second at
+// 2 GHz); a wait that runs out sets RF_DEV_TIMEOUT and the kernel returns.
+constexpr long long kSpinLimitCycles = 1000000000ll;
+
+}  // namespace rfi
+
+struct rf_ctx {
+    int device = 0;
+    int32_t numRanks = 0;
+    uint32_t itemBytes = 0;
+    uint64_t capacity = 0;
+    uint32_t tileItems = 0;  // items per exchange tile
+    uint32_t maxTiles = 0;   // tiles for a full queue, rounded up to a multiple of 4
+    int numSMs = 0;
+    int countBlocks = 0, scatterBlocks = 0;
+    size_t scatterSmem = 0;
+
+    void *in = nullptr;
+    void *out = nullptr;
+    int32_t *dest = nullptr;
+    uint32_t *inOffset = nullptr;  // numRanks + 1
+    uint32_t *count = nullptr;     // numRanks
+    uint32_t *tileHist = nullptr;  // numRanks x maxTiles, digit-major
+    rfi::DevState *dev = nullptr;
+    rfi::DevState *host = nullptr;  // pinned mirror of *dev
+    void *staging = nullptr;        // lazily allocated: capacity items (host-memory runs)
+    unsigned long long *stagingCount = nullptr;
+
+    cudaStream_t lastStream = nullptr;
+    bool pending = false;  // an exchange's read-back has not been waited for
+
+    uint32_t *zipfThr = nullptr;  // numRanks words: Zipf table of the microbenchmark
+    double zipfS = -1.0;           // exponent the table was built for
+
+    bool timing = false;
+    unsigned pendingSlots = 0;  // timing slots recorded since the last read-back
+    cudaEvent_t ev[10] = {};
+    rf_phase_times times = {};
+};
+
+namespace rfi {
+
+extern std::atomic<unsigned long long> g_launches;
+
+void set_error(const char *fmt, ...);
+rf_status cuda_fail(cudaError_t e, const char *what);
+
+inline void count_launch(unsigned long long k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+#define RF_CUDA(call)                                       \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return rfi::cuda_fail(e_, #call); \
+    } while (0)
+
+#define RF_LAUNCHED(name)                                       \
+    do {                                                        \
+        rfi::count_launch();                                    \
+        cudaError_t e_ = cudaGetLastError();                    \
+        if (e_ != cudaSuccess) return rfi::cuda_fail(e_, name); \
+    } while (0)
+
+// Makes the context's device current for the scope of an entry point.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Read back the device state of the last exchange (waits for its stream)
+// and translate the counters into a status.
+rf_status sync_state(rf_ctx *ctx);
+
+// Launch count / scan / scatter / wrap-up for the context's out-queue.
+rf_status launch_exchange(rf_ctx *ctx, cudaStream_t s);
+
+// Allocate ctx->staging (capacity items) on first use.
+rf_status ensure_staging(rf_ctx *ctx);
+
+// Per-phase timing helpers (no-ops unless ctx->timing).
+void time_begin(rf_ctx *ctx, int slot, cudaStream_t s);
+void time_end(rf_ctx *ctx, int slot, cudaStream_t s);
+void time_collect(rf_ctx *ctx);  // after a stream sync: accumulate recorded pairs
+
+enum TimeSlot { kTimeCount = 0, kTimeScan = 1, kTimeScatter = 2, kTimeWork = 3, kTimeSlots = 4 };
+
+// ---------------------------------------------------------------------
+// Inline PTX: mbarrier and bulk asynchronous copy global -> shared.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dstSmem, const void *srcGlobal, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dstSmem)),
+        "l"(srcGlobal), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` to complete, for at most kSpinLimitCycles.
+// Returns false (and the caller must record a timeout) if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kSpinLimitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace rfi

@@ -1,0 +1,298 @@
+"""ctypes binding of librafi_gb.so (include/rafi.h).
+
+Argument marshalling only: every function has the C name, takes plain ints
+for device/host pointers (or objects with ``data_ptr()``, e.g. torch tensors)
+and a stream handle (int, or an object with ``cuda_stream``), and raises
+``RafiError`` for a status other than RF_OK unless the caller allows it.
+All computation happens in the CUDA library; when the library has not been
+built this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librafi_gb.so")
+
+RF_OK, RF_ERR_ARG, RF_ERR_OOM, RF_ERR_CUDA, RF_ERR_OVERFLOW, RF_ERR_BAD_DEST, RF_ERR_MAX_ROUNDS, \
+    RF_ERR_TIMEOUT, RF_ERR_STATE = range(9)
+STATUS_NAMES = ["RF_OK", "RF_ERR_ARG", "RF_ERR_OOM", "RF_ERR_CUDA", "RF_ERR_OVERFLOW", "RF_ERR_BAD_DEST",
+                "RF_ERR_MAX_ROUNDS", "RF_ERR_TIMEOUT", "RF_ERR_STATE"]
+RF_MAX_ITEM_BYTES = 512
+RF_MAX_RANKS = 1024
+RF_MAX_CAPACITY = 0x7FFFFFFF
+RF_C1_UNIFORM, RF_C1_ZIPF, RF_C1_NBR6 = 0, 1, 2
+
+
+class RafiError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{fn}: {name}: {msg}")
+
+
+class rf_device_queues(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("dest", ctypes.c_void_p),
+                ("outCount", ctypes.c_void_p), ("inOffset", ctypes.c_void_p), ("capacity", ctypes.c_uint64),
+                ("itemBytes", ctypes.c_uint32), ("numRanks", ctypes.c_int32)]
+
+
+class rf_round_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("numActive", "emitted", "dropped", "badDest", "holes",
+                                                "exchanges", "totalDelivered", "totalDropped")]
+
+
+class rf_phase_times(ctypes.Structure):
+    _fields_ = [("countMs", ctypes.c_double), ("scanMs", ctypes.c_double), ("scatterMs", ctypes.c_double),
+                ("workMs", ctypes.c_double), ("countLaunches", ctypes.c_uint64),
+                ("scanLaunches", ctypes.c_uint64), ("scatterLaunches", ctypes.c_uint64),
+                ("workLaunches", ctypes.c_uint64), ("scatterItems", ctypes.c_uint64),
+                ("scatterMsLarge", ctypes.c_double), ("scatterItemsLarge", ctypes.c_uint64),
+                ("scatterLaunchesLarge", ctypes.c_uint64)]
+
+
+_P = ctypes.c_void_p
+_i32, _u32, _u64, _f64 = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_PU64 = ctypes.POINTER(ctypes.c_uint64)
+
+# name -> argtypes (every function returns rf_status unless listed in _RESTYPE)
+_SIGS = {
+    "rf_create": [_i32, _u32, _u64, _PP],
+    "rf_destroy": [_P],
+    "rf_resize": [_P, _u64],
+    "rf_get_device_queues": [_P, ctypes.POINTER(rf_device_queues)],
+    "rf_exchange": [_P, _P, _PU64],
+    "rf_num_active": [_P, _PU64],
+    "rf_segment": [_P, _i32, _PU64, _PU64],
+    "rf_stats": [_P, ctypes.POINTER(rf_round_stats)],
+    "rf_push": [_P, _P, _P, _u64, _i32, _P],
+    "rf_snapshot": [_P, _P, _P, _P],
+    "rf_restore": [_P, _P, _P, _u64, _P],
+    "rf_set_timing": [_P, _i32],
+    "rf_get_timing": [_P, ctypes.POINTER(rf_phase_times), _i32],
+    "rf_launch_count": [],
+    "rf_last_error": [],
+    "rf_c1_zipf_thresholds": [_i32, _f64, _P],
+    "rf_c1_seed": [_P, _P, _u64, _P],
+    "rf_c1_work": [_P, _u32, _u32, _i32, _f64, _i32, _i32, _i32, _P, _P, _u64, _i32, _P],
+    "rf_c1_run": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _i32, _u32, _P,
+                  _PU64, _PU64],
+    "rf_c0_make_bricks": [_P, _i32, _i32, _P, _P],
+    "rf_c0_raygen": [_P, _P, _i32, _i32, _i32, _i32, _P, _P],
+    "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
+    "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
+}
+_RESTYPE = {"rf_launch_count": _u64, "rf_last_error": ctypes.c_char_p}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load librafi_gb.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = _RESTYPE.get(name, ctypes.c_int)
+            _lib = L
+    return _lib
+
+
+def ptr(x) -> int | None:
+    """Pointer value of an int, None, or an object with data_ptr() (torch tensor) / ctypes data."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy array
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)!r}")
+
+
+def stream_handle(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(fn: str, st: int, allow=()):
+    if st != RF_OK and st not in allow:
+        raise RafiError(st, fn, lib().rf_last_error().decode())
+    return st
+
+
+def rf_last_error() -> str:
+    return lib().rf_last_error().decode()
+
+
+def rf_launch_count() -> int:
+    return int(lib().rf_launch_count())
+
+
+def rf_create(num_ranks: int, item_bytes: int, capacity: int) -> int:
+    h = ctypes.c_void_p()
+    _check("rf_create", lib().rf_create(num_ranks, item_bytes, capacity, ctypes.byref(h)))
+    return h.value
+
+
+def rf_destroy(ctx: int) -> None:
+    _check("rf_destroy", lib().rf_destroy(ctx))
+
+
+def rf_resize(ctx: int, capacity: int) -> None:
+    _check("rf_resize", lib().rf_resize(ctx, capacity))
+
+
+def rf_get_device_queues(ctx: int) -> rf_device_queues:
+    q = rf_device_queues()
+    _check("rf_get_device_queues", lib().rf_get_device_queues(ctx, ctypes.byref(q)))
+    return q
+
+
+def rf_exchange(ctx: int, stream=None, sync: bool = True, allow=()):
+    """forwardRays(): returns (status, numActive) when sync, else (status, None)."""
+    n = ctypes.c_uint64()
+    st = lib().rf_exchange(ctx, stream_handle(stream), ctypes.byref(n) if sync else None)
+    _check("rf_exchange", st, allow)
+    return st, (n.value if sync else None)
+
+
+def rf_num_active(ctx: int, allow=()) -> int:
+    n = ctypes.c_uint64()
+    _check("rf_num_active", lib().rf_num_active(ctx, ctypes.byref(n)), allow)
+    return n.value
+
+
+def rf_segment(ctx: int, rank: int, allow=()):
+    o, c = ctypes.c_uint64(), ctypes.c_uint64()
+    _check("rf_segment", lib().rf_segment(ctx, rank, ctypes.byref(o), ctypes.byref(c)), allow)
+    return o.value, c.value
+
+
+def rf_stats(ctx: int, allow=()) -> rf_round_stats:
+    s = rf_round_stats()
+    _check("rf_stats", lib().rf_stats(ctx, ctypes.byref(s)), allow)
+    return s
+
+
+def rf_push(ctx: int, items, dest, n: int, host_memory: bool, stream=None) -> None:
+    _check("rf_push", lib().rf_push(ctx, ptr(items), ptr(dest), n, int(host_memory), stream_handle(stream)))
+
+
+def rf_snapshot(ctx: int, items_out, offsets_out, stream=None, allow=()) -> None:
+    _check("rf_snapshot", lib().rf_snapshot(ctx, ptr(items_out), ptr(offsets_out), stream_handle(stream)), allow)
+
+
+def rf_restore(ctx: int, items, offsets, n: int, stream=None) -> None:
+    _check("rf_restore", lib().rf_restore(ctx, ptr(items), ptr(offsets), n, stream_handle(stream)))
+
+
+def rf_set_timing(ctx: int, enable: bool) -> None:
+    _check("rf_set_timing", lib().rf_set_timing(ctx, int(enable)))
+
+
+def rf_get_timing(ctx: int, reset: bool = False, allow=()) -> rf_phase_times:
+    t = rf_phase_times()
+    _check("rf_get_timing", lib().rf_get_timing(ctx, ctypes.byref(t), int(reset)), allow)
+    return t
+
+
+def rf_c1_zipf_thresholds(num_ranks: int, s: float = 1.1):
+    arr = (ctypes.c_uint32 * max(num_ranks, 1))()
+    _check("rf_c1_zipf_thresholds", lib().rf_c1_zipf_thresholds(num_ranks, s, ctypes.cast(arr, _P)))
+    return list(arr)[: max(num_ranks - 1, 0)]
+
+
+def rf_c1_seed(ctx: int, items, n: int, stream=None) -> None:
+    _check("rf_c1_seed", lib().rf_c1_seed(ctx, ptr(items), n, stream_handle(stream)))
+
+
+def rf_c1_work(ctx: int, seed: int, hop: int, mode: int, zipf_s: float, grid, retired, retired_count,
+               retired_capacity: int, deterministic: bool = False, stream=None) -> None:
+    gx, gy, gz = grid
+    _check("rf_c1_work", lib().rf_c1_work(ctx, seed, hop, mode, zipf_s, gx, gy, gz, ptr(retired),
+                                          ptr(retired_count), retired_capacity, int(deterministic),
+                                          stream_handle(stream)))
+
+
+def rf_c1_run(ctx: int, items, n: int, seed: int, mode: int, zipf_s: float, grid, retired,
+              deterministic: bool = False, host_memory: bool = False, max_rounds: int = 100000,
+              stream=None, allow=()):
+    """Whole microbenchmark; returns (status, retired_count, rounds, forwarded)."""
+    gx, gy, gz = grid
+    cnt, rounds, fwd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib().rf_c1_run(ctx, ptr(items), n, seed, mode, zipf_s, gx, gy, gz, ptr(retired), ctypes.byref(cnt),
+                         int(deterministic), int(host_memory), max_rounds, stream_handle(stream),
+                         ctypes.byref(rounds), ctypes.byref(fwd))
+    _check("rf_c1_run", st, allow)
+    return st, cnt.value, rounds.value, fwd.value
+
+
+def rf_c0_make_bricks(volume, n: int, brick: int, bricks, stream=None) -> None:
+    _check("rf_c0_make_bricks", lib().rf_c0_make_bricks(ptr(volume), n, brick, ptr(bricks), stream_handle(stream)))
+
+
+def _cam(cam):
+    arr = (ctypes.c_float * 12)(*[float(x) for x in cam])
+    return arr
+
+
+def rf_c0_raygen(ctx: int, cam, n: int, brick: int, width: int, height: int, image, stream=None) -> None:
+    c = _cam(cam)
+    _check("rf_c0_raygen", lib().rf_c0_raygen(ctx, ctypes.cast(c, _P), n, brick, width, height, ptr(image),
+                                              stream_handle(stream)))
+
+
+def rf_c0_march(ctx: int, bricks, n: int, brick: int, image, hop_log=None, max_hops: int = 0,
+                hop_count=None, stream=None) -> None:
+    _check("rf_c0_march", lib().rf_c0_march(ctx, ptr(bricks), n, brick, ptr(image), ptr(hop_log), max_hops,
+                                            ptr(hop_count), stream_handle(stream)))
+
+
+def rf_c0_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, image, hop_log=None,
+                 max_hops: int = 0, hop_count=None, max_rounds: int = 64, stream=None) -> int:
+    c = _cam(cam)
+    rounds = ctypes.c_uint64()
+    _check("rf_c0_render", lib().rf_c0_render(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height,
+                                              ptr(image), ptr(hop_log), max_hops, ptr(hop_count), max_rounds,
+                                              stream_handle(stream), ctypes.byref(rounds)))
+    return rounds.value
+
+
+class Context:
+    """Owning handle of an rf_ctx (host context of Sec. 3.4)."""
+
+    def __init__(self, num_ranks: int, item_bytes: int, capacity: int):
+        self.handle = rf_create(num_ranks, item_bytes, capacity)
+        self.num_ranks, self.item_bytes, self.capacity = num_ranks, item_bytes, capacity
+
+    def close(self):
+        if self.handle:
+            rf_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

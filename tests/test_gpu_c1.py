@@ -1,0 +1,148 @@
+"""GPU parity: the forwarding microbenchmark against the oracle.
+
+Small runs compare the whole final payload multiset bit-exactly, the round
+count, the forward count and the per-round queues (bit-exact in the
+deterministic mode, whose queue order equals the oracle's; after a canonical
+sort per rank segment in the atomic-append mode).  The full-size run
+(2^24 x 64 B items over 64 ranks, as timed by bench.py) is checked on sampled
+items the oracle walks one by one, plus invariants that hold at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_30294_gb300 import inputs, rafi
+
+from gpu_util import canonical_rows, dev, stream, to_dev
+
+pytestmark = pytest.mark.gpu
+
+R = 64
+GRID = (4, 4, 4)
+MODES = [rafi.RF_C1_UNIFORM, rafi.RF_C1_ZIPF, rafi.RF_C1_NBR6]
+
+
+def _run(items, seed, mode, deterministic=False, host=False):
+    n = len(items)
+    s = stream()
+    with rafi.Context(R, 64, n) as ctx:
+        if host:
+            retired = np.zeros((n, 16), np.uint32)
+            st, cnt, rounds, fwd = rafi.rf_c1_run(ctx.handle, items.ctypes.data, n, seed, mode, 1.1, GRID,
+                                                  retired.ctypes.data, deterministic, True, stream=s)
+            return retired[:cnt], rounds, fwd
+        d_items = to_dev(items)
+        retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        st, cnt, rounds, fwd = rafi.rf_c1_run(ctx.handle, d_items, n, seed, mode, 1.1, GRID, retired,
+                                              deterministic, False, stream=s)
+        return retired[:cnt].cpu().numpy().view(np.uint32), rounds, fwd
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("deterministic", [False, True])
+def test_run_matches_oracle_multiset(mode, deterministic):
+    n, seed = 20011, 3
+    items = inputs.c1_items(n, seed=seed)
+    got, rounds, fwd = _run(items, seed, mode, deterministic)
+    final, hops, _, _ = oracle.c1_walk(items, R, seed, mode, grid=GRID)
+    assert len(got) == n
+    assert rounds == int(hops.max()) + 1
+    assert fwd == int(hops.sum())
+    np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
+
+
+def test_host_memory_run_matches_device_run():
+    n, seed = 10000, 4
+    items = inputs.c1_items(n, seed=seed)
+    a, ra, fa = _run(items, seed, rafi.RF_C1_ZIPF)
+    b, rb, fb = _run(items, seed, rafi.RF_C1_ZIPF, host=True)
+    assert (ra, fa) == (rb, fb)
+    np.testing.assert_array_equal(canonical_rows(a), canonical_rows(b))
+
+
+def _queue(ctx, n, s):
+    q = torch.zeros((max(n, 1), 16), dtype=torch.int32, device=dev())
+    off = torch.zeros(R + 1, dtype=torch.int32, device=dev())
+    rafi.rf_snapshot(ctx.handle, q, off, s)
+    torch.cuda.synchronize()
+    o = off.cpu().numpy().astype(np.int64)
+    return q.cpu().numpy().view(np.uint32)[: o[-1]], o
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("deterministic", [True, False])
+def test_round_queues_match_oracle(mode, deterministic):
+    n, seed, rounds_checked = 6000, 7, 5
+    items = inputs.c1_items(n, seed=seed)
+    s = stream()
+    with rafi.Context(R, 64, n) as ctx:
+        retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        rcount = torch.zeros(1, dtype=torch.int64, device=dev())
+        rafi.rf_c1_seed(ctx.handle, to_dev(items), n, s)
+        st, active = rafi.rf_exchange(ctx.handle, s)
+        for k in range(rounds_checked):
+            want = oracle.c1_rounds(items, R, seed, mode, grid=GRID, dump_round=k)
+            q, off = _queue(ctx, active, s)
+            np.testing.assert_array_equal(off.astype(np.uint64), want["dump_offsets"])
+            assert active == int(want["active"][k])
+            if deterministic:
+                np.testing.assert_array_equal(q, want["dump_items"])
+            else:
+                for r in range(R):
+                    np.testing.assert_array_equal(canonical_rows(q[off[r]:off[r + 1]]),
+                                                  canonical_rows(want["dump_items"][off[r]:off[r + 1]]))
+            before = int(rcount.item())
+            rafi.rf_c1_work(ctx.handle, seed, k, mode, 1.1, GRID, retired, rcount, n, deterministic, s)
+            st, nxt = rafi.rf_exchange(ctx.handle, s)
+            # conservation: active_k = retired_k + active_{k+1}
+            assert active == (int(rcount.item()) - before) + nxt
+            assert int(rcount.item()) - before == int(want["retired"][k])
+            stats = rafi.rf_stats(ctx.handle)
+            assert stats.holes == (active - nxt if deterministic else 0)
+            active = nxt
+
+
+def test_full_size_sampled_parity():
+    # the bench workload: 2^24 items x 64 B, 64 ranks, each destination law
+    n, seed = 1 << 24, 1
+    items = inputs.c1_items(n, seed=seed)
+    d_items = to_dev(items)
+    s = stream()
+    rng = np.random.default_rng(0)
+    sample = rng.choice(n, size=4096, replace=False)
+    key_in = (items[:, 0].astype(np.uint64) << np.uint64(32)) | items[:, 1].astype(np.uint64)
+    assert len(np.unique(key_in)) == n  # (w0, w1) identifies an item
+    with rafi.Context(R, 64, n) as ctx:
+        retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        for mode in MODES:
+            st, cnt, rounds, fwd = rafi.rf_c1_run(ctx.handle, d_items, n, seed, mode, 1.1, GRID, retired,
+                                                  stream=s)
+            got = retired.cpu().numpy().view(np.uint32)
+            assert cnt == n
+            key = (got[:, 0].astype(np.uint64) << np.uint64(32)) | got[:, 1].astype(np.uint64)
+            order = np.argsort(key)
+            # invariants at full size: words 0..12 are the input's, hop counts add up
+            np.testing.assert_array_equal(key[order], np.sort(key_in))
+            inv = np.argsort(key_in)
+            np.testing.assert_array_equal(got[order, :13], items[inv, :13])
+            assert int((got[order, 15] - items[inv, 15]).astype(np.int64).sum()) == fwd
+            assert 9 * n * 0.99 < fwd < 9 * n * 1.01
+            # sampled items walked one by one by the oracle, each from its own start rank
+            final, _, _, _ = oracle.c1_walk(items[sample], R, seed, mode, grid=GRID,
+                                            start_ranks=(sample % R).astype(np.int32))
+            pos = np.searchsorted(key[order], key_in[sample])
+            mism = int(np.sum(np.any(got[order[pos]] != final, axis=1)))
+            assert mism == 0
+
+
+def test_max_rounds_guard():
+    n, seed = 5000, 2
+    items = inputs.c1_items(n, seed=seed)
+    s = stream()
+    with rafi.Context(R, 64, n) as ctx:
+        retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        st, cnt, rounds, fwd = rafi.rf_c1_run(ctx.handle, to_dev(items), n, seed, rafi.RF_C1_UNIFORM, 1.1, GRID,
+                                              retired, max_rounds=3, stream=s,
+                                              allow=(rafi.RF_ERR_MAX_ROUNDS,))
+        assert st == rafi.RF_ERR_MAX_ROUNDS and rounds == 3 and cnt < n
