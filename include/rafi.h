@@ -165,6 +165,40 @@ uint64_t rf_launch_count(void);
 /* Message of the calling thread's most recent error ("" if none). */
 const char *rf_last_error(void);
 
+/* --- allocation-free partition ------------------------------------------ */
+
+/* Stable partition of n items by destination into caller buffers, without
+ * allocating anything.  The paper has no counterpart to this entry point.
+ *
+ * It exists for callers that must not allocate device memory once they are
+ * running: code that issues work while a CUDA graph is being captured (an
+ * allocation there is an error), latency-critical loops whose memory budget
+ * is fixed at start-up (an allocation can stall the whole device), and hosts
+ * whose own caching allocator already owns almost all device memory (a fresh
+ * allocation can fail while the host's pool still has room).
+ *
+ * Result: the same as rf_push + rf_exchange on a context: itemsOut (device,
+ * room for n items) receives the items grouped by destination, keeping their
+ * input order within a destination; offsetsOut (device, numRanks + 1 words)
+ * receives the segment offsets.  dest == -1 marks an empty slot (skipped);
+ * other destinations outside [0, numRanks) are dropped.  statsOut (device,
+ * 4 words, may be NULL) receives {delivered, empty slots, dropped, status}.
+ * items (n x itemBytes) and dest (n int32) are device memory.
+ *
+ * Scratch: one file-scope device array of 8 MiB, which every device that
+ * loads the library holds until the process exits.  numRanks x ceil(n /
+ * tile) x 4 bytes (tile = 256 items for 256-byte items, up to 4096 items for
+ * 16-byte items) must fit in 8 MiB - 4352 bytes; larger requests fail with
+ * RF_ERR_ARG and say so.  The scratch is cleared at the start of each call.
+ * Every call shares it: calls whose work may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The first call on a device looks up the array's device address and sets
+ * kernel attributes (no allocation); make that first call before any stream
+ * capture.  Asynchronous on stream; never calls cudaMalloc or cudaFree. */
+rf_status rf_partition_static(const void *items, const int32_t *dest, uint64_t n, uint32_t itemBytes,
+                              int32_t numRanks, void *itemsOut, uint32_t *offsetsOut,
+                              unsigned long long *statsOut, void *stream);
+
 /* --- forwarding microbenchmark (64-byte items) --------------------------- */
 
 /* Destination laws of the microbenchmark work kernel. */

@@ -505,3 +505,147 @@ extern "C" rf_status rf_exchange(rf_ctx *ctx, void *stream, uint64_t *numActiveO
     *numActiveOut = ctx->host->numActive;
     return st;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free stable partition (rf_partition_static).
+//
+// The same count / scan / scatter kernels as rf_exchange, run on caller
+// buffers, with their scratch (device state, per-destination totals, per-tile
+// histograms) in one file-scope device array instead of context allocations.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace rfi {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // 8 MiB, held by every device that loads the library
+constexpr size_t kStaticCountOff = 256;                   // after the device state
+constexpr size_t kStaticHistOff = kStaticCountOff + RF_MAX_RANKS * sizeof(uint32_t);
+static_assert(sizeof(DevState) <= kStaticCountOff, "device state fits its slot");
+static_assert(kStaticHistOff % 256 == 0, "histograms start aligned");
+
+static __device__ __align__(256) unsigned char g_partition_scratch[kStaticScratchBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_base[kStaticMaxDevices] = {};
+
+__global__ void __launch_bounds__(kBlock) static_init_kernel(DevState *s, uint32_t *count, int32_t R,
+                                                             unsigned long long n)
+{
+    for (int e = threadIdx.x; e < R; e += kBlock) count[e] = 0u;
+    if (threadIdx.x == 0) {
+        s->outCount = n;
+        s->bad = 0ull;
+        s->holes = 0ull;
+        s->numActive = 0ull;
+        s->status = 0u;
+    }
+}
+
+__global__ void static_finish_kernel(const DevState *s, unsigned long long *stats)
+{
+    if (threadIdx.x == 0 && stats) {
+        stats[0] = s->numActive;
+        stats[1] = s->holes;
+        stats[2] = s->bad;
+        stats[3] = s->status;
+    }
+}
+
+// Once per device, with that device current: the device address of the
+// scratch array, and the shared-memory limit of every scatter variant.
+rf_status static_setup(int dev, unsigned char **base)
+{
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_base[dev]) {
+        void *p = nullptr;
+        RF_CUDA(cudaGetSymbolAddress(&p, g_partition_scratch));
+        int optin = 0;
+        RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        const ExKernel variants[] = {scatter_kernel<1, 16>, scatter_kernel<2, 8>, scatter_kernel<3, 4>,
+                                     scatter_kernel<4, 4>,  scatter_kernel<8, 2>, scatter_kernel<0, 4>,
+                                     scatter_kernel<0, 2>,  scatter_kernel<0, 1>};
+        for (ExKernel f : variants)
+            RF_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        g_static_base[dev] = p;
+    }
+    *base = static_cast<unsigned char *>(g_static_base[dev]);
+    return RF_OK;
+}
+
+}  // namespace
+}  // namespace rfi
+
+extern "C" rf_status rf_partition_static(const void *items, const int32_t *dest, uint64_t n, uint32_t itemBytes,
+                                         int32_t numRanks, void *itemsOut, uint32_t *offsetsOut,
+                                         unsigned long long *statsOut, void *stream)
+{
+    using namespace rfi;
+    if (numRanks < 1 || numRanks > RF_MAX_RANKS || itemBytes == 0 || itemBytes % 16 ||
+        itemBytes > RF_MAX_ITEM_BYTES || n > RF_MAX_CAPACITY || !offsetsOut || (n && (!items || !dest || !itemsOut))) {
+        set_error("rf_partition_static: bad arguments (numRanks 1..%d, itemBytes a multiple of 16 up to %u, "
+                  "n below 2^31, non-NULL buffers)", RF_MAX_RANKS, RF_MAX_ITEM_BYTES);
+        return RF_ERR_ARG;
+    }
+    const ScatterChoice c = pick_scatter(itemBytes);
+    const uint32_t tileItems = 256u * c.k;
+    const uint64_t tiles = (n + tileItems - 1) / tileItems;
+    const uint64_t maxTiles = tiles < 4 ? 4 : (tiles + 3) / 4 * 4;
+    const uint64_t histBytes = (uint64_t)numRanks * maxTiles * sizeof(uint32_t);
+    if (kStaticHistOff + histBytes > kStaticScratchBytes) {
+        set_error("rf_partition_static: %llu items over %d ranks need %llu bytes of scratch; the static "
+                  "scratch holds %zu (numRanks x ceil(n / %u) x 4 bytes must stay below %zu)",
+                  (unsigned long long)n, numRanks, (unsigned long long)(kStaticHistOff + histBytes),
+                  kStaticScratchBytes, tileItems, kStaticScratchBytes - kStaticHistOff);
+        return RF_ERR_ARG;
+    }
+    int dev = 0;
+    RF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) {
+        set_error("rf_partition_static: device %d beyond the %d supported", dev, kStaticMaxDevices);
+        return RF_ERR_ARG;
+    }
+    unsigned char *base = nullptr;
+    if (rf_status st = static_setup(dev, &base)) return st;
+
+    const size_t smem = scatter_layout(tileItems, itemBytes, numRanks).total;
+    int numSMs = 0, perSM = 0, cperSM = 0;
+    RF_CUDA(cudaDeviceGetAttribute(&numSMs, cudaDevAttrMultiProcessorCount, dev));
+    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, c.fn, kBlock, smem));
+    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cperSM, count_kernel, kBlock,
+                                                          (size_t)numRanks * sizeof(uint32_t)));
+    if (perSM < 1) {
+        set_error("rf_partition_static: scatter tile does not fit on an SM (%zu bytes of shared memory)", smem);
+        return RF_ERR_ARG;
+    }
+    ExArgs a;
+    a.out = items;
+    a.dest = dest;
+    a.in = itemsOut;
+    a.inOffset = offsetsOut;
+    a.count = reinterpret_cast<uint32_t *>(base + kStaticCountOff);
+    a.tileHist = reinterpret_cast<uint32_t *>(base + kStaticHistOff);
+    a.state = reinterpret_cast<DevState *>(base);
+    a.capacity = n;
+    a.tileItems = tileItems;
+    a.maxTiles = (uint32_t)maxTiles;
+    a.itemBytes = itemBytes;
+    a.numRanks = numRanks;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int mt = (int)maxTiles;
+    const int cb = numSMs * (cperSM < 1 ? 1 : cperSM);
+    const int sb = numSMs * perSM;
+    static_init_kernel<<<1, kBlock, 0, s>>>(a.state, a.count, numRanks, n);
+    RF_LAUNCHED("static_init_kernel");
+    count_kernel<<<cb < mt ? cb : mt, kBlock, (size_t)numRanks * sizeof(uint32_t), s>>>(a);
+    RF_LAUNCHED("count_kernel");
+    scan_kernel<<<numRanks, kBlock, 0, s>>>(a);
+    RF_LAUNCHED("scan_kernel");
+    c.fn<<<sb < mt ? sb : mt, kBlock, smem, s>>>(a);
+    RF_LAUNCHED("scatter_kernel");
+    static_finish_kernel<<<1, 32, 0, s>>>(a.state, statsOut);
+    RF_LAUNCHED("static_finish_kernel");
+    return RF_OK;
+}

@@ -75,6 +75,7 @@ _SIGS = {
     "rf_get_timing": [_P, ctypes.POINTER(rf_phase_times), _i32],
     "rf_launch_count": [],
     "rf_last_error": [],
+    "rf_partition_static": [_P, _P, _u64, _u32, _i32, _P, _P, _P, _P],
     "rf_c1_zipf_thresholds": [_i32, _f64, _P],
     "rf_c1_seed": [_P, _P, _u64, _P],
     "rf_c1_work": [_P, _u32, _u32, _i32, _f64, _i32, _i32, _i32, _P, _P, _u64, _i32, _P],
@@ -209,6 +210,14 @@ def rf_get_timing(ctx: int, reset: bool = False, allow=()) -> rf_phase_times:
     t = rf_phase_times()
     _check("rf_get_timing", lib().rf_get_timing(ctx, ctypes.byref(t), int(reset)), allow)
     return t
+
+
+def rf_partition_static(items, dest, n: int, item_bytes: int, num_ranks: int, items_out, offsets_out,
+                        stats_out=None, stream=None) -> None:
+    """Allocation-free stable partition into caller buffers (see rafi.h)."""
+    _check("rf_partition_static", lib().rf_partition_static(ptr(items), ptr(dest), n, item_bytes, num_ranks,
+                                                            ptr(items_out), ptr(offsets_out), ptr(stats_out),
+                                                            stream_handle(stream)))
 
 
 def rf_c1_zipf_thresholds(num_ranks: int, s: float = 1.1):
