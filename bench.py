@@ -5,13 +5,16 @@ One step = the forwarding microbenchmark run to termination three times
 64-byte items over 64 logical ranks, seed, exchange, then {work; exchange}
 rounds until no item is active.  ``value`` counts items delivered by the
 exchanges of work rounds (the seed exchange is timed but not counted) per
-second of device time; inputs are resident in HBM before timing, and the
-1 GiB queues are larger than L2.
+second of device time, for the batched form (all rounds of a run in one
+persistent kernel, rf_c1_run_batched); inputs are resident in HBM before
+timing, and the 1 GiB queues are larger than L2.
 
-Also reported on the same line: the scatter kernel's roofline (algorithmic
-bytes 2 x 64 B per delivered item over its CUDA-event time), the same run end
-to end through rf_c1_run with host buffers, rays/s of the 64^3 marching
-workload, the oracle timed on a bounded sample (cpu_baseline), SM clocks
+Also reported on the same line: the persistent kernel's roofline
+(algorithmic bytes over its CUDA-event time) and its per-round work and
+scatter phase rates from its round log; the plain per-round host loop
+(rf_c1_run) with the scatter kernel's roofline; the same run end to end
+through rf_c1_run_batched with host buffers; rays/s of the 64^3 marching
+workload; the oracle timed on a bounded sample (cpu_baseline); SM clocks
 sampled during the timed region and the number of kernels launched.
 
 ``--impl reference`` times the oracle (the CPU reference of this method) on a
@@ -177,22 +180,6 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the GPU path
 # ---------------------------------------------------------------------------
-def traffic_for_scatter():
-    """DRAM bytes per scatter launch from a committed ncu summary, if it matches the current kernel."""
-    import hashlib
-
-    p = os.path.join(ROOT, "profiles", "scatter_traffic.json")
-    src = os.path.join(ROOT, "paper_2605_30294_gb300", "csrc", "exchange.cu")
-    if not os.path.exists(p):
-        return None
-    with open(p) as f:
-        d = json.load(f)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("exchange_cu_sha256") != h:
-        return None
-    return d.get("bytes_per_full_size_launch")
-
-
 def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
     n, w, h, brick = 64, 128, 128, 32
     vol = inputs.c0_volume(n)
@@ -213,6 +200,27 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
     return w * h / (ms * 1e-3), ms
+
+
+LOG_CAP = 4096  # rounds logged by the persistent kernel
+
+
+def phase_rates(log_rows, item_bytes, min_items=1 << 20):
+    """Per-round GB/s of the work and scatter phases from the persistent kernel's round log."""
+    lg = np.asarray(log_rows, dtype=np.float64)
+    big = lg[:, 4] >= min_items
+    work_b = lg[:, 4] * 2 * item_bytes
+    scat_b = lg[:, 5] * 2 * item_bytes
+    work_t = (lg[:, 1] - lg[:, 0]) * 1e-9
+    scat_t = (lg[:, 3] - lg[:, 2]) * 1e-9
+    out = {"rounds": int(len(lg)), "rounds_ge_2^20": int(big.sum())}
+    if big.any():
+        out["work_gbs_ge_2^20"] = float(work_b[big].sum() / work_t[big].sum() / 1e9)
+        out["scatter_gbs_ge_2^20"] = float(scat_b[big].sum() / scat_t[big].sum() / 1e9)
+        per_round = scat_b[big] / scat_t[big] / 1e9
+        out["scatter_gbs_ge_2^20_min_round"] = float(per_round.min())
+    out["round_ms_total"] = float((lg[-1, 3] - lg[0, 0]) * 1e-6) if len(lg) else 0.0
+    return out
 
 
 def run_ours(args):
@@ -240,41 +248,61 @@ def run_ours(args):
     items = inputs.c1_items(n, seed=SEED)
     d_items = torch.from_numpy(items.view(np.int32)).to(dev)
     retired = torch.zeros((n, 16), dtype=torch.int32, device=dev)
+    log = torch.zeros(6 * LOG_CAP, dtype=torch.int64, device=dev)
     s = torch.cuda.current_stream(dev)
     ctx = rafi.Context(RANKS, ITEM_BYTES, n)
 
-    def step():
+    def step(batched, round_log=None):
         fwd = 0
         for mode in MODES:
-            st, cnt, rounds, f = rafi.rf_c1_run(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired, stream=s)
+            if batched:
+                st, cnt, rounds, f = rafi.rf_c1_run_batched(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired,
+                                                            stream=s, round_log=round_log,
+                                                            round_log_cap=LOG_CAP if round_log is not None else 0)
+            else:
+                st, cnt, rounds, f = rafi.rf_c1_run(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired,
+                                                    stream=s)
             if cnt != n:
                 raise RuntimeError(f"mode {mode}: {cnt} of {n} items retired")
             fwd += f
         return fwd
 
-    for _ in range(args.warmup):
-        step()
+    def timed(batched, steps):
+        rafi.rf_set_timing(ctx.handle, True)
+        rafi.rf_get_timing(ctx.handle, reset=True)
+        barrier()
+        launches0 = rafi.rf_launch_count()
+        with ClockSampler(gpu_id) as clocks:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fwd = 0
+            for _ in range(steps):
+                fwd += step(batched)
+            e1.record(s)
+            barrier()
+        launches = rafi.rf_launch_count() - launches0
+        t = rafi.rf_get_timing(ctx.handle, reset=True)
+        rafi.rf_set_timing(ctx.handle, False)
+        return fwd, e0.elapsed_time(e1), t, launches, clocks.summary()
+
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
     uuid = getattr(props, "uuid", None)
     if uuid is not None:
-        gpu_id = "GPU-" + str(uuid) if not str(uuid).startswith("GPU-") else str(uuid)
-    rafi.rf_set_timing(ctx.handle, True)
-    rafi.rf_get_timing(ctx.handle, reset=True)
-    barrier()
-    launches0 = rafi.rf_launch_count()
-    with ClockSampler(gpu_id) as clocks:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        fwd = 0
-        for _ in range(args.steps):
-            fwd += step()
-        e1.record(s)
-        barrier()
-    launches = rafi.rf_launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    t = rafi.rf_get_timing(ctx.handle, reset=True)
-    rafi.rf_set_timing(ctx.handle, False)
+        gpu_id = str(uuid) if str(uuid).startswith("GPU-") else "GPU-" + str(uuid)
+
+    for _ in range(args.warmup):
+        step(True)
+        step(False)
+    fwd, ms, tb, launches, clocks = timed(True, args.steps)
+    p_steps = max(3, args.steps // 4)
+    p_fwd, p_ms, tp, p_launches, p_clocks = timed(False, p_steps)
+
+    # per-round phase rates of the persistent kernel (one extra, untimed step)
+    step(True, round_log=log)
+    lg = log.cpu().numpy().reshape(-1, 6)
+    rows = [r for r in lg if r[0] > 0]
+    rates = phase_rates(rows, ITEM_BYTES)
 
     # end to end through the public call with host buffers (H2D + D2H inside)
     h_items = torch.from_numpy(items.view(np.int32)).pin_memory()
@@ -283,8 +311,8 @@ def run_ours(args):
     def e2e_step():
         f = 0
         for mode in MODES:
-            st, cnt, rounds, ff = rafi.rf_c1_run(ctx.handle, h_items.data_ptr(), n, SEED, mode, 1.1, GRID,
-                                                 h_ret.data_ptr(), host_memory=True, stream=s)
+            st, cnt, rounds, ff = rafi.rf_c1_run_batched(ctx.handle, h_items.data_ptr(), n, SEED, mode, 1.1, GRID,
+                                                         h_ret.data_ptr(), host_memory=True, stream=s)
             f += ff
         return f
 
@@ -301,7 +329,6 @@ def run_ours(args):
     rays_s, c0_ms = c0_rays_per_s(torch, rafi, inputs, s)
     ctx.close()
 
-    # max over ranks of the timed region
     sec = ms / 1e3
     total_fwd = fwd
     if pg:
@@ -313,29 +340,44 @@ def run_ours(args):
         sec, e2e_s = float(mx[0]), float(mx[2])
         total_fwd, e2e_fwd = int(sm[1]), int(sm[3])
     if rank != 0:
+        if pg:
+            pg.destroy_process_group()
         return 0
 
     peak, peak_kind = peaks()
-    bytes_alg = t.scatterItems * 2 * ITEM_BYTES
-    achieved = bytes_alg / (t.scatterMs * 1e-3) / 1e9 if t.scatterMs > 0 else 0.0
-    achieved_large = (t.scatterItemsLarge * 2 * ITEM_BYTES / (t.scatterMsLarge * 1e-3) / 1e9
-                      if t.scatterMsLarge > 0 else 0.0)
-    traffic = traffic_for_scatter()
+    # persistent kernel: 2 x 64 B per item through the work phase (all items of every
+    # round) plus 2 x 64 B per item through the scatter phase (items delivered)
+    runs = tb.roundsLaunches
+    alg_bytes = 2 * ITEM_BYTES * (runs * n + 2 * fwd)
+    achieved = alg_bytes / (tb.roundsMs * 1e-3) / 1e9 if tb.roundsMs > 0 else 0.0
+    p_bytes = tp.scatterItems * 2 * ITEM_BYTES
+    p_ach = p_bytes / (tp.scatterMs * 1e-3) / 1e9 if tp.scatterMs > 0 else 0.0
+    p_ach_l = (tp.scatterItemsLarge * 2 * ITEM_BYTES / (tp.scatterMsLarge * 1e-3) / 1e9
+               if tp.scatterMsLarge > 0 else 0.0)
     cpu_v, cpu_fwd, cpu_dt = oracle_baseline()
     line = {
         "metric": METRIC, "value": total_fwd / sec, "unit": "items/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "items": n, "item_bytes": ITEM_BYTES, "ranks": RANKS,
+                   "form": "batched: all rounds in one persistent cooperative kernel per run",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "no flush: the 1 GiB item queues exceed the 129 MB L2"},
-        "roofline": {"bound": "hbm", "kernel": "scatter_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": peak_kind,
-                     "achieved_rounds_ge_2^20": achieved_large, "frac_rounds_ge_2^20": achieved_large / peak,
-                     "launches": t.scatterLaunches, "launches_ge_2^20": t.scatterLaunchesLarge,
-                     "ms_total": t.scatterMs},
-        "phase_ms": {"work": t.workMs, "count": t.countMs, "scan": t.scanMs, "scatter": t.scatterMs},
+        "roofline": {"bound": "hbm", "kernel": "rounds_kernel<C1Work>", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes / max(runs, 1), "launches": runs,
+                     "ms_total": tb.roundsMs},
+        "phases_from_round_log": {**rates,
+                                  "scatter_frac_ge_2^20": rates.get("scatter_gbs_ge_2^20", 0.0) / peak,
+                                  "work_frac_ge_2^20": rates.get("work_gbs_ge_2^20", 0.0) / peak},
+        "plain": {"value": p_fwd / (p_ms / 1e3), "ms_per_step": p_ms / p_steps, "steps": p_steps,
+                  "form": "host loop: work kernel + count/scan/scatter/wrap-up kernels + one sync per round",
+                  "roofline_scatter": {"achieved": p_ach, "frac": p_ach / peak,
+                                       "achieved_rounds_ge_2^20": p_ach_l, "frac_rounds_ge_2^20": p_ach_l / peak,
+                                       "launches": tp.scatterLaunches},
+                  "phase_ms": {"work": tp.workMs, "count": tp.countMs, "scan": tp.scanMs,
+                               "scatter": tp.scatterMs},
+                  "gpu_launches": p_launches, "clocks": p_clocks},
         "e2e": {"value": e2e_fwd / e2e_s, "unit": "items/s",
                 "h2d_bytes_per_step": len(MODES) * n * ITEM_BYTES,
                 "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8)},
@@ -344,7 +386,7 @@ def run_ours(args):
         "cpu_baseline": {"value": cpu_v, "unit": "items/s", "cores": 1, "kind": "oracle",
                          "sample": f"{BASELINE_ITEMS} items per destination law, round-by-round oracle, "
                                    f"{cpu_dt:.1f} s"},
-        "clocks": clocks.summary(),
+        "clocks": clocks,
         "gpu_launches": launches,
     }
     print(json.dumps(line), flush=True)

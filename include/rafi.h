@@ -96,6 +96,8 @@ typedef struct rf_phase_times {
     double scatterMsLarge;      /* the same, restricted to exchanges of >= 2^20 items */
     uint64_t scatterItemsLarge;
     uint64_t scatterLaunchesLarge;
+    double roundsMs;            /* persistent round kernels (batched form) */
+    uint64_t roundsLaunches;
 } rf_phase_times;
 
 /* --- host context (Sec. 3.4) ------------------------------------------- */
@@ -245,6 +247,23 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
                     int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,
                     int32_t deterministic, int32_t hostMemory, uint32_t maxRounds, void *stream,
                     uint64_t *rounds, uint64_t *forwarded);
+
+/* Batched form of rf_c1_run: the seed and its exchange as in rf_c1_run, then
+ * every work round and exchange inside one persistent cooperative kernel
+ * (phase 1: work step written back to the same queue slots, destination -1
+ * for a retired item; bounded grid barrier; destination offsets and the next
+ * active count; phase 3: stable scatter; bounded grid barrier), so no round
+ * needs the host.  Queue order is deterministic: round k's incoming queue is
+ * the one of rf_c1_run with deterministic != 0.  roundLog (device, 6 x
+ * roundLogCap words, nullable) receives per round, as seen by CTA 0, the
+ * %globaltimer ns at round start, end of the work phase, after the first
+ * barrier and at the end of the scatter phase, then the incoming and the
+ * delivered item counts.  RF_ERR_TIMEOUT if a bounded wait gave up.
+ * Other arguments and results as rf_c1_run. */
+rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
+                            int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,
+                            int32_t hostMemory, uint32_t maxRounds, void *stream, uint64_t *rounds,
+                            uint64_t *forwarded, unsigned long long *roundLog, uint32_t roundLogCap);
 
 /* --- absorption marching through bricks (48-byte rays) ------------------- */
 

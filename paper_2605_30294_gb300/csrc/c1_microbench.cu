@@ -16,6 +16,7 @@
 
 #include "internal.cuh"
 #include "rafi_device.cuh"
+#include "rounds.cuh"
 
 namespace rfi {
 
@@ -155,6 +156,47 @@ __global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
         }
     }
 }
+
+// The hop rule as a workload policy of the persistent round kernel
+// (rounds.cuh): same arithmetic as work_kernel, one item at a time.
+struct C1Work {
+    static constexpr int V = 4;
+    static constexpr bool kAppendRetired = true;
+    const uint32_t *zipfThr;
+    uint4 *retired;
+    unsigned long long *retiredCount;
+    unsigned long long retiredCap;
+    uint32_t seed;
+    int32_t mode, gx, gy, gz, R;
+
+    __host__ __device__ uint32_t smemBytes() const { return (uint32_t)RF_MAX_RANKS * 4u; }
+    __device__ void load_smem(void *s) const
+    {
+        uint32_t *t = static_cast<uint32_t *>(s);
+        if (mode == RF_C1_ZIPF)
+            for (int e = threadIdx.x; e < R - 1; e += blockDim.x) t[e] = zipfThr[e];
+    }
+    __device__ int32_t step(uint4 (&w)[4], int32_t rank, uint32_t round, const void *s) const
+    {
+        const uint4 r = philox4x32_10(make_uint4(w[0].x, w[0].y, w[3].w, round), make_uint2(seed, 1u));
+        if (r.x < kRetire) return -1;
+        const int32_t d = choose_dest(mode, rank, r.y, R, static_cast<const uint32_t *>(s), gx, gy, gz);
+        w[3].z = (uint32_t)d;
+        w[3].y ^= r.z;
+        w[3].w += 1u;
+        return d;
+    }
+    __device__ unsigned long long *retiredCounter() const { return retiredCount; }
+    __device__ void retire(const uint4 (&w)[4], unsigned long long slot) const
+    {
+        if (slot >= retiredCap) return;
+        uint4 *o = retired + (size_t)slot * 4;
+        o[0] = w[0];
+        o[1] = w[1];
+        o[2] = w[2];
+        o[3] = w[3];
+    }
+};
 
 // Seed: emit item i to rank i mod R at out slot base + i, where base was
 // reserved on the append counter by reserve_kernel.
@@ -362,3 +404,72 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
 }
 
 }  // extern "C"
+
+extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode,
+                                       double zipfS, int32_t gx, int32_t gy, int32_t gz, void *retired,
+                                       uint64_t *retiredCountOut, int32_t hostMemory, uint32_t maxRounds,
+                                       void *stream, uint64_t *rounds, uint64_t *forwarded,
+                                       unsigned long long *roundLog, uint32_t roundLogCap)
+{
+    using namespace rfi;
+    if (rf_status st = check_c1(ctx, "rf_c1_run_batched")) return st;
+    if (n > ctx->capacity || (n && (!items || !retired)) || !retiredCountOut ||
+        mode < RF_C1_UNIFORM || mode > RF_C1_NBR6) {
+        set_error("rf_c1_run_batched: n %llu above capacity, NULL buffer or bad mode", (unsigned long long)n);
+        return RF_ERR_ARG;
+    }
+    if (mode == RF_C1_NBR6 && (gx < 1 || gy < 1 || gz < 1 || gx * gy * gz != ctx->numRanks)) {
+        set_error("rf_c1_run_batched: torus %dx%dx%d does not have %d ranks", gx, gy, gz, ctx->numRanks);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (mode == RF_C1_ZIPF)
+        if (rf_status st = ensure_zipf(ctx, zipfS)) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *devRetired = retired;
+    if (hostMemory) {
+        if (rf_status st = ensure_staging(ctx)) return st;
+        devRetired = ctx->staging;
+    }
+    RF_CUDA(cudaMemsetAsync(ctx->stagingCount, 0, sizeof(unsigned long long), s));
+    rf_device_queues q;
+    rf_get_device_queues(ctx, &q);
+    if (hostMemory) {
+        if (n) RF_CUDA(cudaMemcpyAsync(q.out, items, (size_t)n * 64u, cudaMemcpyHostToDevice, s));
+        seed_dest_kernel<<<grid_for(ctx, n, 8), kBlock, 0, s>>>((uint32_t)n, q);
+        RF_LAUNCHED("seed_dest_kernel");
+    } else {
+        if (rf_status st = rf_c1_seed(ctx, items, n, stream)) return st;
+    }
+    // the seed exchange runs asynchronously; the persistent kernel starts from its result
+    if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
+
+    C1Work w;
+    w.zipfThr = ctx->zipfThr;
+    w.retired = static_cast<uint4 *>(devRetired);
+    w.retiredCount = ctx->stagingCount;
+    w.retiredCap = n;
+    w.seed = seed;
+    w.mode = mode;
+    w.gx = gx;
+    w.gy = gy;
+    w.gz = gz;
+    w.R = ctx->numRanks;
+    unsigned long long res[4];
+    rf_status st = launch_rounds(ctx, w, maxRounds, s, roundLog, roundLogCap, res);
+    if (st != RF_OK) return st;
+    unsigned long long cnt = 0;
+    RF_CUDA(cudaMemcpy(&cnt, ctx->stagingCount, sizeof cnt, cudaMemcpyDeviceToHost));
+    if (hostMemory && cnt)
+        RF_CUDA(cudaMemcpyAsync(retired, ctx->staging, (size_t)(cnt < n ? cnt : n) * 64u, cudaMemcpyDeviceToHost, s));
+    RF_CUDA(cudaStreamSynchronize(s));
+    *retiredCountOut = cnt;
+    if (rounds) *rounds = res[0];
+    if (forwarded) *forwarded = res[1];
+    if (ctx->host->numActive) {
+        set_error("rf_c1_run_batched: %llu items still active after %u rounds",
+                  (unsigned long long)ctx->host->numActive, maxRounds);
+        return RF_ERR_MAX_ROUNDS;
+    }
+    return RF_OK;
+}

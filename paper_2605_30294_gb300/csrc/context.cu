@@ -56,6 +56,7 @@ void time_end(rf_ctx *ctx, int slot, cudaStream_t s)
     case kTimeScan: ctx->times.scanLaunches++; break;
     case kTimeScatter: ctx->times.scatterLaunches++; break;
     case kTimeWork: ctx->times.workLaunches++; break;
+    case kTimeRounds: ctx->times.roundsLaunches++; break;
     default: break;
     }
     ctx->pendingSlots |= 1u << slot;
@@ -81,6 +82,7 @@ void time_collect(rf_ctx *ctx)
             }
             break;
         case kTimeWork: ctx->times.workMs += ms; break;
+        case kTimeRounds: ctx->times.roundsMs += ms; break;
         default: break;
         }
     }
@@ -155,6 +157,18 @@ rf_status check_ctx(rf_ctx *ctx, const char *fn)
 }
 
 }  // namespace
+
+rf_status ensure_rounds_scratch(rf_ctx *ctx, size_t bytes)
+{
+    if (ctx->roundsScratch && ctx->roundsScratchBytes >= bytes) return RF_OK;
+    cudaFree(ctx->roundsScratch);
+    ctx->roundsScratch = nullptr;
+    ctx->roundsScratchBytes = 0;
+    RF_CUDA(cudaMalloc(&ctx->roundsScratch, bytes));
+    RF_CUDA(cudaMemset(ctx->roundsScratch, 0, bytes));
+    ctx->roundsScratchBytes = bytes;
+    return RF_OK;
+}
 
 rf_status ensure_staging(rf_ctx *ctx)
 {
@@ -243,6 +257,7 @@ rf_status rf_destroy(rf_ctx *ctx)
     cudaFree(ctx->dev);
     cudaFree(ctx->stagingCount);
     cudaFree(ctx->zipfThr);
+    cudaFree(ctx->roundsScratch);
     if (ctx->host) cudaFreeHost(ctx->host);
     for (int i = 0; i < 2 * kTimeSlots; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);

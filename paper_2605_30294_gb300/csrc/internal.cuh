@@ -62,6 +62,9 @@ struct rf_ctx {
     cudaStream_t lastStream = nullptr;
     bool pending = false;  // an exchange's read-back has not been waited for
 
+    void *roundsScratch = nullptr;  // lazily allocated scratch of the persistent round kernel
+    size_t roundsScratchBytes = 0;
+
     uint32_t *zipfThr = nullptr;  // numRanks words: Zipf table of the microbenchmark
     double zipfS = -1.0;           // exponent the table was built for
 
@@ -117,12 +120,15 @@ rf_status launch_exchange(rf_ctx *ctx, cudaStream_t s);
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);
 
+// Allocate (or grow) ctx->roundsScratch to at least `bytes` (zeroed).
+rf_status ensure_rounds_scratch(rf_ctx *ctx, size_t bytes);
+
 // Per-phase timing helpers (no-ops unless ctx->timing).
 void time_begin(rf_ctx *ctx, int slot, cudaStream_t s);
 void time_end(rf_ctx *ctx, int slot, cudaStream_t s);
 void time_collect(rf_ctx *ctx);  // after a stream sync: accumulate recorded pairs
 
-enum TimeSlot { kTimeCount = 0, kTimeScan = 1, kTimeScatter = 2, kTimeWork = 3, kTimeSlots = 4 };
+enum TimeSlot { kTimeCount = 0, kTimeScan = 1, kTimeScatter = 2, kTimeWork = 3, kTimeRounds = 4, kTimeSlots = 5 };
 
 // ---------------------------------------------------------------------
 // Inline PTX: mbarrier and bulk asynchronous copy global -> shared.

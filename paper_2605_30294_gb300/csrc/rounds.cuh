@@ -1,0 +1,543 @@
+// Batched form of the forwarding loop: every round of "work, then exchange"
+// in one persistent cooperative kernel, with no host round trip per round.
+//
+// The plain loop (Sec. 5.1's "alternate between the render kernel and
+// forwardRays until no ray is left") launches a work kernel and the exchange
+// kernels per round and reads the active count back on the host.  Here all
+// CTAs of one cooperative launch stay resident and run the rounds
+// themselves:
+//
+//   phase 1  each CTA takes a contiguous range of the incoming queue, stages
+//            it tile by tile with a bulk async copy, applies the workload's
+//            step to every item and writes the tile back to the same slots of
+//            the out-queue with one bulk store (destination -1 for an item
+//            that retired: the paper's first single-array queue, Sec. 3.2),
+//            counting destinations per CTA;
+//   barrier  (bounded spin)
+//   phase 2  per-destination totals -> segment offsets (Sec. 4.2.2) and the
+//            next active count (Sec. 4.2.3); each CTA's base per destination =
+//            segment offset + the counts of the CTAs before it;
+//   phase 3  each CTA re-reads its range of the out-queue and scatters it,
+//            stably and grouped by destination, into the incoming queue;
+//   barrier  then the next round, until no item is active.
+//
+// Because the out slot of an item is its input slot and every step is
+// stable, queue order never depends on scheduling: round k's incoming queue
+// equals the one of a serial round-by-round simulation.
+//
+// Every wait is bounded; a wait that gives up raises an abort flag that all
+// CTAs check at the next barrier, and the kernel returns with a timeout status.
+#pragma once
+
+#include "internal.cuh"
+#include "rafi_device.cuh"
+
+namespace rfi {
+
+struct GridSync {
+    unsigned int count;  // CTAs arrived at the current barrier
+    unsigned int gen;    // barrier generation
+    unsigned int abort;  // set by a CTA whose wait gave up
+    unsigned int pad;
+};
+
+struct RoundsArgs {
+    uint4 *in;
+    uint4 *out;
+    int32_t *dest;
+    uint32_t *inOffset;        // numRanks + 1
+    uint32_t *tot;             // gridDim.x x numRanks: per-CTA destination counts of a round
+    unsigned int *total;       // 2 x numRanks: per-destination totals (round parity)
+    GridSync *sync;
+    unsigned long long *result;  // {rounds, forwarded, status, spare}
+    unsigned long long *numActiveOut;  // items still active when the kernel returns
+    unsigned long long *roundLog;  // nullable: per round {t_start, t_work_end, t_barrier, t_scatter_end, n_in, n_next}
+    uint32_t maxRounds;
+    uint32_t roundLogCap;
+    int32_t numRanks;
+};
+
+constexpr int kRoundsBlock = 256;
+constexpr int kRoundsWarps = kRoundsBlock / 32;
+constexpr int kRoundsK = 4;  // items per thread per tile
+constexpr uint32_t kRoundsTile = kRoundsBlock * kRoundsK;
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void bulk_s2g(void *dstGlobal, const void *srcSmem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dstGlobal),
+                 "r"(smem_u32(srcSmem)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Orders this thread's generic-proxy global accesses with async-proxy
+// (bulk copy) accesses to global memory, in either direction.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Lanes of the warp holding the same key (keys in [0, 2^nbits)): one ballot
+// per key bit, the ballot form of __match_any_sync.
+__device__ __forceinline__ unsigned peers_of(int key, int nbits)
+{
+    unsigned p = 0xFFFFFFFFu;
+    for (int b = 0; b < nbits; ++b) {
+        const bool bit = (key >> b) & 1;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, bit);
+        p &= bit ? bal : ~bal;
+    }
+    return p;
+}
+
+// Bounded grid barrier for a cooperative launch (all CTAs resident).
+// Returns false when any CTA has given up; the caller must then return.
+__device__ bool grid_barrier(GridSync *gs, unsigned int *sFlag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int ok = 1;
+        const unsigned int g = ld_acquire(&gs->gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&gs->count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            st_release(&gs->gen, g + 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire(&gs->gen) == g) {
+                if (ld_acquire(&gs->abort)) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > kSpinLimitCycles) {
+                    atomicExch(&gs->abort, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (ld_acquire(&gs->abort)) ok = 0;
+        *sFlag = ok;
+    }
+    __syncthreads();
+    return *sFlag != 0;
+}
+
+// Exclusive block scan of v[0..n) in shared memory (n <= 4 * kRoundsBlock).
+__device__ uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __syncthreads();
+    uint32_t x[4], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = tid * 4 + j;
+        const uint32_t t = i < n ? v[i] : 0u;
+        x[j] = sum;
+        sum += t;
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < kRoundsWarps ? tmp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < kRoundsWarps) tmp[lane] = wi - w;
+        if (lane == 31) tmp[kRoundsWarps] = wi;
+    }
+    __syncthreads();
+    const uint32_t base = tmp[warp] + incl - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = tid * 4 + j;
+        if (i < n) v[i] = base + x[j];
+    }
+    const uint32_t total = tmp[kRoundsWarps];
+    __syncthreads();
+    return total;
+}
+
+struct RoundsLayout {
+    uint32_t items, wc, cnt, start, base, tot, off, slotSrc, slotDst, tmp, flag, bar, work, total;
+};
+
+__host__ __device__ inline uint32_t rounds_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int R, uint32_t workBytes)
+{
+    RoundsLayout L;
+    uint32_t o = 0;
+    L.items = o;   o = rounds_align(o + kRoundsTile * itemBytes, 128);
+    L.wc = o;      o = rounds_align(o + kRoundsWarps * R * 4u, 16);
+    L.cnt = o;     o = rounds_align(o + R * 4u, 16);
+    L.start = o;   o = rounds_align(o + R * 4u, 16);
+    L.base = o;    o = rounds_align(o + R * 4u, 16);
+    L.tot = o;     o = rounds_align(o + R * 4u, 16);
+    L.off = o;     o = rounds_align(o + (R + 1) * 4u, 16);
+    L.slotSrc = o; o = rounds_align(o + kRoundsTile * 2u, 16);
+    L.slotDst = o; o = rounds_align(o + kRoundsTile * 4u, 16);
+    L.tmp = o;     o = rounds_align(o + (kRoundsWarps + 1) * 4u, 16);
+    L.flag = o;    o = rounds_align(o + 4u, 16);
+    L.bar = o;     o = rounds_align(o + 8u, 16);
+    L.work = o;    o = rounds_align(o + workBytes, 16);
+    L.total = o;
+    return L;
+}
+
+// The workload policy W provides:
+//   static constexpr int V;               16-byte vectors per item
+//   static constexpr bool kAppendRetired; retire() gets a slot from the block append
+//   uint32_t smemBytes() const;           its own shared memory
+//   void load_smem(void *s) const;        fill it (all threads; a barrier follows)
+//   int32_t step(uint4 (&w)[V], int32_t rank, uint32_t round, const void *s) const;
+//       advances one item: returns the destination rank (w updated) or -1 to retire
+//   unsigned long long *retiredCounter() const;
+//   void retire(const uint4 (&w)[V], unsigned long long slot) const;
+template <class W>
+__global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W work)
+{
+    constexpr int V = W::V;
+    constexpr uint32_t kItemBytes = 16u * V;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int R = a.numRanks;
+    const RoundsLayout L = rounds_layout(kItemBytes, R, work.smemBytes());
+    uint4 *sItems = reinterpret_cast<uint4 *>(smem + L.items);
+    uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
+    uint32_t *dCnt = reinterpret_cast<uint32_t *>(smem + L.cnt);
+    uint32_t *dStart = reinterpret_cast<uint32_t *>(smem + L.start);
+    uint32_t *dBase = reinterpret_cast<uint32_t *>(smem + L.base);
+    uint32_t *sTot = reinterpret_cast<uint32_t *>(smem + L.tot);
+    uint32_t *sOff = reinterpret_cast<uint32_t *>(smem + L.off);
+    uint16_t *slotSrc = reinterpret_cast<uint16_t *>(smem + L.slotSrc);
+    uint32_t *slotDst = reinterpret_cast<uint32_t *>(smem + L.slotDst);
+    uint32_t *tmp = reinterpret_cast<uint32_t *>(smem + L.tmp);
+    unsigned int *sFlag = reinterpret_cast<unsigned int *>(smem + L.flag);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    void *sWork = smem + L.work;
+    __shared__ typename rf::BlockAppend<kRoundsBlock>::Storage sRet;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, c = blockIdx.x;
+    const int nbits = 32 - __clz(R);  // keys 0..R (R = no item)
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_proxy_async_smem();
+    }
+    work.load_smem(sWork);
+    __syncthreads();
+
+    uint32_t phase = 0;
+    uint32_t n = a.inOffset[R];
+    unsigned long long forwarded = 0;
+    uint32_t round = 0;
+    bool failed = false;
+
+    for (;; ++round) {
+        if (n == 0 || round >= a.maxRounds) break;
+        const bool logRound = a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
+        if (logRound) a.roundLog[6 * round + 0] = globaltimer();
+        for (int e = tid; e <= R; e += kRoundsBlock) sOff[e] = a.inOffset[e];
+        for (int e = tid; e < R; e += kRoundsBlock) sTot[e] = 0u;
+        __syncthreads();
+        const uint32_t lo = (uint32_t)(((unsigned long long)n * c) / G);
+        const uint32_t hi = (uint32_t)(((unsigned long long)n * (c + 1)) / G);
+
+        // ---- phase 1: work step, write back to the same slots ------------------
+        for (uint32_t b = lo; b < hi; b += kRoundsTile) {
+            const uint32_t cnt = min(kRoundsTile, hi - b);
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                fence_proxy_async_global();
+                mbar_arrive_expect_tx(bar, cnt * kItemBytes);
+                bulk_g2s(sItems, a.in + (size_t)b * V, cnt * kItemBytes, bar);
+            }
+            const bool ok = mbar_wait_bounded(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicExch(&a.sync->abort, 1u);
+                    (void)mbar_wait_bounded(bar, phase ^ 1u);
+                }
+                failed = true;
+                break;
+            }
+#pragma unroll
+            for (int k = 0; k < kRoundsK; ++k) {
+                const uint32_t j = (uint32_t)(k * kRoundsBlock + tid);
+                const bool valid = j < cnt;
+                int32_t d = -2;
+                uint4 w[V];
+                if (valid) {
+#pragma unroll
+                    for (int q = 0; q < V; ++q) w[q] = sItems[j * V + q];
+                    const int32_t rank = rf::rankOf(sOff, R, b + j);
+                    d = work.step(w, rank, round, sWork);
+                    if (d >= 0) {
+#pragma unroll
+                        for (int q = 0; q < V; ++q) sItems[j * V + q] = w[q];
+                    }
+                    a.dest[b + j] = d >= 0 ? d : -1;
+                }
+                const bool fwd = valid && d >= 0;
+                const int key = fwd ? d : R;
+                const unsigned peers = peers_of(key, nbits);
+                if (fwd && lane == __ffs(peers) - 1) atomicAdd(&sTot[d], (uint32_t)__popc(peers));
+                const bool ret = valid && d < 0;
+                if (W::kAppendRetired) {
+                    const unsigned long long slot =
+                        rf::BlockAppend<kRoundsBlock>::reserve(sRet, work.retiredCounter(), ret);
+                    if (ret) work.retire(w, slot);
+                } else if (ret) {
+                    work.retire(w, 0ull);
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                bulk_s2g(a.out + (size_t)b * V, sItems, cnt * kItemBytes);
+                bulk_wait_read();
+            }
+            __syncthreads();
+        }
+        if (tid == 0) bulk_wait_all();
+        fence_proxy_async_global();
+        if (logRound) a.roundLog[6 * round + 1] = globaltimer();
+        if (!failed) {
+            for (int e = tid; e < R; e += kRoundsBlock) {
+                const uint32_t v = sTot[e];
+                a.tot[(size_t)c * R + e] = v;
+                if (v) atomicAdd(&a.total[(round & 1u) * R + e], v);
+            }
+        }
+        if (failed || !grid_barrier(a.sync, sFlag)) {
+            failed = true;
+            break;
+        }
+        if (logRound) a.roundLog[6 * round + 2] = globaltimer();
+
+        // ---- phase 2: offsets, next count, this CTA's base per destination -----
+        for (int e = tid; e < R; e += kRoundsBlock) dStart[e] = a.total[(round & 1u) * R + e];
+        const uint32_t nNext = rounds_block_scan(dStart, R, tmp);
+        {
+            // dBase[e] = offset[e] + sum of the counts of CTAs 0 .. c-1
+            const int groups = R >= kRoundsBlock ? 1 : kRoundsBlock / R;
+            for (int e = tid; e < R; e += kRoundsBlock) dBase[e] = 0u;
+            __syncthreads();
+            for (int t = tid; t < groups * R; t += kRoundsBlock) {
+                const int e = t % R, g = t / R;
+                uint32_t s = 0;
+                for (int cc = g; cc < c; cc += groups) s += a.tot[(size_t)cc * R + e];
+                if (s) atomicAdd(&dBase[e], s);
+            }
+            __syncthreads();
+            for (int e = tid; e < R; e += kRoundsBlock) dBase[e] += dStart[e];
+        }
+        if (c == 0) {
+            for (int e = tid; e < R; e += kRoundsBlock) {
+                a.inOffset[e] = dStart[e];
+                a.total[((round + 1u) & 1u) * R + e] = 0u;
+            }
+            if (tid == 0) a.inOffset[R] = nNext;
+        }
+        forwarded += nNext;
+        __syncthreads();
+
+        // ---- phase 3: stable scatter of this CTA's range -----------------------
+        for (uint32_t b = lo; b < hi; b += kRoundsTile) {
+            const uint32_t cnt = min(kRoundsTile, hi - b);
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                fence_proxy_async_global();
+                mbar_arrive_expect_tx(bar, cnt * kItemBytes);
+                bulk_g2s(sItems, a.out + (size_t)b * V, cnt * kItemBytes, bar);
+            }
+            for (int e = lane; e < R; e += 32) wc[warp * R + e] = 0u;
+            __syncwarp();
+            int myD[kRoundsK];
+            uint32_t myR[kRoundsK];
+#pragma unroll
+            for (int k = 0; k < kRoundsK; ++k) {
+                const uint32_t idx = (uint32_t)(warp * 32 * kRoundsK + k * 32 + lane);
+                const int32_t d = idx < cnt ? a.dest[b + idx] : -1;
+                const bool valid = (uint32_t)d < (uint32_t)R;
+                const int key = valid ? d : R;
+                const unsigned peers = peers_of(key, nbits);
+                const int leader = __ffs(peers) - 1;
+                uint32_t old = 0;
+                if (valid && lane == leader) {
+                    old = wc[warp * R + d];
+                    wc[warp * R + d] = old + (uint32_t)__popc(peers);
+                }
+                old = __shfl_sync(0xFFFFFFFFu, old, leader);
+                __syncwarp();
+                myD[k] = valid ? d : -1;
+                myR[k] = old + (uint32_t)__popc(peers & lanemask_lt());
+            }
+            __syncthreads();
+            for (int e = tid; e < R; e += kRoundsBlock) {
+                uint32_t s = 0;
+#pragma unroll
+                for (int ww = 0; ww < kRoundsWarps; ++ww) {
+                    const uint32_t v = wc[ww * R + e];
+                    wc[ww * R + e] = s;
+                    s += v;
+                }
+                dCnt[e] = s;
+                dStart[e] = s;
+            }
+            const uint32_t nValid = rounds_block_scan(dStart, R, tmp);
+#pragma unroll
+            for (int k = 0; k < kRoundsK; ++k) {
+                if (myD[k] >= 0) {
+                    const int d = myD[k];
+                    const uint32_t within = wc[warp * R + d] + myR[k];
+                    const uint32_t slot = dStart[d] + within;
+                    slotSrc[slot] = (uint16_t)(warp * 32 * kRoundsK + k * 32 + lane);
+                    slotDst[slot] = dBase[d] + within;
+                }
+            }
+            const bool ok = mbar_wait_bounded(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicExch(&a.sync->abort, 1u);
+                    (void)mbar_wait_bounded(bar, phase ^ 1u);
+                }
+                failed = true;
+                break;
+            }
+            const uint32_t total = nValid * V;
+            for (uint32_t v = tid; v < total; v += kRoundsBlock) {
+                const uint32_t slot = v / V;
+                const uint32_t part = v - slot * V;
+                a.in[(size_t)slotDst[slot] * V + part] = sItems[(uint32_t)slotSrc[slot] * V + part];
+            }
+            __syncthreads();
+            for (int e = tid; e < R; e += kRoundsBlock) dBase[e] += dCnt[e];
+            __syncthreads();
+        }
+        fence_proxy_async_global();
+        if (logRound) {
+            a.roundLog[6 * round + 3] = globaltimer();
+            a.roundLog[6 * round + 4] = n;
+            a.roundLog[6 * round + 5] = nNext;
+        }
+        if (failed || !grid_barrier(a.sync, sFlag)) {
+            failed = true;
+            break;
+        }
+        n = nNext;
+    }
+    if (c == 0 && tid == 0) {
+        a.result[0] = round;
+        a.result[1] = forwarded;
+        a.result[2] = failed ? RF_DEV_TIMEOUT : 0u;
+        *a.numActiveOut = failed ? 0ull : n;
+    }
+}
+
+// Host side: one cooperative launch of rounds_kernel<W> over the context's
+// queues, starting from its current incoming queue.  res (host) receives
+// {rounds, forwarded, status, 0}.  Waits for the stream.
+template <class W>
+rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStream_t s,
+                        unsigned long long *roundLog, uint32_t roundLogCap, unsigned long long res[4])
+{
+    const uint32_t itemBytes = 16u * W::V;
+    if (ctx->itemBytes != itemBytes) {
+        set_error("persistent rounds: the workload moves %u-byte items, the context %u", itemBytes,
+                  ctx->itemBytes);
+        return RF_ERR_ARG;
+    }
+    const int R = ctx->numRanks;
+    const RoundsLayout L = rounds_layout(itemBytes, R, work.smemBytes());
+    int optin = 0;
+    RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if ((int)L.total > optin) {
+        set_error("persistent rounds: %u bytes of shared memory per CTA exceed the device's %d", L.total, optin);
+        return RF_ERR_ARG;
+    }
+    auto fn = rounds_kernel<W>;
+    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    int perSM = 0;
+    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
+    if (perSM < 1) {
+        set_error("persistent rounds: the kernel does not fit on an SM");
+        return RF_ERR_ARG;
+    }
+    const int G = ctx->numSMs * perSM;
+    const size_t totBytes = (size_t)G * R * sizeof(uint32_t);
+    const size_t totalBytes = (size_t)2 * R * sizeof(unsigned int);
+    const size_t tailBytes = totalBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
+    if (rf_status st = ensure_rounds_scratch(ctx, totBytes + tailBytes)) return st;
+    unsigned char *base = static_cast<unsigned char *>(ctx->roundsScratch);
+    RoundsArgs a;
+    a.in = static_cast<uint4 *>(ctx->in);
+    a.out = static_cast<uint4 *>(ctx->out);
+    a.dest = ctx->dest;
+    a.inOffset = ctx->inOffset;
+    a.tot = reinterpret_cast<uint32_t *>(base);
+    a.total = reinterpret_cast<unsigned int *>(base + totBytes);
+    a.sync = reinterpret_cast<GridSync *>(base + totBytes + totalBytes);
+    a.result = reinterpret_cast<unsigned long long *>(base + totBytes + totalBytes + sizeof(GridSync));
+    a.numActiveOut = &ctx->dev->numActive;
+    a.roundLog = roundLog;
+    a.roundLogCap = roundLog ? roundLogCap : 0u;
+    a.maxRounds = maxRounds;
+    a.numRanks = R;
+    RF_CUDA(cudaMemsetAsync(base + totBytes, 0, tailBytes, s));
+    W w = work;
+    void *params[] = {&a, &w};
+    time_begin(ctx, kTimeRounds, s);
+    RF_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(fn), dim3(G), dim3(kRoundsBlock), params,
+                                        L.total, s));
+    count_launch();
+    time_end(ctx, kTimeRounds, s);
+    RF_CUDA(cudaMemcpyAsync(ctx->host, ctx->dev, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    unsigned long long r[4] = {0, 0, 0, 0};
+    RF_CUDA(cudaMemcpyAsync(r, a.result, sizeof r, cudaMemcpyDeviceToHost, s));
+    RF_CUDA(cudaStreamSynchronize(s));
+    ctx->pending = false;
+    time_collect(ctx);
+    for (int i = 0; i < 4; ++i) res[i] = r[i];
+    if (r[2] & RF_DEV_TIMEOUT) {
+        set_error("persistent rounds: a bounded device-side wait gave up");
+        return RF_ERR_TIMEOUT;
+    }
+    return RF_OK;
+}
+
+}  // namespace rfi

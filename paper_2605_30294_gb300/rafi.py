@@ -50,7 +50,8 @@ class rf_phase_times(ctypes.Structure):
                 ("scanLaunches", ctypes.c_uint64), ("scatterLaunches", ctypes.c_uint64),
                 ("workLaunches", ctypes.c_uint64), ("scatterItems", ctypes.c_uint64),
                 ("scatterMsLarge", ctypes.c_double), ("scatterItemsLarge", ctypes.c_uint64),
-                ("scatterLaunchesLarge", ctypes.c_uint64)]
+                ("scatterLaunchesLarge", ctypes.c_uint64), ("roundsMs", ctypes.c_double),
+                ("roundsLaunches", ctypes.c_uint64)]
 
 
 _P = ctypes.c_void_p
@@ -81,6 +82,8 @@ _SIGS = {
     "rf_c1_work": [_P, _u32, _u32, _i32, _f64, _i32, _i32, _i32, _P, _P, _u64, _i32, _P],
     "rf_c1_run": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _i32, _u32, _P,
                   _PU64, _PU64],
+    "rf_c1_run_batched": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _u32, _P,
+                          _PU64, _PU64, _P, _u32],
     "rf_c0_make_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c0_raygen": [_P, _P, _i32, _i32, _i32, _i32, _P, _P],
     "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
@@ -248,6 +251,19 @@ def rf_c1_run(ctx: int, items, n: int, seed: int, mode: int, zipf_s: float, grid
                          int(deterministic), int(host_memory), max_rounds, stream_handle(stream),
                          ctypes.byref(rounds), ctypes.byref(fwd))
     _check("rf_c1_run", st, allow)
+    return st, cnt.value, rounds.value, fwd.value
+
+
+def rf_c1_run_batched(ctx: int, items, n: int, seed: int, mode: int, zipf_s: float, grid, retired,
+                      host_memory: bool = False, max_rounds: int = 100000, stream=None, round_log=None,
+                      round_log_cap: int = 0, allow=()):
+    """Persistent-kernel microbenchmark; returns (status, retired_count, rounds, forwarded)."""
+    gx, gy, gz = grid
+    cnt, rounds, fwd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib().rf_c1_run_batched(ctx, ptr(items), n, seed, mode, zipf_s, gx, gy, gz, ptr(retired),
+                                 ctypes.byref(cnt), int(host_memory), max_rounds, stream_handle(stream),
+                                 ctypes.byref(rounds), ctypes.byref(fwd), ptr(round_log), round_log_cap)
+    _check("rf_c1_run_batched", st, allow)
     return st, cnt.value, rounds.value, fwd.value
 
 

@@ -146,3 +146,101 @@ def test_max_rounds_guard():
                                               retired, max_rounds=3, stream=s,
                                               allow=(rafi.RF_ERR_MAX_ROUNDS,))
         assert st == rafi.RF_ERR_MAX_ROUNDS and rounds == 3 and cnt < n
+
+
+# ---------------------------------------------------------------------------
+# batched form: all rounds in one persistent kernel
+# ---------------------------------------------------------------------------
+def _run_batched(items, seed, mode, host=False, max_rounds=100000, ctx=None, allow=()):
+    n = len(items)
+    s = stream()
+    own = ctx is None
+    ctx = ctx or rafi.Context(R, 64, n)
+    try:
+        if host:
+            retired = np.zeros((n, 16), np.uint32)
+            st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, items.ctypes.data, n, seed, mode, 1.1, GRID,
+                                                          retired.ctypes.data, True, max_rounds, s, allow=allow)
+            return retired[:cnt], rounds, fwd, st
+        retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, to_dev(items), n, seed, mode, 1.1, GRID, retired,
+                                                      False, max_rounds, s, allow=allow)
+        return retired[:cnt].cpu().numpy().view(np.uint32), rounds, fwd, st
+    finally:
+        if own:
+            ctx.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n", [1, 777, 20011, 300007])
+def test_batched_matches_oracle_multiset(mode, n):
+    seed = 5
+    items = inputs.c1_items(n, seed=seed)
+    got, rounds, fwd, st = _run_batched(items, seed, mode)
+    final, hops, _, _ = oracle.c1_walk(items, R, seed, mode, grid=GRID)
+    assert st == rafi.RF_OK and len(got) == n
+    assert rounds == int(hops.max()) + 1
+    assert fwd == int(hops.sum())
+    np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_batched_round_queues_bit_exact(mode):
+    # stopping after k rounds leaves round k's incoming queue, in the serial order
+    n, seed = 50000, 8
+    items = inputs.c1_items(n, seed=seed)
+    s = stream()
+    for k in (0, 1, 3, 7):
+        want = oracle.c1_rounds(items, R, seed, mode, grid=GRID, dump_round=k)
+        with rafi.Context(R, 64, n) as ctx:
+            got, rounds, fwd, st = _run_batched(items, seed, mode, max_rounds=k, ctx=ctx,
+                                                allow=(rafi.RF_ERR_MAX_ROUNDS,))
+            assert rounds == k
+            assert fwd == int(want["active"][1:k + 1].sum())
+            assert rafi.rf_num_active(ctx.handle) == int(want["active"][k])
+            q, off = _queue(ctx, n, s)
+        np.testing.assert_array_equal(off.astype(np.uint64), want["dump_offsets"])
+        np.testing.assert_array_equal(q, want["dump_items"])
+        # the retired items so far are the oracle's first k rounds of retirements
+        ret = int(want["retired"][:k].sum())
+        assert len(got) == ret
+        np.testing.assert_array_equal(canonical_rows(got), canonical_rows(want["retired_items"][:ret]))
+
+
+def test_batched_host_memory_and_round_log():
+    n, seed = 100000, 9
+    items = inputs.c1_items(n, seed=seed)
+    a, ra, fa, _ = _run_batched(items, seed, rafi.RF_C1_NBR6)
+    b, rb, fb, _ = _run_batched(items, seed, rafi.RF_C1_NBR6, host=True)
+    assert (ra, fa) == (rb, fb)
+    np.testing.assert_array_equal(canonical_rows(a), canonical_rows(b))
+    s = stream()
+    log = torch.zeros(6 * 512, dtype=torch.int64, device=dev())
+    retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+    with rafi.Context(R, 64, n) as ctx:
+        st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, to_dev(items), n, seed, rafi.RF_C1_NBR6, 1.1,
+                                                      GRID, retired, False, 100000, s, log, 512)
+    lg = log.cpu().numpy().reshape(-1, 6)[:rounds]
+    t = lg[:, :4]
+    assert rounds == ra and np.all(t > 0)
+    assert np.all(np.diff(t, axis=1) >= 0) and np.all(t[1:, 0] >= t[:-1, 3])
+    # counts: n_in of round k+1 = n_next of round k; round 0 starts with all items
+    assert lg[0, 4] == n and np.all(lg[1:, 4] == lg[:-1, 5]) and lg[-1, 5] == 0
+    assert int(lg[:, 5].sum()) == fwd
+
+
+def test_batched_full_size_matches_plain():
+    n, seed = 1 << 24, 1
+    items = inputs.c1_items(n, seed=seed)
+    d_items = to_dev(items)
+    s = stream()
+    with rafi.Context(R, 64, n) as ctx:
+        ra = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        rb = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        for mode in MODES:
+            st, ca, roa, fa = rafi.rf_c1_run(ctx.handle, d_items, n, seed, mode, 1.1, GRID, ra, stream=s)
+            st, cb, rob, fb = rafi.rf_c1_run_batched(ctx.handle, d_items, n, seed, mode, 1.1, GRID, rb, stream=s)
+            assert (ca, roa, fa) == (cb, rob, fb) and ca == n
+            ka = canonical_rows(ra.cpu().numpy().view(np.uint32)[:, [0, 1, 13, 14, 15]])
+            kb = canonical_rows(rb.cpu().numpy().view(np.uint32)[:, [0, 1, 13, 14, 15]])
+            np.testing.assert_array_equal(ka, kb)
