@@ -486,12 +486,15 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     const RoundsLayout L = rounds_layout(itemBytes, R, work.smemBytes());
     int optin = 0;
     RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    if ((int)L.total > optin) {
-        set_error("persistent rounds: %u bytes of shared memory per CTA exceed the device's %d", L.total, optin);
+    auto fn = rounds_kernel<W>;
+    cudaFuncAttributes fa;
+    RF_CUDA(cudaFuncGetAttributes(&fa, fn));
+    const int dynMax = optin - (int)fa.sharedSizeBytes;  // the limit covers static shared memory too
+    if ((int)L.total > dynMax) {
+        set_error("persistent rounds: %u bytes of shared memory per CTA exceed the device's %d", L.total, dynMax);
         return RF_ERR_ARG;
     }
-    auto fn = rounds_kernel<W>;
-    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dynMax));
     int perSM = 0;
     RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
     if (perSM < 1) {
