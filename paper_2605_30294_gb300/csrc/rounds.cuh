@@ -59,8 +59,12 @@ struct RoundsArgs {
 
 constexpr int kRoundsBlock = 256;
 constexpr int kRoundsWarps = kRoundsBlock / 32;
-constexpr int kRoundsK = 4;  // items per thread per tile
+constexpr int kRoundsK = 2;  // items per thread per tile
 constexpr uint32_t kRoundsTile = kRoundsBlock * kRoundsK;
+
+// Row stride (words) of the per-CTA count table: rows start 16-byte aligned
+// so a run of rows can be staged with one bulk copy.
+__host__ __device__ inline int rounds_row_stride(int R) { return (R + 3) / 4 * 4; }
 
 __device__ __forceinline__ unsigned long long globaltimer()
 {
@@ -195,11 +199,13 @@ struct RoundsLayout {
 
 __host__ __device__ inline uint32_t rounds_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
+// items: two tile buffers (double buffering); the same bytes stage the
+// per-CTA count rows in phase 2.
 __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int R, uint32_t workBytes)
 {
     RoundsLayout L;
     uint32_t o = 0;
-    L.items = o;   o = rounds_align(o + kRoundsTile * itemBytes, 128);
+    L.items = o;   o = rounds_align(o + 2u * kRoundsTile * itemBytes, 128);
     L.wc = o;      o = rounds_align(o + kRoundsWarps * R * 4u, 16);
     L.cnt = o;     o = rounds_align(o + R * 4u, 16);
     L.start = o;   o = rounds_align(o + R * 4u, 16);
@@ -210,7 +216,7 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int R,
     L.slotDst = o; o = rounds_align(o + kRoundsTile * 4u, 16);
     L.tmp = o;     o = rounds_align(o + (kRoundsWarps + 1) * 4u, 16);
     L.flag = o;    o = rounds_align(o + 4u, 16);
-    L.bar = o;     o = rounds_align(o + 8u, 16);
+    L.bar = o;     o = rounds_align(o + 16u, 16);
     L.work = o;    o = rounds_align(o + workBytes, 16);
     L.total = o;
     return L;
@@ -226,14 +232,17 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int R,
 //   unsigned long long *retiredCounter() const;
 //   void retire(const uint4 (&w)[V], unsigned long long slot) const;
 template <class W>
-__global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W work)
+__global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W work)
 {
     constexpr int V = W::V;
     constexpr uint32_t kItemBytes = 16u * V;
+    constexpr uint32_t kTileVecs = kRoundsTile * V;
     extern __shared__ __align__(128) unsigned char smem[];
     const int R = a.numRanks;
+    const int Rp = rounds_row_stride(R);
     const RoundsLayout L = rounds_layout(kItemBytes, R, work.smemBytes());
-    uint4 *sItems = reinterpret_cast<uint4 *>(smem + L.items);
+    uint4 *sBuf = reinterpret_cast<uint4 *>(smem + L.items);  // two tiles of kTileVecs
+    uint32_t *sRows = reinterpret_cast<uint32_t *>(smem + L.items);
     uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
     uint32_t *dCnt = reinterpret_cast<uint32_t *>(smem + L.cnt);
     uint32_t *dStart = reinterpret_cast<uint32_t *>(smem + L.start);
@@ -244,22 +253,54 @@ __global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W
     uint32_t *slotDst = reinterpret_cast<uint32_t *>(smem + L.slotDst);
     uint32_t *tmp = reinterpret_cast<uint32_t *>(smem + L.tmp);
     unsigned int *sFlag = reinterpret_cast<unsigned int *>(smem + L.flag);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);  // bar[0], bar[1]: one per tile buffer
     void *sWork = smem + L.work;
     __shared__ typename rf::BlockAppend<kRoundsBlock>::Storage sRet;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, c = blockIdx.x;
     const int nbits = 32 - __clz(R);  // keys 0..R (R = no item)
+    const uint32_t rowsPerStage = (2u * kTileVecs * 16u) / (uint32_t)(Rp * 4);
 
     if (tid == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_proxy_async_smem();
     }
     work.load_smem(sWork);
     __syncthreads();
 
-    uint32_t phase = 0;
+    uint32_t par[2] = {0u, 0u};       // phase parity of bar[0], bar[1]
+    bool pending[2] = {false, false};  // thread 0: a bulk load into the buffer is in flight
+    // issue a bulk load of `bytes` at src into staging buffer `buf` (thread 0)
+    auto issue_bytes = [&](int buf, void *dst, const void *src, uint32_t bytes) {
+        fence_proxy_async_smem();
+        fence_proxy_async_global();
+        mbar_arrive_expect_tx(&bar[buf], bytes);
+        bulk_g2s(dst, src, bytes, &bar[buf]);
+        pending[buf] = true;
+    };
+    auto issue = [&](int buf, const uint4 *src, uint32_t cnt) {
+        issue_bytes(buf, sBuf + buf * kTileVecs, src, cnt * kItemBytes);
+    };
+    // wait for buffer `buf` (all threads).  On a timeout: raise the abort flag,
+    // let every copy still in flight land (bounded), return false.
+    auto wait = [&](int buf) -> bool {
+        const bool ok = mbar_wait_bounded(&bar[buf], par[buf]);
+        par[buf] ^= 1u;
+        pending[buf] = false;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(&a.sync->abort, 1u);
+                (void)mbar_wait_bounded(&bar[buf], par[buf] ^ 1u);
+                const int other = buf ^ 1;
+                if (pending[other]) (void)mbar_wait_bounded(&bar[other], par[other]);
+            }
+            return false;
+        }
+        return true;
+    };
+
     uint32_t n = a.inOffset[R];
     unsigned long long forwarded = 0;
     uint32_t round = 0;
@@ -274,26 +315,24 @@ __global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W
         __syncthreads();
         const uint32_t lo = (uint32_t)(((unsigned long long)n * c) / G);
         const uint32_t hi = (uint32_t)(((unsigned long long)n * (c + 1)) / G);
+        const uint32_t nt = (hi - lo + kRoundsTile - 1) / kRoundsTile;
 
         // ---- phase 1: work step, write back to the same slots ------------------
-        for (uint32_t b = lo; b < hi; b += kRoundsTile) {
+        if (tid == 0 && nt) issue(0, a.in + (size_t)lo * V, min(kRoundsTile, hi - lo));
+        for (uint32_t t = 0; t < nt; ++t) {
+            const int buf = t & 1;
+            const uint32_t b = lo + t * kRoundsTile;
             const uint32_t cnt = min(kRoundsTile, hi - b);
-            if (tid == 0) {
-                fence_proxy_async_smem();
-                fence_proxy_async_global();
-                mbar_arrive_expect_tx(bar, cnt * kItemBytes);
-                bulk_g2s(sItems, a.in + (size_t)b * V, cnt * kItemBytes, bar);
+            if (tid == 0 && t + 1 < nt) {
+                bulk_wait_read();  // the store of tile t-1 has left buffer buf^1
+                const uint32_t nb = b + kRoundsTile;
+                issue(buf ^ 1, a.in + (size_t)nb * V, min(kRoundsTile, hi - nb));
             }
-            const bool ok = mbar_wait_bounded(bar, phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicExch(&a.sync->abort, 1u);
-                    (void)mbar_wait_bounded(bar, phase ^ 1u);
-                }
+            if (!wait(buf)) {
                 failed = true;
                 break;
             }
+            uint4 *sItems = sBuf + buf * kTileVecs;
 #pragma unroll
             for (int k = 0; k < kRoundsK; ++k) {
                 const uint32_t j = (uint32_t)(k * kRoundsBlock + tid);
@@ -326,22 +365,18 @@ __global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W
             }
             fence_proxy_async_smem();
             __syncthreads();
-            if (tid == 0) {
-                bulk_s2g(a.out + (size_t)b * V, sItems, cnt * kItemBytes);
-                bulk_wait_read();
-            }
-            __syncthreads();
+            if (tid == 0) bulk_s2g(a.out + (size_t)b * V, sItems, cnt * kItemBytes);
         }
         if (tid == 0) bulk_wait_all();
-        fence_proxy_async_global();
         if (logRound) a.roundLog[6 * round + 1] = globaltimer();
         if (!failed) {
             for (int e = tid; e < R; e += kRoundsBlock) {
                 const uint32_t v = sTot[e];
-                a.tot[(size_t)c * R + e] = v;
+                a.tot[(size_t)c * Rp + e] = v;
                 if (v) atomicAdd(&a.total[(round & 1u) * R + e], v);
             }
         }
+        fence_proxy_async_global();
         if (failed || !grid_barrier(a.sync, sFlag)) {
             failed = true;
             break;
@@ -349,20 +384,29 @@ __global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W
         if (logRound) a.roundLog[6 * round + 2] = globaltimer();
 
         // ---- phase 2: offsets, next count, this CTA's base per destination -----
-        for (int e = tid; e < R; e += kRoundsBlock) dStart[e] = a.total[(round & 1u) * R + e];
+        for (int e = tid; e < R; e += kRoundsBlock) {
+            dStart[e] = a.total[(round & 1u) * R + e];
+            dBase[e] = 0u;
+        }
         const uint32_t nNext = rounds_block_scan(dStart, R, tmp);
         {
-            // dBase[e] = offset[e] + sum of the counts of CTAs 0 .. c-1
+            // counts of CTAs 0 .. c-1, staged a block of rows at a time
             const int groups = R >= kRoundsBlock ? 1 : kRoundsBlock / R;
-            for (int e = tid; e < R; e += kRoundsBlock) dBase[e] = 0u;
-            __syncthreads();
-            for (int t = tid; t < groups * R; t += kRoundsBlock) {
-                const int e = t % R, g = t / R;
-                uint32_t s = 0;
-                for (int cc = g; cc < c; cc += groups) s += a.tot[(size_t)cc * R + e];
-                if (s) atomicAdd(&dBase[e], s);
+            for (uint32_t r0 = 0; r0 < (uint32_t)c && !failed; r0 += rowsPerStage) {
+                const uint32_t rows = min(rowsPerStage, (uint32_t)c - r0);
+                if (tid == 0) issue_bytes(0, sRows, a.tot + (size_t)r0 * Rp, rows * Rp * 4u);
+                if (!wait(0)) {
+                    failed = true;
+                    break;
+                }
+                for (int t = tid; t < groups * R; t += kRoundsBlock) {
+                    const int e = t % R, g = t / R;
+                    uint32_t sum = 0;
+                    for (uint32_t rr = g; rr < rows; rr += groups) sum += sRows[rr * Rp + e];
+                    if (sum) atomicAdd(&dBase[e], sum);
+                }
+                __syncthreads();
             }
-            __syncthreads();
             for (int e = tid; e < R; e += kRoundsBlock) dBase[e] += dStart[e];
         }
         if (c == 0) {
@@ -376,13 +420,14 @@ __global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W
         __syncthreads();
 
         // ---- phase 3: stable scatter of this CTA's range -----------------------
-        for (uint32_t b = lo; b < hi; b += kRoundsTile) {
+        if (tid == 0 && nt && !failed) issue(0, a.out + (size_t)lo * V, min(kRoundsTile, hi - lo));
+        for (uint32_t t = 0; t < nt && !failed; ++t) {
+            const int buf = t & 1;
+            const uint32_t b = lo + t * kRoundsTile;
             const uint32_t cnt = min(kRoundsTile, hi - b);
-            if (tid == 0) {
-                fence_proxy_async_smem();
-                fence_proxy_async_global();
-                mbar_arrive_expect_tx(bar, cnt * kItemBytes);
-                bulk_g2s(sItems, a.out + (size_t)b * V, cnt * kItemBytes, bar);
+            if (tid == 0 && t + 1 < nt) {
+                const uint32_t nb = b + kRoundsTile;
+                issue(buf ^ 1, a.out + (size_t)nb * V, min(kRoundsTile, hi - nb));
             }
             for (int e = lane; e < R; e += 32) wc[warp * R + e] = 0u;
             __syncwarp();
@@ -408,15 +453,15 @@ __global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W
             }
             __syncthreads();
             for (int e = tid; e < R; e += kRoundsBlock) {
-                uint32_t s = 0;
+                uint32_t sum = 0;
 #pragma unroll
                 for (int ww = 0; ww < kRoundsWarps; ++ww) {
                     const uint32_t v = wc[ww * R + e];
-                    wc[ww * R + e] = s;
-                    s += v;
+                    wc[ww * R + e] = sum;
+                    sum += v;
                 }
-                dCnt[e] = s;
-                dStart[e] = s;
+                dCnt[e] = sum;
+                dStart[e] = sum;
             }
             const uint32_t nValid = rounds_block_scan(dStart, R, tmp);
 #pragma unroll
@@ -429,16 +474,11 @@ __global__ void __launch_bounds__(kRoundsBlock, 1) rounds_kernel(RoundsArgs a, W
                     slotDst[slot] = dBase[d] + within;
                 }
             }
-            const bool ok = mbar_wait_bounded(bar, phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicExch(&a.sync->abort, 1u);
-                    (void)mbar_wait_bounded(bar, phase ^ 1u);
-                }
+            if (!wait(buf)) {
                 failed = true;
                 break;
             }
+            const uint4 *sItems = sBuf + buf * kTileVecs;
             const uint32_t total = nValid * V;
             for (uint32_t v = tid; v < total; v += kRoundsBlock) {
                 const uint32_t slot = v / V;
@@ -502,7 +542,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         return RF_ERR_ARG;
     }
     const int G = ctx->numSMs * perSM;
-    const size_t totBytes = (size_t)G * R * sizeof(uint32_t);
+    const size_t totBytes = (size_t)G * rounds_row_stride(R) * sizeof(uint32_t);
     const size_t totalBytes = (size_t)2 * R * sizeof(unsigned int);
     const size_t tailBytes = totalBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
     if (rf_status st = ensure_rounds_scratch(ctx, totBytes + tailBytes)) return st;
