@@ -158,18 +158,16 @@ __global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
 }
 
 // The hop rule as a workload policy of the persistent round kernel
-// (rounds.cuh): same arithmetic as work_kernel, one item at a time.
+// (rounds.cuh): same arithmetic as work_kernel, one item at a time.  Retired
+// items go to the kernel's retirement sink.
 struct C1Work {
     static constexpr int V = 4;
     static constexpr bool kAppendRetired = true;
     const uint32_t *zipfThr;
-    uint4 *retired;
-    unsigned long long *retiredCount;
-    unsigned long long retiredCap;
     uint32_t seed;
     int32_t mode, gx, gy, gz, R;
 
-    __host__ __device__ uint32_t smemBytes() const { return (uint32_t)RF_MAX_RANKS * 4u; }
+    __host__ __device__ uint32_t smemBytes() const { return (uint32_t)(R > 1 ? R : 1) * 4u; }
     __device__ void load_smem(void *s) const
     {
         uint32_t *t = static_cast<uint32_t *>(s);
@@ -186,16 +184,7 @@ struct C1Work {
         w[3].w += 1u;
         return d;
     }
-    __device__ unsigned long long *retiredCounter() const { return retiredCount; }
-    __device__ void retire(const uint4 (&w)[4], unsigned long long slot) const
-    {
-        if (slot >= retiredCap) return;
-        uint4 *o = retired + (size_t)slot * 4;
-        o[0] = w[0];
-        o[1] = w[1];
-        o[2] = w[2];
-        o[3] = w[3];
-    }
+    __device__ void retire(const uint4 (&)[4]) const {}
 };
 
 // Seed: emit item i to rank i mod R at out slot base + i, where base was
@@ -446,9 +435,6 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
 
     C1Work w;
     w.zipfThr = ctx->zipfThr;
-    w.retired = static_cast<uint4 *>(devRetired);
-    w.retiredCount = ctx->stagingCount;
-    w.retiredCap = n;
     w.seed = seed;
     w.mode = mode;
     w.gx = gx;
@@ -456,7 +442,8 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
     w.gz = gz;
     w.R = ctx->numRanks;
     unsigned long long res[4];
-    rf_status st = launch_rounds(ctx, w, maxRounds, s, roundLog, roundLogCap, res);
+    rf_status st = launch_rounds(ctx, w, maxRounds, s, roundLog, roundLogCap, static_cast<uint4 *>(devRetired), n,
+                                 ctx->stagingCount, res);
     if (st != RF_OK) return st;
     unsigned long long cnt = 0;
     RF_CUDA(cudaMemcpy(&cnt, ctx->stagingCount, sizeof cnt, cudaMemcpyDeviceToHost));

@@ -137,7 +137,8 @@ rf_status alloc_queues(rf_ctx *ctx, uint64_t capacity)
     const size_t qbytes = (size_t)capacity * ctx->itemBytes;
     RF_CUDA(cudaMalloc(&ctx->in, qbytes));
     RF_CUDA(cudaMalloc(&ctx->out, qbytes));
-    RF_CUDA(cudaMalloc(&ctx->dest, (size_t)capacity * sizeof(int32_t)));
+    // padded to whole 16-byte units (+16 bytes) so a tile of destinations can be bulk-copied
+    RF_CUDA(cudaMalloc(&ctx->dest, ((size_t)capacity + 3) / 4 * 16 + 16));
     RF_CUDA(cudaMalloc(&ctx->tileHist, (size_t)ctx->numRanks * ctx->maxTiles * sizeof(uint32_t)));
     RF_CUDA(cudaMemset(ctx->inOffset, 0, (size_t)(ctx->numRanks + 1) * sizeof(uint32_t)));
     RF_CUDA(cudaMemset(ctx->count, 0, (size_t)ctx->numRanks * sizeof(uint32_t)));

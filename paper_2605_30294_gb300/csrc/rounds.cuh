@@ -44,14 +44,17 @@ struct GridSync {
 struct RoundsArgs {
     uint4 *in;
     uint4 *out;
-    int32_t *dest;
+    int32_t *dest;             // capacity rounded up to 4 entries + 4 (bulk-copied in 16-byte units)
     uint32_t *inOffset;        // numRanks + 1
-    uint32_t *tot;             // gridDim.x x numRanks: per-CTA destination counts of a round
-    unsigned int *total;       // 2 x numRanks: per-destination totals (round parity)
+    uint32_t *tot;             // gridDim.x rows of per-CTA destination counts (row stride: digits rounded to 4)
+    unsigned int *total;       // 2 x digits: per-destination totals (round parity)
     GridSync *sync;
-    unsigned long long *result;  // {rounds, forwarded, status, spare}
+    unsigned long long *result;  // {rounds, forwarded, status, retired}
     unsigned long long *numActiveOut;  // items still active when the kernel returns
     unsigned long long *roundLog;  // nullable: per round {t_start, t_work_end, t_barrier, t_scatter_end, n_in, n_next}
+    uint4 *retiredOut;         // retirement sink (policies with kAppendRetired)
+    unsigned long long retiredCap;
+    unsigned long long *retiredCountOut;
     uint32_t maxRounds;
     uint32_t roundLogCap;
     int32_t numRanks;
@@ -149,15 +152,15 @@ __device__ bool grid_barrier(GridSync *gs, unsigned int *sFlag)
     return *sFlag != 0;
 }
 
-// Exclusive block scan of v[0..n) in shared memory (n <= 4 * kRoundsBlock).
+// Exclusive block scan of v[0..n) in shared memory (n <= 8 * kRoundsBlock).
 __device__ uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __syncthreads();
-    uint32_t x[4], sum = 0;
+    uint32_t x[8], sum = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = tid * 4 + j;
+    for (int j = 0; j < 8; ++j) {
+        const int i = tid * 8 + j;
         const uint32_t t = i < n ? v[i] : 0u;
         x[j] = sum;
         sum += t;
@@ -184,8 +187,8 @@ __device__ uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
     __syncthreads();
     const uint32_t base = tmp[warp] + incl - sum;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = tid * 4 + j;
+    for (int j = 0; j < 8; ++j) {
+        const int i = tid * 8 + j;
         if (i < n) v[i] = base + x[j];
     }
     const uint32_t total = tmp[kRoundsWarps];
@@ -194,24 +197,27 @@ __device__ uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
 }
 
 struct RoundsLayout {
-    uint32_t items, wc, cnt, start, base, tot, off, slotSrc, slotDst, tmp, flag, bar, work, total;
+    uint32_t items, dests, wc, cnt, start, base, tot, off, slotSrc, slotDst, tmp, flag, bar, work, total;
 };
 
 __host__ __device__ inline uint32_t rounds_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 // items: two tile buffers (double buffering); the same bytes stage the
-// per-CTA count rows in phase 2.
-__host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int R, uint32_t workBytes)
+// per-CTA count rows in phase 2.  dests: the tiles' destinations.  D =
+// destination digits (ranks, plus one retirement digit when the policy
+// appends retired items).
+__host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D, uint32_t workBytes)
 {
     RoundsLayout L;
     uint32_t o = 0;
     L.items = o;   o = rounds_align(o + 2u * kRoundsTile * itemBytes, 128);
-    L.wc = o;      o = rounds_align(o + kRoundsWarps * R * 4u, 16);
-    L.cnt = o;     o = rounds_align(o + R * 4u, 16);
-    L.start = o;   o = rounds_align(o + R * 4u, 16);
-    L.base = o;    o = rounds_align(o + R * 4u, 16);
-    L.tot = o;     o = rounds_align(o + R * 4u, 16);
-    L.off = o;     o = rounds_align(o + (R + 1) * 4u, 16);
+    L.dests = o;   o = rounds_align(o + 2u * (kRoundsTile + 4u) * 4u, 16);
+    L.wc = o;      o = rounds_align(o + kRoundsWarps * D * 4u, 16);
+    L.cnt = o;     o = rounds_align(o + D * 4u, 16);
+    L.start = o;   o = rounds_align(o + D * 4u, 16);
+    L.base = o;    o = rounds_align(o + D * 4u, 16);
+    L.tot = o;     o = rounds_align(o + D * 4u, 16);
+    L.off = o;     o = rounds_align(o + (D + 1) * 4u, 16);
     L.slotSrc = o; o = rounds_align(o + kRoundsTile * 2u, 16);
     L.slotDst = o; o = rounds_align(o + kRoundsTile * 4u, 16);
     L.tmp = o;     o = rounds_align(o + (kRoundsWarps + 1) * 4u, 16);
@@ -224,25 +230,28 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int R,
 
 // The workload policy W provides:
 //   static constexpr int V;               16-byte vectors per item
-//   static constexpr bool kAppendRetired; retire() gets a slot from the block append
+//   static constexpr bool kAppendRetired; retired items go, stably, to the
+//                                         retirement sink (else: retire())
 //   uint32_t smemBytes() const;           its own shared memory
 //   void load_smem(void *s) const;        fill it (all threads; a barrier follows)
 //   int32_t step(uint4 (&w)[V], int32_t rank, uint32_t round, const void *s) const;
 //       advances one item: returns the destination rank (w updated) or -1 to retire
-//   unsigned long long *retiredCounter() const;
-//   void retire(const uint4 (&w)[V], unsigned long long slot) const;
+//   void retire(const uint4 (&w)[V]) const;  (used when !kAppendRetired)
 template <class W>
-__global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W work)
+__global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W work)
 {
     constexpr int V = W::V;
     constexpr uint32_t kItemBytes = 16u * V;
     constexpr uint32_t kTileVecs = kRoundsTile * V;
+    constexpr uint32_t kRetFlag = 0x80000000u;
     extern __shared__ __align__(128) unsigned char smem[];
     const int R = a.numRanks;
-    const int Rp = rounds_row_stride(R);
-    const RoundsLayout L = rounds_layout(kItemBytes, R, work.smemBytes());
+    const int D = R + (W::kAppendRetired ? 1 : 0);  // digits: ranks (+ retirement)
+    const int Dp = rounds_row_stride(D);
+    const RoundsLayout L = rounds_layout(kItemBytes, D, work.smemBytes());
     uint4 *sBuf = reinterpret_cast<uint4 *>(smem + L.items);  // two tiles of kTileVecs
     uint32_t *sRows = reinterpret_cast<uint32_t *>(smem + L.items);
+    int32_t *sDst = reinterpret_cast<int32_t *>(smem + L.dests);  // two tiles of kRoundsTile + 4
     uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
     uint32_t *dCnt = reinterpret_cast<uint32_t *>(smem + L.cnt);
     uint32_t *dStart = reinterpret_cast<uint32_t *>(smem + L.start);
@@ -255,12 +264,11 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
     unsigned int *sFlag = reinterpret_cast<unsigned int *>(smem + L.flag);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);  // bar[0], bar[1]: one per tile buffer
     void *sWork = smem + L.work;
-    __shared__ typename rf::BlockAppend<kRoundsBlock>::Storage sRet;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, c = blockIdx.x;
-    const int nbits = 32 - __clz(R);  // keys 0..R (R = no item)
-    const uint32_t rowsPerStage = (2u * kTileVecs * 16u) / (uint32_t)(Rp * 4);
+    const int nbits = 32 - __clz(D);  // keys 0..D (D = no item)
+    const uint32_t rowsPerStage = (2u * kTileVecs * 16u) / (uint32_t)(Dp * 4);
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -270,39 +278,50 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
     work.load_smem(sWork);
     __syncthreads();
 
-    uint32_t par[2] = {0u, 0u};       // phase parity of bar[0], bar[1]
-    bool pending[2] = {false, false};  // thread 0: a bulk load into the buffer is in flight
-    // issue a bulk load of `bytes` at src into staging buffer `buf` (thread 0)
-    auto issue_bytes = [&](int buf, void *dst, const void *src, uint32_t bytes) {
+    uint32_t par0 = 0u, par1 = 0u;     // phase parity of bar[0], bar[1]
+    bool pend0 = false, pend1 = false;  // thread 0: a bulk load into the buffer is in flight
+    // issue bulk loads of `bytes` at src (and optionally `bytes2` at src2) into buffer `buf` (thread 0)
+    auto issue_bytes = [&](int buf, void *dst, const void *src, uint32_t bytes, void *dst2, const void *src2,
+                           uint32_t bytes2) {
         fence_proxy_async_smem();
         fence_proxy_async_global();
-        mbar_arrive_expect_tx(&bar[buf], bytes);
+        mbar_arrive_expect_tx(&bar[buf], bytes + bytes2);
         bulk_g2s(dst, src, bytes, &bar[buf]);
-        pending[buf] = true;
-    };
-    auto issue = [&](int buf, const uint4 *src, uint32_t cnt) {
-        issue_bytes(buf, sBuf + buf * kTileVecs, src, cnt * kItemBytes);
+        if (bytes2) bulk_g2s(dst2, src2, bytes2, &bar[buf]);
+        if (buf) pend1 = true;
+        else pend0 = true;
     };
     // wait for buffer `buf` (all threads).  On a timeout: raise the abort flag,
     // let every copy still in flight land (bounded), return false.
     auto wait = [&](int buf) -> bool {
-        const bool ok = mbar_wait_bounded(&bar[buf], par[buf]);
-        par[buf] ^= 1u;
-        pending[buf] = false;
+        bool ok;
+        if (buf) {
+            ok = mbar_wait_bounded(&bar[1], par1);
+            par1 ^= 1u;
+            pend1 = false;
+        } else {
+            ok = mbar_wait_bounded(&bar[0], par0);
+            par0 ^= 1u;
+            pend0 = false;
+        }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicExch(&a.sync->abort, 1u);
-                (void)mbar_wait_bounded(&bar[buf], par[buf] ^ 1u);
-                const int other = buf ^ 1;
-                if (pending[other]) (void)mbar_wait_bounded(&bar[other], par[other]);
+                (void)mbar_wait_bounded(&bar[buf], (buf ? par1 : par0) ^ 1u);
+                if (buf == 0 && pend1) (void)mbar_wait_bounded(&bar[1], par1);
+                if (buf == 1 && pend0) (void)mbar_wait_bounded(&bar[0], par0);
             }
             return false;
         }
         return true;
     };
+    // this CTA's range of a round with m items: 16-item aligned boundaries
+    auto range_lo = [&](uint32_t m, int cc) -> uint32_t {
+        return cc >= G ? m : (uint32_t)((((unsigned long long)m * cc) / G) & ~15ull);
+    };
 
     uint32_t n = a.inOffset[R];
-    unsigned long long forwarded = 0;
+    unsigned long long forwarded = 0, retiredSoFar = 0;
     uint32_t round = 0;
     bool failed = false;
 
@@ -311,14 +330,17 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
         const bool logRound = a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
         if (logRound) a.roundLog[6 * round + 0] = globaltimer();
         for (int e = tid; e <= R; e += kRoundsBlock) sOff[e] = a.inOffset[e];
-        for (int e = tid; e < R; e += kRoundsBlock) sTot[e] = 0u;
+        for (int e = tid; e < D; e += kRoundsBlock) sTot[e] = 0u;
         __syncthreads();
-        const uint32_t lo = (uint32_t)(((unsigned long long)n * c) / G);
-        const uint32_t hi = (uint32_t)(((unsigned long long)n * (c + 1)) / G);
+        const uint32_t lo = range_lo(n, c);
+        const uint32_t hi = c + 1 == G ? n : range_lo(n, c + 1);
         const uint32_t nt = (hi - lo + kRoundsTile - 1) / kRoundsTile;
 
         // ---- phase 1: work step, write back to the same slots ------------------
-        if (tid == 0 && nt) issue(0, a.in + (size_t)lo * V, min(kRoundsTile, hi - lo));
+        if (tid == 0 && nt) {
+            const uint32_t cnt0 = min(kRoundsTile, hi - lo);
+            issue_bytes(0, sBuf, a.in + (size_t)lo * V, cnt0 * kItemBytes, nullptr, nullptr, 0u);
+        }
         for (uint32_t t = 0; t < nt; ++t) {
             const int buf = t & 1;
             const uint32_t b = lo + t * kRoundsTile;
@@ -326,7 +348,8 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
             if (tid == 0 && t + 1 < nt) {
                 bulk_wait_read();  // the store of tile t-1 has left buffer buf^1
                 const uint32_t nb = b + kRoundsTile;
-                issue(buf ^ 1, a.in + (size_t)nb * V, min(kRoundsTile, hi - nb));
+                issue_bytes(buf ^ 1, sBuf + (buf ^ 1) * kTileVecs, a.in + (size_t)nb * V,
+                            min(kRoundsTile, hi - nb) * kItemBytes, nullptr, nullptr, 0u);
             }
             if (!wait(buf)) {
                 failed = true;
@@ -337,9 +360,9 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
             for (int k = 0; k < kRoundsK; ++k) {
                 const uint32_t j = (uint32_t)(k * kRoundsBlock + tid);
                 const bool valid = j < cnt;
-                int32_t d = -2;
-                uint4 w[V];
+                int32_t d = -1;
                 if (valid) {
+                    uint4 w[V];
 #pragma unroll
                     for (int q = 0; q < V; ++q) w[q] = sItems[j * V + q];
                     const int32_t rank = rf::rankOf(sOff, R, b + j);
@@ -347,21 +370,16 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
                     if (d >= 0) {
 #pragma unroll
                         for (int q = 0; q < V; ++q) sItems[j * V + q] = w[q];
+                    } else if (W::kAppendRetired) {
+                        d = R;  // the retirement digit: scattered to the sink in phase 3
+                    } else {
+                        work.retire(w);
                     }
-                    a.dest[b + j] = d >= 0 ? d : -1;
+                    a.dest[b + j] = d;
                 }
-                const bool fwd = valid && d >= 0;
-                const int key = fwd ? d : R;
+                const int key = (valid && d >= 0) ? d : D;
                 const unsigned peers = peers_of(key, nbits);
-                if (fwd && lane == __ffs(peers) - 1) atomicAdd(&sTot[d], (uint32_t)__popc(peers));
-                const bool ret = valid && d < 0;
-                if (W::kAppendRetired) {
-                    const unsigned long long slot =
-                        rf::BlockAppend<kRoundsBlock>::reserve(sRet, work.retiredCounter(), ret);
-                    if (ret) work.retire(w, slot);
-                } else if (ret) {
-                    work.retire(w, 0ull);
-                }
+                if (key < D && lane == __ffs(peers) - 1) atomicAdd(&sTot[key], (uint32_t)__popc(peers));
             }
             fence_proxy_async_smem();
             __syncthreads();
@@ -370,10 +388,10 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
         if (tid == 0) bulk_wait_all();
         if (logRound) a.roundLog[6 * round + 1] = globaltimer();
         if (!failed) {
-            for (int e = tid; e < R; e += kRoundsBlock) {
+            for (int e = tid; e < D; e += kRoundsBlock) {
                 const uint32_t v = sTot[e];
-                a.tot[(size_t)c * Rp + e] = v;
-                if (v) atomicAdd(&a.total[(round & 1u) * R + e], v);
+                a.tot[(size_t)c * Dp + e] = v;
+                if (v) atomicAdd(&a.total[(round & 1u) * D + e], v);
             }
         }
         fence_proxy_async_global();
@@ -384,67 +402,75 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
         if (logRound) a.roundLog[6 * round + 2] = globaltimer();
 
         // ---- phase 2: offsets, next count, this CTA's base per destination -----
-        for (int e = tid; e < R; e += kRoundsBlock) {
-            dStart[e] = a.total[(round & 1u) * R + e];
+        for (int e = tid; e < D; e += kRoundsBlock) {
+            dStart[e] = a.total[(round & 1u) * D + e];
             dBase[e] = 0u;
         }
-        const uint32_t nNext = rounds_block_scan(dStart, R, tmp);
+        const uint32_t retiredNow = W::kAppendRetired ? a.total[(round & 1u) * D + R] : 0u;
+        const uint32_t nNext = rounds_block_scan(dStart, R, tmp);  // ranks only
+        if (W::kAppendRetired && tid == 0) dStart[R] = (uint32_t)retiredSoFar;
         {
             // counts of CTAs 0 .. c-1, staged a block of rows at a time
-            const int groups = R >= kRoundsBlock ? 1 : kRoundsBlock / R;
+            const int groups = D >= kRoundsBlock ? 1 : kRoundsBlock / D;
             for (uint32_t r0 = 0; r0 < (uint32_t)c && !failed; r0 += rowsPerStage) {
                 const uint32_t rows = min(rowsPerStage, (uint32_t)c - r0);
-                if (tid == 0) issue_bytes(0, sRows, a.tot + (size_t)r0 * Rp, rows * Rp * 4u);
+                if (tid == 0) issue_bytes(0, sRows, a.tot + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
                 if (!wait(0)) {
                     failed = true;
                     break;
                 }
-                for (int t = tid; t < groups * R; t += kRoundsBlock) {
-                    const int e = t % R, g = t / R;
+                for (int t = tid; t < groups * D; t += kRoundsBlock) {
+                    const int e = t % D, g = t / D;
                     uint32_t sum = 0;
-                    for (uint32_t rr = g; rr < rows; rr += groups) sum += sRows[rr * Rp + e];
+                    for (uint32_t rr = g; rr < rows; rr += groups) sum += sRows[rr * Dp + e];
                     if (sum) atomicAdd(&dBase[e], sum);
                 }
                 __syncthreads();
             }
-            for (int e = tid; e < R; e += kRoundsBlock) dBase[e] += dStart[e];
+            __syncthreads();
+            for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dStart[e];
         }
         if (c == 0) {
-            for (int e = tid; e < R; e += kRoundsBlock) {
-                a.inOffset[e] = dStart[e];
-                a.total[((round + 1u) & 1u) * R + e] = 0u;
-            }
+            for (int e = tid; e < R; e += kRoundsBlock) a.inOffset[e] = dStart[e];
+            for (int e = tid; e < D; e += kRoundsBlock) a.total[((round + 1u) & 1u) * D + e] = 0u;
             if (tid == 0) a.inOffset[R] = nNext;
         }
         forwarded += nNext;
+        retiredSoFar += retiredNow;
         __syncthreads();
 
         // ---- phase 3: stable scatter of this CTA's range -----------------------
-        if (tid == 0 && nt && !failed) issue(0, a.out + (size_t)lo * V, min(kRoundsTile, hi - lo));
+        auto issue3 = [&](int buf, uint32_t bb) {
+            const uint32_t cc = min(kRoundsTile, hi - bb);
+            issue_bytes(buf, sBuf + buf * kTileVecs, a.out + (size_t)bb * V, cc * kItemBytes,
+                        sDst + buf * (kRoundsTile + 4u), a.dest + bb, ((cc + 3u) & ~3u) * 4u);
+        };
+        if (tid == 0 && nt && !failed) issue3(0, lo);
         for (uint32_t t = 0; t < nt && !failed; ++t) {
             const int buf = t & 1;
             const uint32_t b = lo + t * kRoundsTile;
             const uint32_t cnt = min(kRoundsTile, hi - b);
-            if (tid == 0 && t + 1 < nt) {
-                const uint32_t nb = b + kRoundsTile;
-                issue(buf ^ 1, a.out + (size_t)nb * V, min(kRoundsTile, hi - nb));
+            if (tid == 0 && t + 1 < nt) issue3(buf ^ 1, b + kRoundsTile);
+            for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
+            if (!wait(buf)) {
+                failed = true;
+                break;
             }
-            for (int e = lane; e < R; e += 32) wc[warp * R + e] = 0u;
-            __syncwarp();
+            const int32_t *dts = sDst + buf * (kRoundsTile + 4u);
             int myD[kRoundsK];
             uint32_t myR[kRoundsK];
 #pragma unroll
             for (int k = 0; k < kRoundsK; ++k) {
                 const uint32_t idx = (uint32_t)(warp * 32 * kRoundsK + k * 32 + lane);
-                const int32_t d = idx < cnt ? a.dest[b + idx] : -1;
-                const bool valid = (uint32_t)d < (uint32_t)R;
-                const int key = valid ? d : R;
+                const int32_t d = idx < cnt ? dts[idx] : -1;
+                const bool valid = (uint32_t)d < (uint32_t)D;
+                const int key = valid ? d : D;
                 const unsigned peers = peers_of(key, nbits);
                 const int leader = __ffs(peers) - 1;
                 uint32_t old = 0;
                 if (valid && lane == leader) {
-                    old = wc[warp * R + d];
-                    wc[warp * R + d] = old + (uint32_t)__popc(peers);
+                    old = wc[warp * D + d];
+                    wc[warp * D + d] = old + (uint32_t)__popc(peers);
                 }
                 old = __shfl_sync(0xFFFFFFFFu, old, leader);
                 __syncwarp();
@@ -452,42 +478,45 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
                 myR[k] = old + (uint32_t)__popc(peers & lanemask_lt());
             }
             __syncthreads();
-            for (int e = tid; e < R; e += kRoundsBlock) {
+            for (int e = tid; e < D; e += kRoundsBlock) {
                 uint32_t sum = 0;
 #pragma unroll
                 for (int ww = 0; ww < kRoundsWarps; ++ww) {
-                    const uint32_t v = wc[ww * R + e];
-                    wc[ww * R + e] = sum;
+                    const uint32_t v = wc[ww * D + e];
+                    wc[ww * D + e] = sum;
                     sum += v;
                 }
                 dCnt[e] = sum;
                 dStart[e] = sum;
             }
-            const uint32_t nValid = rounds_block_scan(dStart, R, tmp);
+            const uint32_t nValid = rounds_block_scan(dStart, D, tmp);
 #pragma unroll
             for (int k = 0; k < kRoundsK; ++k) {
                 if (myD[k] >= 0) {
                     const int d = myD[k];
-                    const uint32_t within = wc[warp * R + d] + myR[k];
+                    const uint32_t within = wc[warp * D + d] + myR[k];
                     const uint32_t slot = dStart[d] + within;
                     slotSrc[slot] = (uint16_t)(warp * 32 * kRoundsK + k * 32 + lane);
-                    slotDst[slot] = dBase[d] + within;
+                    slotDst[slot] = (dBase[d] + within) | (W::kAppendRetired && d == R ? kRetFlag : 0u);
                 }
             }
-            if (!wait(buf)) {
-                failed = true;
-                break;
-            }
+            __syncthreads();
             const uint4 *sItems = sBuf + buf * kTileVecs;
             const uint32_t total = nValid * V;
             for (uint32_t v = tid; v < total; v += kRoundsBlock) {
                 const uint32_t slot = v / V;
                 const uint32_t part = v - slot * V;
-                a.in[(size_t)slotDst[slot] * V + part] = sItems[(uint32_t)slotSrc[slot] * V + part];
+                const uint32_t dst = slotDst[slot];
+                const uint4 val = sItems[(uint32_t)slotSrc[slot] * V + part];
+                if (W::kAppendRetired && (dst & kRetFlag)) {
+                    const uint32_t r = dst & ~kRetFlag;
+                    if (r < a.retiredCap) a.retiredOut[(size_t)r * V + part] = val;
+                } else {
+                    a.in[(size_t)dst * V + part] = val;
+                }
             }
             __syncthreads();
-            for (int e = tid; e < R; e += kRoundsBlock) dBase[e] += dCnt[e];
-            __syncthreads();
+            for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dCnt[e];
         }
         fence_proxy_async_global();
         if (logRound) {
@@ -505,6 +534,8 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
         a.result[0] = round;
         a.result[1] = forwarded;
         a.result[2] = failed ? RF_DEV_TIMEOUT : 0u;
+        a.result[3] = retiredSoFar;
+        if (a.retiredCountOut) *a.retiredCountOut = retiredSoFar;
         *a.numActiveOut = failed ? 0ull : n;
     }
 }
@@ -514,7 +545,8 @@ __global__ void __launch_bounds__(kRoundsBlock, 2) rounds_kernel(RoundsArgs a, W
 // {rounds, forwarded, status, 0}.  Waits for the stream.
 template <class W>
 rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStream_t s,
-                        unsigned long long *roundLog, uint32_t roundLogCap, unsigned long long res[4])
+                        unsigned long long *roundLog, uint32_t roundLogCap, uint4 *retiredOut,
+                        unsigned long long retiredCap, unsigned long long *retiredCountOut, unsigned long long res[4])
 {
     const uint32_t itemBytes = 16u * W::V;
     if (ctx->itemBytes != itemBytes) {
@@ -523,7 +555,12 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         return RF_ERR_ARG;
     }
     const int R = ctx->numRanks;
-    const RoundsLayout L = rounds_layout(itemBytes, R, work.smemBytes());
+    const int D = R + (W::kAppendRetired ? 1 : 0);
+    if (D > 8 * kRoundsBlock) {
+        set_error("persistent rounds: %d destinations exceed %d", D, 8 * kRoundsBlock);
+        return RF_ERR_ARG;
+    }
+    const RoundsLayout L = rounds_layout(itemBytes, D, work.smemBytes());
     int optin = 0;
     RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     auto fn = rounds_kernel<W>;
@@ -542,8 +579,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         return RF_ERR_ARG;
     }
     const int G = ctx->numSMs * perSM;
-    const size_t totBytes = (size_t)G * rounds_row_stride(R) * sizeof(uint32_t);
-    const size_t totalBytes = (size_t)2 * R * sizeof(unsigned int);
+    const size_t totBytes = (size_t)G * rounds_row_stride(D) * sizeof(uint32_t);
+    const size_t totalBytes = (size_t)2 * D * sizeof(unsigned int);
     const size_t tailBytes = totalBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
     if (rf_status st = ensure_rounds_scratch(ctx, totBytes + tailBytes)) return st;
     unsigned char *base = static_cast<unsigned char *>(ctx->roundsScratch);
@@ -559,6 +596,9 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.numActiveOut = &ctx->dev->numActive;
     a.roundLog = roundLog;
     a.roundLogCap = roundLog ? roundLogCap : 0u;
+    a.retiredOut = retiredOut;
+    a.retiredCap = retiredOut ? retiredCap : 0ull;
+    a.retiredCountOut = retiredCountOut;
     a.maxRounds = maxRounds;
     a.numRanks = R;
     RF_CUDA(cudaMemsetAsync(base + totBytes, 0, tailBytes, s));
