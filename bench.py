@@ -206,20 +206,30 @@ LOG_CAP = 4096  # rounds logged by the persistent kernel
 
 
 def phase_rates(log_rows, item_bytes, min_items=1 << 20):
-    """Per-round GB/s of the work and scatter phases from the persistent kernel's round log."""
+    """Per-round GB/s of the work and scatter phases from the persistent kernel's round log.
+
+    A phase lasts until the barrier that ends it completes, so the slowest
+    CTA sets its time: work = round start -> first barrier done, scatter =
+    first barrier done -> second barrier done.
+    """
     lg = np.asarray(log_rows, dtype=np.float64)
-    big = lg[:, 4] >= min_items
-    work_b = lg[:, 4] * 2 * item_bytes
-    scat_b = lg[:, 5] * 2 * item_bytes
-    work_t = (lg[:, 1] - lg[:, 0]) * 1e-9
-    scat_t = (lg[:, 3] - lg[:, 2]) * 1e-9
+    big = lg[:, 5] >= min_items
+    work_b = lg[:, 5] * 2 * item_bytes
+    scat_b = lg[:, 6] * 2 * item_bytes
+    work_t = (lg[:, 2] - lg[:, 0]) * 1e-9
+    scat_t = (lg[:, 4] - lg[:, 2]) * 1e-9
     out = {"rounds": int(len(lg)), "rounds_ge_2^20": int(big.sum())}
     if big.any():
         out["work_gbs_ge_2^20"] = float(work_b[big].sum() / work_t[big].sum() / 1e9)
         out["scatter_gbs_ge_2^20"] = float(scat_b[big].sum() / scat_t[big].sum() / 1e9)
         per_round = scat_b[big] / scat_t[big] / 1e9
         out["scatter_gbs_ge_2^20_min_round"] = float(per_round.min())
-    out["round_ms_total"] = float((lg[-1, 3] - lg[0, 0]) * 1e-6) if len(lg) else 0.0
+        round_s = (lg[big, 4] - lg[big, 0]).sum() * 1e-9
+        out["round_gbs_ge_2^20"] = float((work_b[big].sum() + scat_b[big].sum()) / round_s / 1e9)
+    small = ~big
+    if small.any():
+        out["us_per_round_lt_2^20"] = float((lg[small, 4] - lg[small, 0]).mean() * 1e-3)
+    out["round_ms_total"] = float((lg[-1, 4] - lg[0, 0]) * 1e-6) if len(lg) else 0.0
     return out
 
 
@@ -248,7 +258,7 @@ def run_ours(args):
     items = inputs.c1_items(n, seed=SEED)
     d_items = torch.from_numpy(items.view(np.int32)).to(dev)
     retired = torch.zeros((n, 16), dtype=torch.int32, device=dev)
-    log = torch.zeros(6 * LOG_CAP, dtype=torch.int64, device=dev)
+    log = torch.zeros(7 * LOG_CAP, dtype=torch.int64, device=dev)
     s = torch.cuda.current_stream(dev)
     ctx = rafi.Context(RANKS, ITEM_BYTES, n)
 
@@ -300,7 +310,7 @@ def run_ours(args):
 
     # per-round phase rates of the persistent kernel (one extra, untimed step)
     step(True, round_log=log)
-    lg = log.cpu().numpy().reshape(-1, 6)
+    lg = log.cpu().numpy().reshape(-1, 7)
     rows = [r for r in lg if r[0] > 0]
     rates = phase_rates(rows, ITEM_BYTES)
 

@@ -254,11 +254,13 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
  * for a retired item; bounded grid barrier; destination offsets and the next
  * active count; phase 3: stable scatter; bounded grid barrier), so no round
  * needs the host.  Queue order is deterministic: round k's incoming queue is
- * the one of rf_c1_run with deterministic != 0.  roundLog (device, 6 x
+ * the one of rf_c1_run with deterministic != 0.  Rounds of at most 1024
+ * items run on one CTA (the others return).  roundLog (device, 7 x
  * roundLogCap words, nullable) receives per round, as seen by CTA 0, the
- * %globaltimer ns at round start, end of the work phase, after the first
- * barrier and at the end of the scatter phase, then the incoming and the
- * delivered item counts.  RF_ERR_TIMEOUT if a bounded wait gave up.
+ * %globaltimer ns at round start, end of its work phase, after the first
+ * barrier, end of its scatter phase and after the second barrier, then the
+ * incoming and the delivered item counts.  RF_ERR_TIMEOUT if a bounded wait
+ * gave up.
  * Other arguments and results as rf_c1_run. */
 rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
                             int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,

@@ -51,7 +51,7 @@ struct RoundsArgs {
     GridSync *sync;
     unsigned long long *result;  // {rounds, forwarded, status, retired}
     unsigned long long *numActiveOut;  // items still active when the kernel returns
-    unsigned long long *roundLog;  // nullable: per round {t_start, t_work_end, t_barrier, t_scatter_end, n_in, n_next}
+    unsigned long long *roundLog;  // nullable: per round {t_start, t_work_end, t_barrier1, t_scatter_end, t_barrier2, n_in, n_next}
     uint4 *retiredOut;         // retirement sink (policies with kAppendRetired)
     unsigned long long retiredCap;
     unsigned long long *retiredCountOut;
@@ -315,9 +315,21 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
         }
         return true;
     };
-    // this CTA's range of a round with m items: 16-item aligned boundaries
-    auto range_lo = [&](uint32_t m, int cc) -> uint32_t {
-        return cc >= G ? m : (uint32_t)((((unsigned long long)m * cc) / G) & ~15ull);
+    // CTA cc's range of a round with m items over g CTAs: boundaries rounded up
+    // to 16 items (so a small round lands on the first CTAs)
+    auto bound = [&](uint32_t m, int cc, int g) -> uint32_t {
+        const unsigned long long v = (((unsigned long long)m * cc) / g + 15ull) & ~15ull;
+        return (uint32_t)(v < m ? v : m);
+    };
+    // Once a round is this small, CTA 0 finishes the run alone: the other CTAs
+    // return and the round barriers become block barriers.
+    constexpr uint32_t kSoloItems = 2u * kRoundsTile;
+    bool solo = false;
+    auto round_barrier = [&]() -> bool {
+        if (!solo) return grid_barrier(a.sync, sFlag);
+        __threadfence();
+        __syncthreads();
+        return true;
     };
 
     uint32_t n = a.inOffset[R];
@@ -327,13 +339,18 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
 
     for (;; ++round) {
         if (n == 0 || round >= a.maxRounds) break;
+        if (!solo && n <= kSoloItems) {
+            solo = true;
+            if (c != 0) break;
+        }
+        const int g = solo ? 1 : G;
         const bool logRound = a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
-        if (logRound) a.roundLog[6 * round + 0] = globaltimer();
+        if (logRound) a.roundLog[7 * round + 0] = globaltimer();
         for (int e = tid; e <= R; e += kRoundsBlock) sOff[e] = a.inOffset[e];
         for (int e = tid; e < D; e += kRoundsBlock) sTot[e] = 0u;
         __syncthreads();
-        const uint32_t lo = range_lo(n, c);
-        const uint32_t hi = c + 1 == G ? n : range_lo(n, c + 1);
+        const uint32_t lo = bound(n, c, g);
+        const uint32_t hi = bound(n, c + 1, g);
         const uint32_t nt = (hi - lo + kRoundsTile - 1) / kRoundsTile;
 
         // ---- phase 1: work step, write back to the same slots ------------------
@@ -386,7 +403,7 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
             if (tid == 0) bulk_s2g(a.out + (size_t)b * V, sItems, cnt * kItemBytes);
         }
         if (tid == 0) bulk_wait_all();
-        if (logRound) a.roundLog[6 * round + 1] = globaltimer();
+        if (logRound) a.roundLog[7 * round + 1] = globaltimer();
         if (!failed) {
             for (int e = tid; e < D; e += kRoundsBlock) {
                 const uint32_t v = sTot[e];
@@ -395,11 +412,11 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
             }
         }
         fence_proxy_async_global();
-        if (failed || !grid_barrier(a.sync, sFlag)) {
+        if (failed || !round_barrier()) {
             failed = true;
             break;
         }
-        if (logRound) a.roundLog[6 * round + 2] = globaltimer();
+        if (logRound) a.roundLog[7 * round + 2] = globaltimer();
 
         // ---- phase 2: offsets, next count, this CTA's base per destination -----
         for (int e = tid; e < D; e += kRoundsBlock) {
@@ -412,8 +429,10 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
         {
             // counts of CTAs 0 .. c-1, staged a block of rows at a time
             const int groups = D >= kRoundsBlock ? 1 : kRoundsBlock / D;
-            for (uint32_t r0 = 0; r0 < (uint32_t)c && !failed; r0 += rowsPerStage) {
-                const uint32_t rows = min(rowsPerStage, (uint32_t)c - r0);
+            // (a CTA with nothing to scatter needs no base)
+            const uint32_t rowsNeeded = nt ? (uint32_t)c : 0u;
+            for (uint32_t r0 = 0; r0 < rowsNeeded && !failed; r0 += rowsPerStage) {
+                const uint32_t rows = min(rowsPerStage, rowsNeeded - r0);
                 if (tid == 0) issue_bytes(0, sRows, a.tot + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
                 if (!wait(0)) {
                     failed = true;
@@ -520,14 +539,15 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
         }
         fence_proxy_async_global();
         if (logRound) {
-            a.roundLog[6 * round + 3] = globaltimer();
-            a.roundLog[6 * round + 4] = n;
-            a.roundLog[6 * round + 5] = nNext;
+            a.roundLog[7 * round + 3] = globaltimer();
+            a.roundLog[7 * round + 5] = n;
+            a.roundLog[7 * round + 6] = nNext;
         }
-        if (failed || !grid_barrier(a.sync, sFlag)) {
+        if (failed || !round_barrier()) {
             failed = true;
             break;
         }
+        if (logRound) a.roundLog[7 * round + 4] = globaltimer();
         n = nNext;
     }
     if (c == 0 && tid == 0) {

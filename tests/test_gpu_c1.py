@@ -215,18 +215,18 @@ def test_batched_host_memory_and_round_log():
     assert (ra, fa) == (rb, fb)
     np.testing.assert_array_equal(canonical_rows(a), canonical_rows(b))
     s = stream()
-    log = torch.zeros(6 * 512, dtype=torch.int64, device=dev())
+    log = torch.zeros(7 * 512, dtype=torch.int64, device=dev())
     retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
     with rafi.Context(R, 64, n) as ctx:
         st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, to_dev(items), n, seed, rafi.RF_C1_NBR6, 1.1,
                                                       GRID, retired, False, 100000, s, log, 512)
-    lg = log.cpu().numpy().reshape(-1, 6)[:rounds]
-    t = lg[:, :4]
+    lg = log.cpu().numpy().reshape(-1, 7)[:rounds]
+    t = lg[:, :5]
     assert rounds == ra and np.all(t > 0)
-    assert np.all(np.diff(t, axis=1) >= 0) and np.all(t[1:, 0] >= t[:-1, 3])
+    assert np.all(np.diff(t, axis=1) >= 0) and np.all(t[1:, 0] >= t[:-1, 4])
     # counts: n_in of round k+1 = n_next of round k; round 0 starts with all items
-    assert lg[0, 4] == n and np.all(lg[1:, 4] == lg[:-1, 5]) and lg[-1, 5] == 0
-    assert int(lg[:, 5].sum()) == fwd
+    assert lg[0, 5] == n and np.all(lg[1:, 5] == lg[:-1, 6]) and lg[-1, 6] == 0
+    assert int(lg[:, 6].sum()) == fwd
 
 
 def test_batched_full_size_matches_plain():
