@@ -34,11 +34,14 @@
 
 namespace rfi {
 
+constexpr int kSyncGroups = 16;  // first level of the grid barrier
+
 struct GridSync {
-    unsigned int count;  // CTAs arrived at the current barrier
+    unsigned int count;  // groups complete at the current barrier
     unsigned int gen;    // barrier generation
     unsigned int abort;  // set by a CTA whose wait gave up
-    unsigned int pad;
+    unsigned int pad[29];
+    unsigned int group[kSyncGroups][32];  // CTAs arrived per group, one 128-byte line each
 };
 
 struct RoundsArgs {
@@ -116,7 +119,10 @@ __device__ __forceinline__ unsigned peers_of(int key, int nbits)
     return p;
 }
 
-// Bounded grid barrier for a cooperative launch (all CTAs resident).
+// Bounded grid barrier for a cooperative launch (all CTAs resident), in two
+// levels: CTAs arrive on one of kSyncGroups group counters (separate cache
+// lines), the last CTA of a group arrives on the top counter, and the last
+// group releases everyone by bumping the generation.
 // Returns false when any CTA has given up; the caller must then return.
 __device__ bool grid_barrier(GridSync *gs, unsigned int *sFlag)
 {
@@ -124,9 +130,18 @@ __device__ bool grid_barrier(GridSync *gs, unsigned int *sFlag)
     if (threadIdx.x == 0) {
         unsigned int ok = 1;
         const unsigned int g = ld_acquire(&gs->gen);
+        const unsigned int G = gridDim.x;
+        const unsigned int groups = G < (unsigned)kSyncGroups ? G : (unsigned)kSyncGroups;
+        const unsigned int grp = blockIdx.x % groups;
+        const unsigned int members = G / groups + (grp < G % groups ? 1u : 0u);
         __threadfence();
-        const unsigned int arrived = atomicAdd(&gs->count, 1u) + 1u;
-        if (arrived == gridDim.x) {
+        bool last = false;
+        if (atomicAdd(&gs->group[grp][0], 1u) + 1u == members) {
+            atomicExch(&gs->group[grp][0], 0u);
+            __threadfence();
+            last = atomicAdd(&gs->count, 1u) + 1u == groups;
+        }
+        if (last) {
             atomicExch(&gs->count, 0u);
             __threadfence();
             st_release(&gs->gen, g + 1u);
