@@ -296,6 +296,48 @@ rf_status rf_c0_render(rf_ctx *ctx, const float *bricks, const float *cam, int32
                        int32_t W, int32_t H, float *image, int32_t *hopLog, int32_t maxHops,
                        int32_t *hopCount, uint32_t maxRounds, void *stream, uint64_t *rounds);
 
+/* --- streamlines through bricks (32-byte particles) ------------------------ */
+
+/* Particle: {x, y, z (float bits), id} {steps, hops, set, status}; status 1 =
+ * left the grid, 2 = a step did not move it, 3 = maxSteps reached. */
+#define RF_C2_EXITED 1
+#define RF_C2_STALLED 2
+#define RF_C2_MAXSTEPS 3
+
+/* Cut an N^3 x 3 float vector field (device, index ((z*N + y)*N + x)*3 + c)
+ * into (N/B)^3 bricks of (B+4)^3 float4 {vx, vy, vz, 0} with a two-voxel
+ * halo (clamp to edge at the grid border); brick of rank r = bx + nb*(by +
+ * nb*bz) at bricks + r*(B+4)^3*4 floats. */
+rf_status rf_c2_make_bricks(const float *field, int32_t N, int32_t B, float *bricks, void *stream);
+
+/* Seed (Sec. 5.4 "particles are released at predefined seed points"):
+ * particle i at seeds[i] (device, n x 3 floats, inside [0,N)^3), id i, set
+ * setIds[i] (device, nullable: 0), emitted to the rank owning its position.
+ * The out-queue must be empty.  Follow with rf_exchange. */
+rf_status rf_c2_seed(rf_ctx *ctx, const float *seeds, const uint32_t *setIds, uint64_t n, int32_t N, int32_t B,
+                     void *stream);
+
+/* One round of the per-rank trace kernel (Sec. 5.4): each incoming particle
+ * takes RK4 steps of size h on the trilinear field of its rank's brick
+ * (k1 = v(p), k2 = v(p + h/2 k1), k3 = v(p + h/2 k2), k4 = v(p + h k3),
+ * p' = p + h/6 (k1 + 2 k2 + 2 k3 + k4)); it stops when it has made maxSteps
+ * steps, a step does not move it, or it leaves [0,N)^3, and the stopped
+ * particle is written to out[id] (device, outCapacity x 32 bytes).  It is
+ * forwarded when a step enters another rank's brick (hops + 1), or to its own
+ * rank after stepsPerRound steps (0: no such limit).  Out slot i holds
+ * incoming particle i (destination -1 once stopped). */
+rf_status rf_c2_trace(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, float h, uint32_t maxSteps,
+                      uint32_t stepsPerRound, void *out, uint64_t outCapacity, void *stream);
+
+/* Seed, exchange, then rounds of trace + exchange until no particle is
+ * active.  batched == 0: the plain host loop (rf_c2_trace + rf_exchange per
+ * round); batched != 0: all rounds in one persistent cooperative kernel (the
+ * batched form of rf_c1_run_batched).  out (device) receives every particle
+ * by id; *rounds = trace rounds, *forwarded = particles delivered by them. */
+rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const uint32_t *setIds, uint64_t n,
+                    int32_t N, int32_t B, float h, uint32_t maxSteps, uint32_t stepsPerRound, void *out,
+                    int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,6 +64,12 @@ def _load():
             lib.or_c0_render.restype = None
             lib.or_c0_sigma.argtypes = [P, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float]
             lib.or_c0_sigma.restype = ctypes.c_float
+            lib.or_c2_rk4.argtypes = [P, i32, ctypes.c_float, P, P]
+            lib.or_c2_rk4.restype = None
+            lib.or_c2_velocity.argtypes = [P, i32, P, P]
+            lib.or_c2_velocity.restype = None
+            lib.or_c2_trace.argtypes = [P, i32, i32, P, u64, ctypes.c_float, u32, P, P, P, P]
+            lib.or_c2_trace.restype = None
             _lib = lib
     return _lib
 
@@ -217,3 +223,42 @@ def c0_render(vol: np.ndarray, cam: np.ndarray, width: int, height: int, brick: 
 def c0_sigma(vol: np.ndarray, p) -> float:
     vol = _c(vol, np.float32)
     return float(_load().or_c0_sigma(_p(vol), vol.shape[0], float(p[0]), float(p[1]), float(p[2])))
+
+
+# --------------------------------------------------------------------------
+# Streamlines (Sec. 5.4): RK4 through a trilinear vector field
+# --------------------------------------------------------------------------
+EXITED, STALLED, MAXSTEPS = 1, 2, 3
+
+
+def c2_velocity(field: np.ndarray, p) -> np.ndarray:
+    field = _c(field, np.float32)
+    q = _c(np.asarray(p, np.float32).reshape(3), np.float32)
+    out = np.zeros(3, np.float32)
+    _load().or_c2_velocity(_p(field), field.shape[0], _p(q), _p(out))
+    return out
+
+
+def c2_rk4(field: np.ndarray, p, h: float = 0.25) -> np.ndarray:
+    field = _c(field, np.float32)
+    q = _c(np.asarray(p, np.float32).reshape(3), np.float32)
+    out = np.zeros(3, np.float32)
+    _load().or_c2_rk4(_p(field), field.shape[0], h, _p(q), _p(out))
+    return out
+
+
+def c2_trace(field: np.ndarray, seeds: np.ndarray, brick: int, h: float = 0.25, max_steps: int = 2000):
+    """Trace particles through the unpartitioned field (field: N x N x N x 3, index [z, y, x, c]).
+
+    Returns dict(pos n x 3, steps, hops, status).
+    """
+    field = _c(field, np.float32)
+    seeds = _c(seeds, np.float32).reshape(-1, 3)
+    n = seeds.shape[0]
+    pos = np.zeros((n, 3), np.float32)
+    steps = np.zeros(n, np.uint32)
+    hops = np.zeros(n, np.uint32)
+    status = np.zeros(n, np.uint32)
+    _load().or_c2_trace(_p(field), field.shape[0], brick, _p(seeds), n, h, max_steps, _p(pos), _p(steps),
+                        _p(hops), _p(status))
+    return dict(pos=pos, steps=steps, hops=hops, status=status)

@@ -422,3 +422,96 @@ float or_c0_sigma(const float *vol, int32_t N, float px, float py, float pz)
 {
     return or_c0_sample(vol, N, px, py, pz);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Streamlines (Sec. 5.4): particles advected by RK4 through a trilinear     */
+/* vector field, one particle per work item, forwarded between the ranks     */
+/* that own the grid's bricks.                                               */
+/*                                                                          */
+/* field: N^3 x 3 floats, index ((z*N + y)*N + x)*3 + c, voxel centres at    */
+/* v + 0.5.  v(p): trilinear per component over voxel centres, clamp to      */
+/* edge (the weights of the marching workload).                             */
+/* One step (float, written order, no contraction), step h:                 */
+/*   k1 = v(p); k2 = v(p + (h*0.5)*k1); k3 = v(p + (h*0.5)*k2);             */
+/*   k4 = v(p + h*k3); p' = p + (h/6)*(((k1 + 2*k2) + 2*k3) + k4)           */
+/* A particle stops when it has made maxSteps steps (status 3), when a step */
+/* does not move it (p' == p, status 2), or when p' leaves [0, N)^3 (the    */
+/* step is taken, status 1).  hops = changes of owner brick (brick B) along */
+/* the accepted positions inside the grid.                                  */
+/* ------------------------------------------------------------------------ */
+static void or_c2_sample(const float *f, int32_t N, const float *p, float *out)
+{
+    int32_t i0[3], i1[3];
+    float fr[3];
+    for (int a = 0; a < 3; ++a) {
+        float u = p[a] - 0.5f;
+        float fl = floorf(u);
+        fr[a] = u - fl;
+        int32_t lo = (int32_t)fl;
+        int32_t hi = lo + 1;
+        i0[a] = lo < 0 ? 0 : (lo > N - 1 ? N - 1 : lo);
+        i1[a] = hi < 0 ? 0 : (hi > N - 1 ? N - 1 : hi);
+    }
+    float gx = 1.0f - fr[0], gy = 1.0f - fr[1], gz = 1.0f - fr[2];
+#define F(x, y, z, c) f[(((size_t)(z) * (size_t)N + (size_t)(y)) * (size_t)N + (size_t)(x)) * 3u + (c)]
+    for (int c = 0; c < 3; ++c) {
+        float c00 = F(i0[0], i0[1], i0[2], c) * gx + F(i1[0], i0[1], i0[2], c) * fr[0];
+        float c10 = F(i0[0], i1[1], i0[2], c) * gx + F(i1[0], i1[1], i0[2], c) * fr[0];
+        float c01 = F(i0[0], i0[1], i1[2], c) * gx + F(i1[0], i0[1], i1[2], c) * fr[0];
+        float c11 = F(i0[0], i1[1], i1[2], c) * gx + F(i1[0], i1[1], i1[2], c) * fr[0];
+        float c0 = c00 * gy + c10 * fr[1];
+        float c1 = c01 * gy + c11 * fr[1];
+        out[c] = c0 * gz + c1 * fr[2];
+    }
+#undef F
+}
+
+/* one RK4 step from p into q */
+void or_c2_rk4(const float *f, int32_t N, float h, const float *p, float *q)
+{
+    float k1[3], k2[3], k3[3], k4[3], t[3];
+    float half = h * 0.5f, sixth = h / 6.0f;
+    or_c2_sample(f, N, p, k1);
+    for (int a = 0; a < 3; ++a) t[a] = p[a] + half * k1[a];
+    or_c2_sample(f, N, t, k2);
+    for (int a = 0; a < 3; ++a) t[a] = p[a] + half * k2[a];
+    or_c2_sample(f, N, t, k3);
+    for (int a = 0; a < 3; ++a) t[a] = p[a] + h * k3[a];
+    or_c2_sample(f, N, t, k4);
+    for (int a = 0; a < 3; ++a) {
+        float s = ((k1[a] + 2.0f * k2[a]) + 2.0f * k3[a]) + k4[a];
+        q[a] = p[a] + sixth * s;
+    }
+}
+
+/* v(p) for tests */
+void or_c2_velocity(const float *f, int32_t N, const float *p, float *out) { or_c2_sample(f, N, p, out); }
+
+/* Trace n particles through the unpartitioned field.  seeds n x 3;
+ * outputs: pos n x 3 (final position), steps, hops, status. */
+void or_c2_trace(const float *f, int32_t N, int32_t B, const float *seeds, uint64_t n, float h, uint32_t maxSteps,
+                 float *pos, uint32_t *steps, uint32_t *hops, uint32_t *status)
+{
+    int32_t nb = N / B;
+    for (uint64_t i = 0; i < n; ++i) {
+        float p[3] = {seeds[3 * i], seeds[3 * i + 1], seeds[3 * i + 2]};
+        uint32_t k = 0, hp = 0, st = 0;
+        int32_t own = or_c0_owner(p[0], p[1], p[2], B, nb);
+        for (;;) {
+            if (k >= maxSteps) { st = 3; break; }
+            float q[3];
+            or_c2_rk4(f, N, h, p, q);
+            if (q[0] == p[0] && q[1] == p[1] && q[2] == p[2]) { st = 2; break; }
+            k++;
+            p[0] = q[0]; p[1] = q[1]; p[2] = q[2];
+            if (!(p[0] >= 0.0f && p[0] < (float)N && p[1] >= 0.0f && p[1] < (float)N && p[2] >= 0.0f &&
+                  p[2] < (float)N)) { st = 1; break; }
+            int32_t o = or_c0_owner(p[0], p[1], p[2], B, nb);
+            if (o != own) { hp++; own = o; }
+        }
+        pos[3 * i] = p[0]; pos[3 * i + 1] = p[1]; pos[3 * i + 2] = p[2];
+        steps[i] = k;
+        hops[i] = hp;
+        status[i] = st;
+    }
+}

@@ -118,3 +118,95 @@ def c0_camera(n: int = 64, width: int = 128, height: int = 128) -> np.ndarray:
     """The marching workload's camera: eye (n/2, n/2, -n), looking at the centre, +y up, 40 deg."""
     c = n / 2.0
     return camera((c, c, -float(n)), (c, c, c), (0.0, 1.0, 0.0), 40.0, width, height)
+
+
+# ---------------------------------------------------------------------------
+# Streamline workload: v = curl A, A = sum_m a_m sin(2 pi k_m . x / n + phi_m)
+# ---------------------------------------------------------------------------
+def c2_modes(nmodes: int = 32, seed: int = 2, kmax: float = 8.0):
+    """Integer wave vectors 1 <= |k| <= kmax, amplitudes a perpendicular to k, phases.
+
+    Uniforms from Philox(key={seed,3}, ctr={m, j, 0, 0}); a wave vector is redrawn
+    (j = 0, 2, 4, ...) until its length is in range.
+    """
+    ks, amps, phis = [], [], []
+    for m in range(nmodes):
+        j = 0
+        while True:
+            r = philox4x32_10(m, j, 0, 0, seed, 3)
+            k = np.array([int(r[i]) % 17 - 8 for i in range(3)], np.float64)
+            if 1.0 <= np.linalg.norm(k) <= kmax:
+                break
+            j += 2
+        r2 = philox4x32_10(m, j + 1, 0, 0, seed, 3)
+        u = np.array([float(r2[i]) / 4294967296.0 for i in range(4)])
+        v = u[:3] * 2.0 - 1.0
+        kh = k / np.linalg.norm(k)
+        a = v - v.dot(kh) * kh
+        if np.linalg.norm(a) < 1e-6:
+            a = np.cross(kh, [1.0, 0.0, 0.0]) if abs(kh[0]) < 0.9 else np.cross(kh, [0.0, 1.0, 0.0])
+        a = a / np.linalg.norm(a) * (0.5 + 0.5 * u[3])
+        ks.append(k)
+        amps.append(a)
+        phis.append(2.0 * math.pi * (float(r[3]) / 4294967296.0))
+    return np.array(ks), np.array(amps), np.array(phis)
+
+
+def c2_velocity_exact(p, n: int, modes=None, scale: float = 1.0) -> np.ndarray:
+    """The analytic (unscaled unless scale is given) field at points p (... x 3), float64."""
+    k, a, phi = c2_modes() if modes is None else modes
+    p = np.asarray(p, np.float64)
+    th = 2.0 * math.pi * (p @ k.T) / n + phi          # ... x m
+    w = (2.0 * math.pi / n) * np.cross(k, a)          # m x 3
+    return scale * (np.cos(th) @ w)
+
+
+def c2_field(n: int = 512, modes=None, zchunk: int = 16):
+    """n^3 x 3 float32 velocity at voxel centres, index [z, y, x, c], scaled so max |v| = 1.
+
+    Evaluated in float64 as a sum of separable complex exponentials (one GEMM per
+    slab of z), scaled by the largest voxel speed, then rounded to float32.
+    Returns (field, scale).
+    """
+    k, a, phi = c2_modes() if modes is None else modes
+    m = len(k)
+    x = (np.arange(n, dtype=np.float64) + 0.5) * (2.0 * math.pi / n)
+    ex = np.exp(1j * np.outer(k[:, 0], x))            # m x n
+    ey = np.exp(1j * np.outer(k[:, 1], x))
+    ez = np.exp(1j * np.outer(k[:, 2], x))
+    w = (2.0 * math.pi / n) * np.cross(k, a)          # m x 3
+    coef = np.exp(1j * phi)                           # m
+
+    def slab(z0, z1):
+        # A[(z, y), m] = coef_m ez[m, z] ey[m, y]; v_c = Re((A * w_c) @ ex)
+        zz = ez[:, z0:z1].T[:, None, :] * ey.T[None, :, :] * coef[None, None, :]   # dz x n x m
+        A = zz.reshape(-1, m)
+        out = np.empty((z1 - z0, n, n, 3), np.float64)
+        for c in range(3):
+            out[..., c] = (A * w[:, c][None, :]).dot(ex).real.reshape(z1 - z0, n, n)
+        return out
+
+    vmax = 0.0
+    for z0 in range(0, n, zchunk):
+        s = slab(z0, min(n, z0 + zchunk))
+        vmax = max(vmax, float(np.sqrt((s * s).sum(-1)).max()))
+    scale = 1.0 / vmax
+    field = np.empty((n, n, n, 3), np.float32)
+    for z0 in range(0, n, zchunk):
+        z1 = min(n, z0 + zchunk)
+        field[z0:z1] = (slab(z0, z1) * scale).astype(np.float32)
+    return field, scale
+
+
+def c2_seeds(count: int, n: int = 512, seed: int = 2, stream: int = 4) -> np.ndarray:
+    """count x 3 float32 seed points uniform in [0, n)^3 (Philox key {seed, stream})."""
+    i = np.arange(count, dtype=np.uint32)
+    z = np.zeros_like(i)
+    r = philox4x32_10(i, z, z, z, seed, stream)
+    pts = np.stack([r[0], r[1], r[2]], 1).astype(np.float64) / 4294967296.0 * n
+    return np.minimum(pts.astype(np.float32), np.float32(n) - np.float32(n) * np.float32(2**-24))
+
+
+def c2_seed_set_sizes(count: int = 16) -> list:
+    """Uneven batch: round(2^(12 + 8 k / 15)), k = 0 .. 15 (4096 .. 1048576)."""
+    return [int(round(2 ** (12 + 8 * k / (count - 1)))) for k in range(count)]

@@ -85,6 +85,11 @@ _SIGS = {
     "rf_c1_run_batched": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _u32, _P,
                           _PU64, _PU64, _P, _u32],
     "rf_c0_make_bricks": [_P, _i32, _i32, _P, _P],
+    "rf_c2_make_bricks": [_P, _i32, _i32, _P, _P],
+    "rf_c2_seed": [_P, _P, _P, _u64, _i32, _i32, _P],
+    "rf_c2_trace": [_P, _P, _i32, _i32, ctypes.c_float, _u32, _u32, _P, _u64, _P],
+    "rf_c2_run": [_P, _P, _P, _P, _u64, _i32, _i32, ctypes.c_float, _u32, _u32, _P, _i32, _u32, _P, _PU64,
+                  _PU64],
     "rf_c0_raygen": [_P, _P, _i32, _i32, _i32, _i32, _P, _P],
     "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
     "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
@@ -296,6 +301,34 @@ def rf_c0_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: 
                                               ptr(image), ptr(hop_log), max_hops, ptr(hop_count), max_rounds,
                                               stream_handle(stream), ctypes.byref(rounds)))
     return rounds.value
+
+
+RF_C2_EXITED, RF_C2_STALLED, RF_C2_MAXSTEPS = 1, 2, 3
+
+
+def rf_c2_make_bricks(field, n: int, brick: int, bricks, stream=None) -> None:
+    _check("rf_c2_make_bricks", lib().rf_c2_make_bricks(ptr(field), n, brick, ptr(bricks), stream_handle(stream)))
+
+
+def rf_c2_seed(ctx: int, seeds, set_ids, count: int, n: int, brick: int, stream=None) -> None:
+    _check("rf_c2_seed", lib().rf_c2_seed(ctx, ptr(seeds), ptr(set_ids), count, n, brick, stream_handle(stream)))
+
+
+def rf_c2_trace(ctx: int, bricks, n: int, brick: int, h: float, max_steps: int, steps_per_round: int, out,
+                out_capacity: int, stream=None) -> None:
+    _check("rf_c2_trace", lib().rf_c2_trace(ctx, ptr(bricks), n, brick, h, max_steps, steps_per_round, ptr(out),
+                                            out_capacity, stream_handle(stream)))
+
+
+def rf_c2_run(ctx: int, bricks, seeds, set_ids, count: int, n: int, brick: int, h: float, max_steps: int,
+              steps_per_round: int, out, batched: bool, max_rounds: int = 1 << 20, stream=None, allow=()):
+    """Whole streamline run; returns (status, rounds, forwarded)."""
+    rounds, fwd = ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib().rf_c2_run(ctx, ptr(bricks), ptr(seeds), ptr(set_ids), count, n, brick, h, max_steps,
+                         steps_per_round, ptr(out), int(batched), max_rounds, stream_handle(stream),
+                         ctypes.byref(rounds), ctypes.byref(fwd))
+    _check("rf_c2_run", st, allow)
+    return st, rounds.value, fwd.value
 
 
 class Context:
