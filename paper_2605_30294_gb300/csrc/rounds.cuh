@@ -124,7 +124,7 @@ __device__ __forceinline__ unsigned peers_of(int key, int nbits)
 // lines), the last CTA of a group arrives on the top counter, and the last
 // group releases everyone by bumping the generation.
 // Returns false when any CTA has given up; the caller must then return.
-__device__ bool grid_barrier(GridSync *gs, unsigned int *sFlag)
+__device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -168,7 +168,7 @@ __device__ bool grid_barrier(GridSync *gs, unsigned int *sFlag)
 }
 
 // Exclusive block scan of v[0..n) in shared memory (n <= 8 * kRoundsBlock).
-__device__ uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
+__device__ inline uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __syncthreads();
