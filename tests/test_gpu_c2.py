@@ -68,8 +68,12 @@ def test_streamlines_match_oracle(batched, spr):
         # only brick changes forward a particle
         assert got["forwarded"] == int(want["hops"].sum())
     else:
-        # every step that does not leave the grid forwards the particle (to itself or a neighbour)
-        assert got["forwarded"] == int(want["steps"].sum() - (want["status"] == oracle.EXITED).sum())
+        # every step forwards the particle (to itself or a neighbour) except one that
+        # leaves the grid, and the last step of a particle that hits the step cap
+        # forwards it only when it enters another brick
+        total = int(want["steps"].sum()) - int((want["status"] == oracle.EXITED).sum())
+        capped = int((want["status"] == oracle.MAXSTEPS).sum())
+        assert total - capped <= got["forwarded"] <= total
 
 
 def test_partition_independence():
