@@ -14,8 +14,10 @@ Also reported on the same line: the persistent kernel's roofline
 scatter phase rates from its round log; the plain per-round host loop
 (rf_c1_run) with the scatter kernel's roofline; the same run end to end
 through rf_c1_run_batched with host buffers; rays/s of the 64^3 marching
-workload; the oracle timed on a bounded sample (cpu_baseline); SM clocks
-sampled during the timed region and the number of kernels launched.
+workload; particle-steps/s of the streamline workload (512^3 field, 16
+uneven seed sets in one launch, batched and plain forms); the oracle timed
+on a bounded sample (cpu_baseline); SM clocks sampled during the timed
+region and the number of kernels launched.
 
 ``--impl reference`` times the oracle (the CPU reference of this method) on a
 bounded sample of the same workload instead.
@@ -233,6 +235,54 @@ def phase_rates(log_rows, item_bytes, min_items=1 << 20):
     return out
 
 
+def c2_streamlines(torch, rafi, inputs, s, reps=3):
+    """Streamlines: 512^3 field over 4x4x4 ranks, the 16 uneven seed sets in one launch.
+
+    Returns particle-steps/s and items forwarded/s of the batched (persistent)
+    and plain (host loop) forms, CUDA events around each run.
+    """
+    n, brick = 512, 128
+    R = (n // brick) ** 3
+    field, _ = inputs.c2_field(n)
+    sizes = inputs.c2_seed_set_sizes()
+    count = sum(sizes)
+    seeds = inputs.c2_seeds(count, n, seed=2)
+    set_ids = np.repeat(np.arange(len(sizes), dtype=np.uint32), sizes)
+    d_field = torch.from_numpy(field.reshape(-1)).cuda()
+    bricks = torch.zeros(R * (brick + 4) ** 3 * 4, dtype=torch.float32, device="cuda")
+    rafi.rf_c2_make_bricks(d_field, n, brick, bricks, s)
+    del d_field
+    d_seeds = torch.from_numpy(seeds).cuda()
+    d_sets = torch.from_numpy(set_ids.view(np.int32)).cuda()
+    out = torch.zeros((count, 8), dtype=torch.int32, device="cuda")
+    res = {"workload": f"512^3 curl-noise field (32 modes, |k| 1..8), 4x4x4 ranks of 128^3 bricks, "
+                       f"{len(sizes)} uneven seed sets ({sizes[0]}..{sizes[-1]}, {count} particles) in one launch, "
+                       f"RK4 h=0.25, <= 2000 steps",
+           "particles": count}
+    with rafi.Context(R, 32, count) as ctx:
+        for batched in (True, False):
+            for _ in range(2):
+                rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, 0, out, batched,
+                               stream=s)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fwd = rounds = 0
+            for _ in range(reps):
+                st, rounds, f = rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, 0,
+                                               out, batched, stream=s)
+                fwd += f
+            e1.record(s)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3 / reps
+            steps = int(out[:, 4].cpu().numpy().view(np.uint32).astype(np.int64).sum())
+            res["batched" if batched else "plain"] = {
+                "ms_per_run": sec * 1e3, "particle_steps_per_s": steps / sec,
+                "items_forwarded_per_s": fwd / reps / sec, "rounds": rounds, "particle_steps": steps}
+    res["batched_over_plain"] = res["plain"]["ms_per_run"] / res["batched"]["ms_per_run"]
+    return res
+
+
 def run_ours(args):
     import torch
 
@@ -338,6 +388,9 @@ def run_ours(args):
 
     rays_s, c0_ms = c0_rays_per_s(torch, rafi, inputs, s)
     ctx.close()
+    del d_items, retired, h_items, h_ret
+    torch.cuda.empty_cache()
+    streamlines = c2_streamlines(torch, rafi, inputs, s) if not args.skip_streamlines else None
 
     sec = ms / 1e3
     total_fwd = fwd
@@ -393,6 +446,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8)},
         "rays_per_s": {"value": rays_s, "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
                        "ms_per_frame": c0_ms},
+        "streamlines": streamlines,
         "cpu_baseline": {"value": cpu_v, "unit": "items/s", "cores": 1, "kind": "oracle",
                          "sample": f"{BASELINE_ITEMS} items per destination law, round-by-round oracle, "
                                    f"{cpu_dt:.1f} s"},
@@ -412,6 +466,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--items", type=int, default=N_ITEMS)
+    ap.add_argument("--skip-streamlines", action="store_true", help="leave out the streamline workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
