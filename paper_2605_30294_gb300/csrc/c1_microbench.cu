@@ -163,6 +163,8 @@ __global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
 struct C1Work {
     static constexpr int V = 4;
     static constexpr bool kAppendRetired = true;
+    static constexpr bool kDynamicWork = false;
+    static constexpr int kMinBlocksPerSM = 3;
     const uint32_t *zipfThr;
     uint32_t seed;
     int32_t mode, gx, gy, gz, R;

@@ -160,6 +160,8 @@ __device__ __forceinline__ void c2_write_out(const C2Params &P, const uint4 (&w)
 struct C2Work {
     static constexpr int V = 2;
     static constexpr bool kAppendRetired = false;
+    static constexpr bool kDynamicWork = true;
+    static constexpr int kMinBlocksPerSM = 4;
     C2Params P;
     __host__ __device__ uint32_t smemBytes() const { return 0u; }
     __device__ void load_smem(void *) const {}

@@ -40,7 +40,8 @@ struct GridSync {
     unsigned int count;  // groups complete at the current barrier
     unsigned int gen;    // barrier generation
     unsigned int abort;  // set by a CTA whose wait gave up
-    unsigned int pad[29];
+    unsigned int work[2];  // work-phase chunk counters (round parity), dynamic policies
+    unsigned int pad[27];
     unsigned int group[kSyncGroups][32];  // CTAs arrived per group, one 128-byte line each
 };
 
@@ -247,13 +248,16 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
 //   static constexpr int V;               16-byte vectors per item
 //   static constexpr bool kAppendRetired; retired items go, stably, to the
 //                                         retirement sink (else: retire())
+//   static constexpr bool kDynamicWork;   long, uneven per-item work: the work
+//                                         phase hands out chunks dynamically
+//   static constexpr int kMinBlocksPerSM; resident CTAs per SM to compile for
 //   uint32_t smemBytes() const;           its own shared memory
 //   void load_smem(void *s) const;        fill it (all threads; a barrier follows)
 //   int32_t step(uint4 (&w)[V], int32_t rank, uint32_t round, const void *s) const;
 //       advances one item: returns the destination rank (w updated) or -1 to retire
 //   void retire(const uint4 (&w)[V]) const;  (used when !kAppendRetired)
 template <class W>
-__global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W work)
+__global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kernel(RoundsArgs a, W work)
 {
     constexpr int V = W::V;
     constexpr uint32_t kItemBytes = 16u * V;
@@ -369,11 +373,43 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
         const uint32_t nt = (hi - lo + kRoundsTile - 1) / kRoundsTile;
 
         // ---- phase 1: work step, write back to the same slots ------------------
-        if (tid == 0 && nt) {
+        // Policies with long, uneven per-item work (W::kDynamicWork) take
+        // 32-item chunks from a round counter instead of a fixed range; each
+        // CTA then counts its own range's destinations after the barrier.
+        const bool dynamic = W::kDynamicWork && !solo;
+        if (dynamic) {
+            unsigned int *ticket = &a.sync->work[round & 1u];
+            for (;;) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(ticket, 32u);
+                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (base >= n) break;
+                const uint32_t i = base + lane;
+                if (i < n) {
+                    uint4 w[V];
+#pragma unroll
+                    for (int q = 0; q < V; ++q) w[q] = __ldcg(a.in + (size_t)i * V + q);
+                    int32_t d = work.step(w, rf::rankOf(sOff, R, i), round, sWork);
+                    if (d >= 0) {
+#pragma unroll
+                        for (int q = 0; q < V; ++q) a.out[(size_t)i * V + q] = w[q];
+                    } else if (W::kAppendRetired) {
+#pragma unroll
+                        for (int q = 0; q < V; ++q) a.out[(size_t)i * V + q] = w[q];
+                        d = R;
+                    } else {
+                        work.retire(w);
+                    }
+                    a.dest[i] = d;
+                }
+            }
+            if (c == 0 && tid == 0) a.sync->work[(round + 1u) & 1u] = 0u;  // next round's counter
+        }
+        if (!dynamic && tid == 0 && nt) {
             const uint32_t cnt0 = min(kRoundsTile, hi - lo);
             issue_bytes(0, sBuf, a.in + (size_t)lo * V, cnt0 * kItemBytes, nullptr, nullptr, 0u);
         }
-        for (uint32_t t = 0; t < nt; ++t) {
+        for (uint32_t t = 0; !dynamic && t < nt; ++t) {
             const int buf = t & 1;
             const uint32_t b = lo + t * kRoundsTile;
             const uint32_t cnt = min(kRoundsTile, hi - b);
@@ -419,6 +455,22 @@ __global__ void __launch_bounds__(kRoundsBlock, 3) rounds_kernel(RoundsArgs a, W
         }
         if (tid == 0) bulk_wait_all();
         if (logRound) a.roundLog[7 * round + 1] = globaltimer();
+        if (dynamic) {
+            fence_proxy_async_global();
+            if (!round_barrier()) {
+                failed = true;
+                break;
+            }
+            // count the destinations of this CTA's range
+            for (uint32_t b = lo; b < hi; b += kRoundsBlock) {
+                const uint32_t i = b + tid;
+                const int32_t d = i < hi ? __ldcg(a.dest + i) : -1;
+                const int key = (uint32_t)d < (uint32_t)D ? d : D;
+                const unsigned peers = peers_of(key, nbits);
+                if (key < D && lane == __ffs(peers) - 1) atomicAdd(&sTot[key], (uint32_t)__popc(peers));
+            }
+            __syncthreads();
+        }
         if (!failed) {
             for (int e = tid; e < D; e += kRoundsBlock) {
                 const uint32_t v = sTot[e];
