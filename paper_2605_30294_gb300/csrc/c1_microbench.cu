@@ -165,6 +165,7 @@ struct C1Work {
     static constexpr bool kAppendRetired = true;
     static constexpr bool kDynamicWork = false;
     static constexpr int kMinBlocksPerSM = 3;
+    static constexpr int kItemsPerThread = 2;
     const uint32_t *zipfThr;
     uint32_t seed;
     int32_t mode, gx, gy, gz, R;

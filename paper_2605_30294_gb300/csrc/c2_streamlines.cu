@@ -162,6 +162,7 @@ struct C2Work {
     static constexpr bool kAppendRetired = false;
     static constexpr bool kDynamicWork = true;
     static constexpr int kMinBlocksPerSM = 4;
+    static constexpr int kItemsPerThread = 1;
     C2Params P;
     __host__ __device__ uint32_t smemBytes() const { return 0u; }
     __device__ void load_smem(void *) const {}

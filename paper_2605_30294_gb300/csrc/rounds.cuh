@@ -222,20 +222,21 @@ __host__ __device__ inline uint32_t rounds_align(uint32_t x, uint32_t a) { retur
 // per-CTA count rows in phase 2.  dests: the tiles' destinations.  D =
 // destination digits (ranks, plus one retirement digit when the policy
 // appends retired items).
-__host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D, uint32_t workBytes)
+__host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D, uint32_t workBytes,
+                                                  uint32_t tile = kRoundsTile)
 {
     RoundsLayout L;
     uint32_t o = 0;
-    L.items = o;   o = rounds_align(o + 2u * kRoundsTile * itemBytes, 128);
-    L.dests = o;   o = rounds_align(o + 2u * (kRoundsTile + 4u) * 4u, 16);
+    L.items = o;   o = rounds_align(o + 2u * tile * itemBytes, 128);
+    L.dests = o;   o = rounds_align(o + 2u * (tile + 4u) * 4u, 16);
     L.wc = o;      o = rounds_align(o + kRoundsWarps * D * 4u, 16);
     L.cnt = o;     o = rounds_align(o + D * 4u, 16);
     L.start = o;   o = rounds_align(o + D * 4u, 16);
     L.base = o;    o = rounds_align(o + D * 4u, 16);
     L.tot = o;     o = rounds_align(o + D * 4u, 16);
     L.off = o;     o = rounds_align(o + (D + 1) * 4u, 16);
-    L.slotSrc = o; o = rounds_align(o + kRoundsTile * 2u, 16);
-    L.slotDst = o; o = rounds_align(o + kRoundsTile * 4u, 16);
+    L.slotSrc = o; o = rounds_align(o + tile * 2u, 16);
+    L.slotDst = o; o = rounds_align(o + tile * 4u, 16);
     L.tmp = o;     o = rounds_align(o + (kRoundsWarps + 1) * 4u, 16);
     L.flag = o;    o = rounds_align(o + 4u, 16);
     L.bar = o;     o = rounds_align(o + 16u, 16);
@@ -251,6 +252,7 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
 //   static constexpr bool kDynamicWork;   long, uneven per-item work: the work
 //                                         phase hands out chunks dynamically
 //   static constexpr int kMinBlocksPerSM; resident CTAs per SM to compile for
+//   static constexpr int kItemsPerThread; tile = 256 x this many items
 //   uint32_t smemBytes() const;           its own shared memory
 //   void load_smem(void *s) const;        fill it (all threads; a barrier follows)
 //   int32_t step(uint4 (&w)[V], int32_t rank, uint32_t round, const void *s) const;
@@ -261,16 +263,18 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
 {
     constexpr int V = W::V;
     constexpr uint32_t kItemBytes = 16u * V;
-    constexpr uint32_t kTileVecs = kRoundsTile * V;
+    constexpr int kK = W::kItemsPerThread;  // items per thread per tile
+    constexpr uint32_t kTile = kRoundsBlock * kK;
+    constexpr uint32_t kTileVecs = kTile * V;
     constexpr uint32_t kRetFlag = 0x80000000u;
     extern __shared__ __align__(128) unsigned char smem[];
     const int R = a.numRanks;
     const int D = R + (W::kAppendRetired ? 1 : 0);  // digits: ranks (+ retirement)
     const int Dp = rounds_row_stride(D);
-    const RoundsLayout L = rounds_layout(kItemBytes, D, work.smemBytes());
+    const RoundsLayout L = rounds_layout(kItemBytes, D, work.smemBytes(), kTile);
     uint4 *sBuf = reinterpret_cast<uint4 *>(smem + L.items);  // two tiles of kTileVecs
     uint32_t *sRows = reinterpret_cast<uint32_t *>(smem + L.items);
-    int32_t *sDst = reinterpret_cast<int32_t *>(smem + L.dests);  // two tiles of kRoundsTile + 4
+    int32_t *sDst = reinterpret_cast<int32_t *>(smem + L.dests);  // two tiles of kTile + 4
     uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
     uint32_t *dCnt = reinterpret_cast<uint32_t *>(smem + L.cnt);
     uint32_t *dStart = reinterpret_cast<uint32_t *>(smem + L.start);
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     };
     // Once a round is this small, CTA 0 finishes the run alone: the other CTAs
     // return and the round barriers become block barriers.
-    constexpr uint32_t kSoloItems = 2u * kRoundsTile;
+    constexpr uint32_t kSoloItems = 2u * kTile;
     bool solo = false;
     auto round_barrier = [&]() -> bool {
         if (!solo) return grid_barrier(a.sync, sFlag);
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         __syncthreads();
         const uint32_t lo = bound(n, c, g);
         const uint32_t hi = bound(n, c + 1, g);
-        const uint32_t nt = (hi - lo + kRoundsTile - 1) / kRoundsTile;
+        const uint32_t nt = (hi - lo + kTile - 1) / kTile;
 
         // ---- phase 1: work step, write back to the same slots ------------------
         // Policies with long, uneven per-item work (W::kDynamicWork) take
@@ -406,18 +410,18 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             if (c == 0 && tid == 0) a.sync->work[(round + 1u) & 1u] = 0u;  // next round's counter
         }
         if (!dynamic && tid == 0 && nt) {
-            const uint32_t cnt0 = min(kRoundsTile, hi - lo);
+            const uint32_t cnt0 = min(kTile, hi - lo);
             issue_bytes(0, sBuf, a.in + (size_t)lo * V, cnt0 * kItemBytes, nullptr, nullptr, 0u);
         }
         for (uint32_t t = 0; !dynamic && t < nt; ++t) {
             const int buf = t & 1;
-            const uint32_t b = lo + t * kRoundsTile;
-            const uint32_t cnt = min(kRoundsTile, hi - b);
+            const uint32_t b = lo + t * kTile;
+            const uint32_t cnt = min(kTile, hi - b);
             if (tid == 0 && t + 1 < nt) {
                 bulk_wait_read();  // the store of tile t-1 has left buffer buf^1
-                const uint32_t nb = b + kRoundsTile;
+                const uint32_t nb = b + kTile;
                 issue_bytes(buf ^ 1, sBuf + (buf ^ 1) * kTileVecs, a.in + (size_t)nb * V,
-                            min(kRoundsTile, hi - nb) * kItemBytes, nullptr, nullptr, 0u);
+                            min(kTile, hi - nb) * kItemBytes, nullptr, nullptr, 0u);
             }
             if (!wait(buf)) {
                 failed = true;
@@ -425,7 +429,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             }
             uint4 *sItems = sBuf + buf * kTileVecs;
 #pragma unroll
-            for (int k = 0; k < kRoundsK; ++k) {
+            for (int k = 0; k < kK; ++k) {
                 const uint32_t j = (uint32_t)(k * kRoundsBlock + tid);
                 const bool valid = j < cnt;
                 int32_t d = -1;
@@ -527,27 +531,27 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
 
         // ---- phase 3: stable scatter of this CTA's range -----------------------
         auto issue3 = [&](int buf, uint32_t bb) {
-            const uint32_t cc = min(kRoundsTile, hi - bb);
+            const uint32_t cc = min(kTile, hi - bb);
             issue_bytes(buf, sBuf + buf * kTileVecs, a.out + (size_t)bb * V, cc * kItemBytes,
-                        sDst + buf * (kRoundsTile + 4u), a.dest + bb, ((cc + 3u) & ~3u) * 4u);
+                        sDst + buf * (kTile + 4u), a.dest + bb, ((cc + 3u) & ~3u) * 4u);
         };
         if (tid == 0 && nt && !failed) issue3(0, lo);
         for (uint32_t t = 0; t < nt && !failed; ++t) {
             const int buf = t & 1;
-            const uint32_t b = lo + t * kRoundsTile;
-            const uint32_t cnt = min(kRoundsTile, hi - b);
-            if (tid == 0 && t + 1 < nt) issue3(buf ^ 1, b + kRoundsTile);
+            const uint32_t b = lo + t * kTile;
+            const uint32_t cnt = min(kTile, hi - b);
+            if (tid == 0 && t + 1 < nt) issue3(buf ^ 1, b + kTile);
             for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
             if (!wait(buf)) {
                 failed = true;
                 break;
             }
-            const int32_t *dts = sDst + buf * (kRoundsTile + 4u);
-            int myD[kRoundsK];
-            uint32_t myR[kRoundsK];
+            const int32_t *dts = sDst + buf * (kTile + 4u);
+            int myD[kK];
+            uint32_t myR[kK];
 #pragma unroll
-            for (int k = 0; k < kRoundsK; ++k) {
-                const uint32_t idx = (uint32_t)(warp * 32 * kRoundsK + k * 32 + lane);
+            for (int k = 0; k < kK; ++k) {
+                const uint32_t idx = (uint32_t)(warp * 32 * kK + k * 32 + lane);
                 const int32_t d = idx < cnt ? dts[idx] : -1;
                 const bool valid = (uint32_t)d < (uint32_t)D;
                 const int key = valid ? d : D;
@@ -577,12 +581,12 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             }
             const uint32_t nValid = rounds_block_scan(dStart, D, tmp);
 #pragma unroll
-            for (int k = 0; k < kRoundsK; ++k) {
+            for (int k = 0; k < kK; ++k) {
                 if (myD[k] >= 0) {
                     const int d = myD[k];
                     const uint32_t within = wc[warp * D + d] + myR[k];
                     const uint32_t slot = dStart[d] + within;
-                    slotSrc[slot] = (uint16_t)(warp * 32 * kRoundsK + k * 32 + lane);
+                    slotSrc[slot] = (uint16_t)(warp * 32 * kK + k * 32 + lane);
                     slotDst[slot] = (dBase[d] + within) | (W::kAppendRetired && d == R ? kRetFlag : 0u);
                 }
             }
@@ -647,7 +651,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         set_error("persistent rounds: %d destinations exceed %d", D, 8 * kRoundsBlock);
         return RF_ERR_ARG;
     }
-    const RoundsLayout L = rounds_layout(itemBytes, D, work.smemBytes());
+    const RoundsLayout L = rounds_layout(itemBytes, D, work.smemBytes(), kRoundsBlock * W::kItemsPerThread);
     int optin = 0;
     RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     auto fn = rounds_kernel<W>;
