@@ -260,26 +260,31 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3):
                        f"RK4 h=0.25, <= 2000 steps",
            "particles": count}
     with rafi.Context(R, 32, count) as ctx:
-        for batched in (True, False):
-            for _ in range(2):
-                rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, 0, out, batched,
-                               stream=s)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            fwd = rounds = 0
-            for _ in range(reps):
-                st, rounds, f = rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, 0,
-                                               out, batched, stream=s)
-                fwd += f
-            e1.record(s)
-            torch.cuda.synchronize()
-            sec = e0.elapsed_time(e1) / 1e3 / reps
-            steps = int(out[:, 4].cpu().numpy().view(np.uint32).astype(np.int64).sum())
-            res["batched" if batched else "plain"] = {
-                "ms_per_run": sec * 1e3, "particle_steps_per_s": steps / sec,
-                "items_forwarded_per_s": fwd / reps / sec, "rounds": rounds, "particle_steps": steps}
-    res["batched_over_plain"] = res["plain"]["ms_per_run"] / res["batched"]["ms_per_run"]
+        # steps per round: 0 = until a particle leaves its brick; 1 = the paper's
+        # pattern (one RK step per round, every particle forwarded every round)
+        for spr, nrep in ((0, reps), (1, 1)):
+            key = "brick_exit" if spr == 0 else "one_step_per_round"
+            res[key] = {}
+            for batched in (True, False):
+                for _ in range(2 if spr == 0 else 1):
+                    rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, spr, out,
+                                   batched, stream=s)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                fwd = rounds = 0
+                for _ in range(nrep):
+                    st, rounds, f = rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000,
+                                                   spr, out, batched, stream=s)
+                    fwd += f
+                e1.record(s)
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) / 1e3 / nrep
+                steps = int(out[:, 4].cpu().numpy().view(np.uint32).astype(np.int64).sum())
+                res[key]["batched" if batched else "plain"] = {
+                    "ms_per_run": sec * 1e3, "particle_steps_per_s": steps / sec,
+                    "items_forwarded_per_s": fwd / nrep / sec, "rounds": rounds, "particle_steps": steps}
+            res[key]["batched_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["batched"]["ms_per_run"]
     return res
 
 

@@ -161,7 +161,7 @@ struct C2Work {
     static constexpr int V = 2;
     static constexpr bool kAppendRetired = false;
     static constexpr bool kDynamicWork = true;
-    static constexpr int kMinBlocksPerSM = 4;
+    static constexpr int kMinBlocksPerSM = 3;
     static constexpr int kItemsPerThread = 1;
     C2Params P;
     __host__ __device__ uint32_t smemBytes() const { return 0u; }
