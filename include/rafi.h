@@ -338,6 +338,32 @@ rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const 
                     int32_t N, int32_t B, float h, uint32_t maxSteps, uint32_t stepsPerRound, void *out,
                     int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded);
 
+/* --- differentiable emission-absorption rendering (64-byte rays) ---------- */
+
+/* Forward render through bricks made by rf_c0_make_bricks (halo 1): spp
+ * jittered rays per pixel of a W x H camera cam (host, 12 floats), sample s
+ * of pixel p aiming at (x + u, y + v) with u, v the top 24 bits of words 0
+ * and 1 of Philox4x32-10(key {seed, 5}, counter {p, s, 0, 0}) / 2^24.
+ * Samples at t0 + (k + 0.5) * 0.5; per sample e = expf(-sigma/2), alpha =
+ * 1 - e, c = 20 sigma, C += (T alpha) c, T *= e (the Lander renderer's
+ * emission-absorption model, Sec. 5.2, each ray carrying C and T across
+ * bricks).  rayC (device, W*H*spp) receives every sample's C, image (device,
+ * W*H) the mean over a pixel's samples. */
+rf_status rf_c3_render(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W, int32_t H,
+                       int32_t spp, uint32_t seed, float *rayC, float *image, uint32_t maxRounds, void *stream,
+                       uint64_t *rounds);
+
+/* Adjoint of rf_c3_render: given rayC from the forward call and gradImage =
+ * dL/dimage (device, W*H), adds dL/dsigma to gradVolume (device, N^3, x
+ * fastest; the caller zeroes it).  Adjoint rays carry their forward C and
+ * dL/dC (= gradImage / spp) through the same bricks, recompute T and the
+ * running sum per brick, and scatter dC/dsigma_k = T_k (0.5 e_k c_k + 20
+ * alpha_k) - 0.5 (C - sum_{j<=k} T_j alpha_j c_j) with the trilinear weights
+ * (atomic adds: the summation order, not the value, depends on scheduling). */
+rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W,
+                        int32_t H, int32_t spp, uint32_t seed, const float *rayC, const float *gradImage,
+                        float *gradVolume, uint32_t maxRounds, void *stream, uint64_t *rounds);
+
 #ifdef __cplusplus
 }
 #endif

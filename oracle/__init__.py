@@ -70,6 +70,10 @@ def _load():
             lib.or_c2_velocity.restype = None
             lib.or_c2_trace.argtypes = [P, i32, i32, P, u64, ctypes.c_float, u32, P, P, P, P]
             lib.or_c2_trace.restype = None
+            lib.or_c3_render.argtypes = [P, i32, P, i32, i32, i32, u32, P, P]
+            lib.or_c3_render.restype = None
+            lib.or_c3_adjoint_f64.argtypes = [P, i32, P, i32, i32, i32, u32, P, P]
+            lib.or_c3_adjoint_f64.restype = f64
             _lib = lib
     return _lib
 
@@ -262,3 +266,27 @@ def c2_trace(field: np.ndarray, seeds: np.ndarray, brick: int, h: float = 0.25, 
     _load().or_c2_trace(_p(field), field.shape[0], brick, _p(seeds), n, h, max_steps, _p(pos), _p(steps),
                         _p(hops), _p(status))
     return dict(pos=pos, steps=steps, hops=hops, status=status)
+
+
+# --------------------------------------------------------------------------
+# Differentiable emission-absorption rendering (Sec. 5.2's integration model)
+# --------------------------------------------------------------------------
+def c3_render(vol: np.ndarray, cam: np.ndarray, width: int, height: int, spp: int, seed: int = 3):
+    """Float forward render: returns (image W*H, per-sample C W*H*spp)."""
+    vol = _c(vol, np.float32)
+    cam = _c(cam, np.float32)
+    rayC = np.zeros(width * height * spp, np.float32)
+    image = np.zeros(width * height, np.float32)
+    _load().or_c3_render(_p(vol), vol.shape[0], _p(cam), width, height, spp, seed, _p(rayC), _p(image))
+    return image, rayC
+
+
+def c3_adjoint_f64(vol: np.ndarray, cam: np.ndarray, width: int, height: int, spp: int, dLdC: np.ndarray,
+                   seed: int = 3):
+    """Reference gradient dL/dvol (float64, N^3) for per-sample dL/dC (W*H*spp)."""
+    vol = _c(vol, np.float32)
+    cam = _c(cam, np.float32)
+    g = _c(dLdC, np.float64)
+    grad = np.zeros(vol.shape, np.float64)
+    acc = _load().or_c3_adjoint_f64(_p(vol), vol.shape[0], _p(cam), width, height, spp, seed, _p(g), _p(grad))
+    return grad, acc

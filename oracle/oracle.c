@@ -515,3 +515,165 @@ void or_c2_trace(const float *f, int32_t N, int32_t B, const float *seeds, uint6
         status[i] = st;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Differentiable emission-absorption rendering through the same kind of    */
+/* density grid (the Lander renderer's integration model, Sec. 5.2, on a    */
+/* structured grid).                                                        */
+/*                                                                          */
+/* spp jittered primary rays per pixel: sample s of pixel p = y*W + x       */
+/* aims at (x + u, y + v), u = hi24(r0) / 2^24, v = hi24(r1) / 2^24 with    */
+/* r = Philox4x32-10(key {seed, 5}, counter {p, s, 0, 0}).                  */
+/* Samples t_k = t0 + (k + 0.5) * 0.5 while t_k < t1 (as in the marching    */
+/* workload).  With sigma_k = sigma(p_k):                                   */
+/*   e_k = expf(-sigma_k * 0.5), alpha_k = 1 - e_k, c_k = sigma_k * 20      */
+/*   C += (T * alpha_k) * c_k;  T = T * e_k        (T starts at 1, C at 0)  */
+/* The pixel value is the mean of its samples' C.                            */
+/* ------------------------------------------------------------------------ */
+static float or_u24(uint32_t r) { return (float)(r >> 8) * (1.0f / 16777216.0f); }
+
+/* direction and box interval of sample s of pixel (x, y); 1 if it has a sample */
+static int32_t or_c3_ray(const float *cam, int32_t N, int32_t W, int32_t x, int32_t y, int32_t s, uint32_t seed,
+                         float *dir, float *t0out, float *t1out)
+{
+    uint32_t ctr[4] = {(uint32_t)(y * W + x), (uint32_t)s, 0u, 0u};
+    uint32_t key[2] = {seed, 5u};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    float px = (float)x + or_u24(r[0]), py = (float)y + or_u24(r[1]);
+    float d[3];
+    for (int a = 0; a < 3; ++a) d[a] = cam[3 + a] + cam[6 + a] * px + cam[9 + a] * py;
+    float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; ++a) d[a] = d[a] / len;
+    float tn[3], tf[3];
+    for (int a = 0; a < 3; ++a) {
+        float ta = (0.0f - cam[a]) / d[a];
+        float tb = ((float)N - cam[a]) / d[a];
+        tn[a] = fminf(ta, tb);
+        tf[a] = fmaxf(ta, tb);
+    }
+    float t0 = fmaxf(fmaxf(fmaxf(tn[0], tn[1]), tn[2]), 0.0f);
+    float t1 = fminf(fminf(tf[0], tf[1]), tf[2]);
+    for (int a = 0; a < 3; ++a) dir[a] = d[a];
+    *t0out = t0;
+    *t1out = t1;
+    return (t0 + 0.5f * 0.5f) < t1 ? 1 : 0;
+}
+
+/* Forward render (float, written order).  rayC[(p*spp + s)] = C of each
+ * sample, image[p] = their mean (sum in sample order, then / spp). */
+void or_c3_render(const float *vol, int32_t N, const float *cam, int32_t W, int32_t H, int32_t spp, uint32_t seed,
+                  float *rayC, float *image)
+{
+    for (int32_t y = 0; y < H; ++y) {
+        for (int32_t x = 0; x < W; ++x) {
+            int32_t pix = y * W + x;
+            float sum = 0.0f;
+            for (int32_t s = 0; s < spp; ++s) {
+                float dir[3], t0, t1;
+                float T = 1.0f, C = 0.0f;
+                if (or_c3_ray(cam, N, W, x, y, s, seed, dir, &t0, &t1)) {
+                    for (int32_t k = 0;; ++k) {
+                        float tk = t0 + ((float)k + 0.5f) * 0.5f;
+                        if (!(tk < t1)) break;
+                        float px = cam[0] + dir[0] * tk, py = cam[1] + dir[1] * tk, pz = cam[2] + dir[2] * tk;
+                        float sg = or_c0_sample(vol, N, px, py, pz);
+                        float e = expf(-(sg * 0.5f));
+                        float al = 1.0f - e;
+                        float cc = sg * 20.0f;
+                        C = C + (T * al) * cc;
+                        T = T * e;
+                    }
+                }
+                rayC[(size_t)pix * spp + s] = C;
+                sum = sum + C;
+            }
+            image[pix] = sum / (float)spp;
+        }
+    }
+}
+
+/* Reference gradient, in double: dL/dvol given dLdC per sample ray
+ * ((p*spp + s) order).  Every quantity is recomputed in double from the
+ * float volume (sigma by trilinear interpolation in double, positions from
+ * the float ray).  Per ray: forward to collect sigma_k, T_k, alpha_k, c_k;
+ * then k from last to first with the suffix S = sum_{j>k} T_j alpha_j c_j:
+ *   dC/dsigma_k = T_k (0.5 e_k c_k + alpha_k * 20) - 0.5 S,
+ * scattered to the 8 voxels with the trilinear weights (clamped taps add).
+ * Returns the loss-independent sum of dLdC * C (a consistency value). */
+double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t W, int32_t H, int32_t spp,
+                         uint32_t seed, const double *dLdC, double *grad)
+{
+    int32_t maxK = (int32_t)(2.0f * 1.7321f * (float)N) + 8;
+    double *sg = (double *)malloc((size_t)maxK * sizeof(double));
+    double *Tk = (double *)malloc((size_t)maxK * sizeof(double));
+    float *pk = (float *)malloc((size_t)maxK * 3 * sizeof(float));
+    double acc = 0.0;
+    for (int32_t y = 0; y < H; ++y) {
+        for (int32_t x = 0; x < W; ++x) {
+            int32_t pix = y * W + x;
+            for (int32_t s = 0; s < spp; ++s) {
+                double g = dLdC[(size_t)pix * spp + s];
+                float dir[3], t0, t1;
+                if (!or_c3_ray(cam, N, W, x, y, s, seed, dir, &t0, &t1)) continue;
+                int32_t K = 0;
+                double T = 1.0, C = 0.0;
+                for (;; ++K) {
+                    float tk = t0 + ((float)K + 0.5f) * 0.5f;
+                    if (!(tk < t1) || K >= maxK) break;
+                    float p[3] = {cam[0] + dir[0] * tk, cam[1] + dir[1] * tk, cam[2] + dir[2] * tk};
+                    /* trilinear in double */
+                    double w[3];
+                    int32_t i0[3], i1[3];
+                    for (int a = 0; a < 3; ++a) {
+                        double u = (double)p[a] - 0.5, fl = floor(u);
+                        w[a] = u - fl;
+                        int32_t lo = (int32_t)fl, hi = lo + 1;
+                        i0[a] = lo < 0 ? 0 : (lo > N - 1 ? N - 1 : lo);
+                        i1[a] = hi < 0 ? 0 : (hi > N - 1 ? N - 1 : hi);
+                    }
+                    double v = 0.0;
+                    for (int c = 0; c < 8; ++c) {
+                        int32_t ix = (c & 1) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 4) ? i1[2] : i0[2];
+                        double wt = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
+                                    ((c & 4) ? w[2] : 1.0 - w[2]);
+                        v += wt * (double)vol[((size_t)iz * N + iy) * N + ix];
+                    }
+                    sg[K] = v;
+                    Tk[K] = T;
+                    pk[3 * K] = p[0]; pk[3 * K + 1] = p[1]; pk[3 * K + 2] = p[2];
+                    double e = exp(-v * 0.5);
+                    C += T * (1.0 - e) * (v * 20.0);
+                    T *= e;
+                }
+                acc += g * C;
+                double S = 0.0;
+                for (int32_t k = K - 1; k >= 0; --k) {
+                    double e = exp(-sg[k] * 0.5), al = 1.0 - e, cc = sg[k] * 20.0;
+                    double dCds = Tk[k] * (0.5 * e * cc + al * 20.0) - 0.5 * S;
+                    S += Tk[k] * al * cc;
+                    double gs = g * dCds;
+                    double w[3];
+                    int32_t i0[3], i1[3];
+                    for (int a = 0; a < 3; ++a) {
+                        double u = (double)pk[3 * k + a] - 0.5, fl = floor(u);
+                        w[a] = u - fl;
+                        int32_t lo = (int32_t)fl, hi = lo + 1;
+                        i0[a] = lo < 0 ? 0 : (lo > N - 1 ? N - 1 : lo);
+                        i1[a] = hi < 0 ? 0 : (hi > N - 1 ? N - 1 : hi);
+                    }
+                    for (int c = 0; c < 8; ++c) {
+                        int32_t ix = (c & 1) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 4) ? i1[2] : i0[2];
+                        double wt = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
+                                    ((c & 4) ? w[2] : 1.0 - w[2]);
+                        grad[((size_t)iz * N + iy) * N + ix] += gs * wt;
+                    }
+                }
+            }
+        }
+    }
+    free(sg);
+    free(Tk);
+    free(pk);
+    return acc;
+}

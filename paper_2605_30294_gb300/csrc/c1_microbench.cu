@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "philox.cuh"
 #include "rafi_device.cuh"
 #include "rounds.cuh"
 
@@ -26,26 +27,6 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr uint32_t kRetire = 429496730u;  // ceil(0.1 * 2^32)
-
-// One Philox4x32 round and the 10-round generator (Salmon et al., SC'11).
-__device__ __forceinline__ uint4 philox_round(uint4 c, uint2 k)
-{
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-    return make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-}
-
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
-{
-    c = philox_round(c, k);
-#pragma unroll
-    for (int r = 1; r < 10; ++r) {
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-        c = philox_round(c, k);
-    }
-    return c;
-}
 
 struct WorkArgs {
     rf_device_queues q;

@@ -210,3 +210,16 @@ def c2_seeds(count: int, n: int = 512, seed: int = 2, stream: int = 4) -> np.nda
 def c2_seed_set_sizes(count: int = 16) -> list:
     """Uneven batch: round(2^(12 + 8 k / 15)), k = 0 .. 15 (4096 .. 1048576)."""
     return [int(round(2 ** (12 + 8 * k / (count - 1)))) for k in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# Differentiable rendering workload
+# ---------------------------------------------------------------------------
+def c3_target_volume(vol: np.ndarray, seed: int = 3, rel: float = 0.1) -> np.ndarray:
+    """The target density sigma * (1 + rel * u), u uniform in [-1, 1) per voxel
+    from Philox(key={seed, 6}, ctr={voxel, 0, 0, 0})."""
+    i = np.arange(vol.size, dtype=np.uint32)
+    z = np.zeros_like(i)
+    r = philox4x32_10(i, z, z, z, seed, 6)[0]
+    u = r.astype(np.float64) / 4294967296.0 * 2.0 - 1.0
+    return (vol.astype(np.float64).reshape(-1) * (1.0 + rel * u)).astype(np.float32).reshape(vol.shape)

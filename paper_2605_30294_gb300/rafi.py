@@ -86,6 +86,8 @@ _SIGS = {
                           _PU64, _PU64, _P, _u32],
     "rf_c0_make_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c2_make_bricks": [_P, _i32, _i32, _P, _P],
+    "rf_c3_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _u32, _P, _PU64],
+    "rf_c3_adjoint": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _P, _u32, _P, _PU64],
     "rf_c2_seed": [_P, _P, _P, _u64, _i32, _i32, _P],
     "rf_c2_trace": [_P, _P, _i32, _i32, ctypes.c_float, _u32, _u32, _P, _u64, _P],
     "rf_c2_run": [_P, _P, _P, _P, _u64, _i32, _i32, ctypes.c_float, _u32, _u32, _P, _i32, _u32, _P, _PU64,
@@ -329,6 +331,26 @@ def rf_c2_run(ctx: int, bricks, seeds, set_ids, count: int, n: int, brick: int, 
                          ctypes.byref(rounds), ctypes.byref(fwd))
     _check("rf_c2_run", st, allow)
     return st, rounds.value, fwd.value
+
+
+def rf_c3_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, spp: int, seed: int, ray_c,
+                 image, max_rounds: int = 64, stream=None) -> int:
+    c = _cam(cam)
+    rounds = ctypes.c_uint64()
+    _check("rf_c3_render", lib().rf_c3_render(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height, spp,
+                                              seed, ptr(ray_c), ptr(image), max_rounds, stream_handle(stream),
+                                              ctypes.byref(rounds)))
+    return rounds.value
+
+
+def rf_c3_adjoint(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, spp: int, seed: int, ray_c,
+                  grad_image, grad_volume, max_rounds: int = 64, stream=None) -> int:
+    c = _cam(cam)
+    rounds = ctypes.c_uint64()
+    _check("rf_c3_adjoint", lib().rf_c3_adjoint(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height, spp,
+                                                seed, ptr(ray_c), ptr(grad_image), ptr(grad_volume), max_rounds,
+                                                stream_handle(stream), ctypes.byref(rounds)))
+    return rounds.value
 
 
 class Context:
