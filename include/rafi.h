@@ -364,6 +364,27 @@ rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int3
                         int32_t H, int32_t spp, uint32_t seed, const float *rayC, const float *gradImage,
                         float *gradVolume, uint32_t maxRounds, void *stream, uint64_t *rounds);
 
+/* --- stochastic transport by delta tracking (64-byte paths) -------------- */
+
+/* Render numViews views (cams: host, 12 floats each; sizes: host, {W, H}
+ * each) at spp paths per pixel through bricks made by rf_c0_make_bricks
+ * (halo 1) of an N^3 extinction grid with majorant sigmaMax (>= every
+ * voxel).  Path s of global pixel gpix (pixels numbered view after view,
+ * row-major) starts where its jittered ray (Philox key {seed, 9}) enters
+ * the grid; event (bounce b, index e) draws r = Philox4x32-10(key {seed, 7},
+ * counter {gpix, s, b, e}): free flight -logf(1 - u(r0)) / sigmaMax; leaving
+ * the grid scores 1; a real collision (u(r1) sigmaMax < sigma) scatters when
+ * u(r2) < 0.8 (Henyey-Greenstein g = 0.3 from u(r3) and word 0 of Philox
+ * key {seed, 8}; more than 64 bounces score 0), else absorbs (score 0); a
+ * null collision moves on with e + 1.  u(r) = top 24 bits / 2^24.  Paths are
+ * forwarded to the rank owning their next tentative collision point (VoPaT,
+ * Sec. 5.1, Fig. 1).  score (device, total pixels; the caller zeroes it)
+ * receives the number of escaped paths per pixel.  batched != 0: all rounds
+ * in one persistent kernel.  *rounds, *forwarded as rf_c2_run. */
+rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, float sigmaMax, int32_t numViews,
+                       const float *cams, const int32_t *sizes, int32_t spp, uint32_t seed, float *score,
+                       int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded);
+
 #ifdef __cplusplus
 }
 #endif

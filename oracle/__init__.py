@@ -74,6 +74,13 @@ def _load():
             lib.or_c3_render.restype = None
             lib.or_c3_adjoint_f64.argtypes = [P, i32, P, i32, i32, i32, u32, P, P]
             lib.or_c3_adjoint_f64.restype = f64
+            lib.or_c4_path.argtypes = [P, i32, ctypes.c_float, P, i32, i32, i32, u32, u32, u32, P, P]
+            lib.or_c4_path.restype = i32
+            lib.or_c4_render_crop.argtypes = [P, i32, ctypes.c_float, P, i32, u32, i32, i32, i32, i32, i32, u32,
+                                              P, P]
+            lib.or_c4_render_crop.restype = None
+            lib.or_c4_hg_sample.argtypes = [P, ctypes.c_float, ctypes.c_float, P]
+            lib.or_c4_hg_sample.restype = None
             _lib = lib
     return _lib
 
@@ -290,3 +297,34 @@ def c3_adjoint_f64(vol: np.ndarray, cam: np.ndarray, width: int, height: int, sp
     grad = np.zeros(vol.shape, np.float64)
     acc = _load().or_c3_adjoint_f64(_p(vol), vol.shape[0], _p(cam), width, height, spp, seed, _p(g), _p(grad))
     return grad, acc
+
+
+# --------------------------------------------------------------------------
+# Delta-tracking transport (Sec. 5.1's trace step with scattering)
+# --------------------------------------------------------------------------
+def c4_path(vol, sigma_max, cam, width, x, y, gpix, s, seed=4):
+    """Score, events and bounces of one path."""
+    vol = _c(vol, np.float32)
+    cam = _c(cam, np.float32)
+    ev = np.zeros(1, np.uint32)
+    bo = np.zeros(1, np.uint32)
+    sc = _load().or_c4_path(_p(vol), vol.shape[0], sigma_max, _p(cam), width, x, y, gpix, s, seed, _p(ev), _p(bo))
+    return int(sc), int(ev[0]), int(bo[0])
+
+
+def c4_render_crop(vol, sigma_max, cam, width, pix_base, x0, y0, cw, ch, spp, seed=4):
+    """Mean path score over spp per pixel of a crop (ch x cw) and the number of events."""
+    vol = _c(vol, np.float32)
+    cam = _c(cam, np.float32)
+    img = np.zeros(cw * ch, np.float32)
+    ev = np.zeros(1, np.uint64)
+    _load().or_c4_render_crop(_p(vol), vol.shape[0], sigma_max, _p(cam), width, pix_base, x0, y0, cw, ch, spp,
+                              seed, _p(img), _p(ev))
+    return img.reshape(ch, cw), int(ev[0])
+
+
+def c4_hg_sample(d, xi: float, xphi: float) -> np.ndarray:
+    d = _c(np.asarray(d, np.float32).reshape(3), np.float32)
+    out = np.zeros(3, np.float32)
+    _load().or_c4_hg_sample(_p(d), xi, xphi, _p(out))
+    return out

@@ -677,3 +677,123 @@ double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t 
     free(pk);
     return acc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Stochastic transport by delta tracking (VoPaT's trace step, Sec. 5.1,    */
+/* Fig. 1: rays that collide scatter and are forwarded to themselves, rays  */
+/* that leave the local data go to the next rank).                         */
+/*                                                                          */
+/* Path (gpix, s): jittered primary ray (Philox key {seed, 9}, counter      */
+/* {gpix, s, 0, 0}, as the emission-absorption renderer) enters [0,N)^3 at  */
+/* t0 (a miss escapes at once).  Event (bounce b, index e): r = Philox(key  */
+/* {seed, 7}, counter {gpix, s, b, e}); free flight t = -logf(1 - u(r0)) /  */
+/* sigmaMax; q = p + t d.  q outside the grid: the path escapes and scores  */
+/* 1 (environment radiance 1).  Otherwise with sigma(q) (trilinear): a real */
+/* collision when u(r1) * sigmaMax < sigma; then u(r2) < 0.8 scatters (b+1; */
+/* more than 64 bounces score 0) with a Henyey-Greenstein (g = 0.3)         */
+/* direction from u(r3) and u of word 0 of Philox(key {seed, 8}, counter    */
+/* {gpix, s, b, e}); otherwise the path is absorbed (scores 0).  A null     */
+/* collision moves p to q and increments e.  u(r) = top 24 bits / 2^24.     */
+/* ------------------------------------------------------------------------ */
+static void or_c4_hg(float *d, float xi, float xphi)
+{
+    const float g = 0.3f;
+    float s = (1.0f - g * g) / (1.0f - g + 2.0f * g * xi);
+    float ct = (1.0f + g * g - s * s) / (2.0f * g);
+    ct = fminf(1.0f, fmaxf(-1.0f, ct));
+    float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float phi = 6.2831853f * xphi;
+    float cp = cosf(phi), sp = sinf(phi);
+    float ax = fabsf(d[0]) < 0.9f ? 1.0f : 0.0f, ay = 1.0f - ax;
+    /* u = normalize(d x a), v = d x u */
+    float ux = d[1] * 0.0f - d[2] * ay, uy = d[2] * ax - d[0] * 0.0f, uz = d[0] * ay - d[1] * ax;
+    float ul = sqrtf(ux * ux + uy * uy + uz * uz);
+    ux = ux / ul; uy = uy / ul; uz = uz / ul;
+    float vx = d[1] * uz - d[2] * uy, vy = d[2] * ux - d[0] * uz, vz = d[0] * uy - d[1] * ux;
+    float nx = (st * cp) * ux + (st * sp) * vx + ct * d[0];
+    float ny = (st * cp) * uy + (st * sp) * vy + ct * d[1];
+    float nz = (st * cp) * uz + (st * sp) * vz + ct * d[2];
+    float nl = sqrtf(nx * nx + ny * ny + nz * nz);
+    d[0] = nx / nl; d[1] = ny / nl; d[2] = nz / nl;
+}
+
+/* score (0 or 1) of one path; *events = events drawn, *bounces = scatterings */
+int32_t or_c4_path(const float *vol, int32_t N, float sigmaMax, const float *cam, int32_t W, int32_t x, int32_t y,
+                   uint32_t gpix, uint32_t s, uint32_t seed, uint32_t *events, uint32_t *bounces)
+{
+    uint32_t ctr[4] = {gpix, s, 0u, 0u}, key[2] = {seed, 9u}, r[4];
+    or_philox4x32_10(ctr, key, r);
+    float px = (float)x + or_u24(r[0]), py = (float)y + or_u24(r[1]);
+    float d[3];
+    for (int a = 0; a < 3; ++a) d[a] = cam[3 + a] + cam[6 + a] * px + cam[9 + a] * py;
+    float len = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; ++a) d[a] = d[a] / len;
+    float tn[3], tf[3];
+    for (int a = 0; a < 3; ++a) {
+        float ta = (0.0f - cam[a]) / d[a];
+        float tb = ((float)N - cam[a]) / d[a];
+        tn[a] = fminf(ta, tb);
+        tf[a] = fmaxf(ta, tb);
+    }
+    float t0 = fmaxf(fmaxf(fmaxf(tn[0], tn[1]), tn[2]), 0.0f);
+    float t1 = fminf(fminf(tf[0], tf[1]), tf[2]);
+    *events = 0;
+    *bounces = 0;
+    if (!(t0 < t1)) return 1;
+    float p[3] = {cam[0] + d[0] * t0, cam[1] + d[1] * t0, cam[2] + d[2] * t0};
+    uint32_t b = 0, e = 0;
+    for (;;) {
+        uint32_t c2[4] = {gpix, s, b, e}, k2[2] = {seed, 7u}, q4[4];
+        or_philox4x32_10(c2, k2, q4);
+        (*events)++;
+        float t = -logf(1.0f - or_u24(q4[0])) / sigmaMax;
+        float q[3] = {p[0] + d[0] * t, p[1] + d[1] * t, p[2] + d[2] * t};
+        if (!(q[0] >= 0.0f && q[0] < (float)N && q[1] >= 0.0f && q[1] < (float)N && q[2] >= 0.0f &&
+              q[2] < (float)N))
+            return 1;
+        float sg = or_c0_sample(vol, N, q[0], q[1], q[2]);
+        p[0] = q[0]; p[1] = q[1]; p[2] = q[2];
+        if (or_u24(q4[1]) * sigmaMax < sg) {
+            if (!(or_u24(q4[2]) < 0.8f)) return 0;
+            uint32_t k3[2] = {seed, 8u}, h4[4];
+            or_philox4x32_10(c2, k3, h4);
+            b++;
+            (*bounces)++;
+            if (b > 64u) return 0;
+            or_c4_hg(d, or_u24(q4[3]), or_u24(h4[0]));
+            e = 0;
+        } else {
+            e++;
+        }
+    }
+}
+
+/* A crop [x0, x0+cw) x [y0, y0+ch) of a W x H view whose first pixel has
+ * global index pixBase: image = mean score over spp paths per pixel. */
+void or_c4_render_crop(const float *vol, int32_t N, float sigmaMax, const float *cam, int32_t W, uint32_t pixBase,
+                       int32_t x0, int32_t y0, int32_t cw, int32_t ch, int32_t spp, uint32_t seed, float *image,
+                       uint64_t *events)
+{
+    uint64_t ev = 0;
+    for (int32_t yy = 0; yy < ch; ++yy) {
+        for (int32_t xx = 0; xx < cw; ++xx) {
+            int32_t x = x0 + xx, y = y0 + yy;
+            uint32_t gpix = pixBase + (uint32_t)(y * W + x);
+            int32_t sum = 0;
+            for (int32_t s = 0; s < spp; ++s) {
+                uint32_t e, b;
+                sum += or_c4_path(vol, N, sigmaMax, cam, W, x, y, gpix, (uint32_t)s, seed, &e, &b);
+                ev += e;
+            }
+            image[yy * cw + xx] = (float)sum / (float)spp;
+        }
+    }
+    if (events) *events = ev;
+}
+
+/* test access to the Henyey-Greenstein sampler */
+void or_c4_hg_sample(const float *d, float xi, float xphi, float *out)
+{
+    out[0] = d[0]; out[1] = d[1]; out[2] = d[2];
+    or_c4_hg(out, xi, xphi);
+}

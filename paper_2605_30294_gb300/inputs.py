@@ -223,3 +223,73 @@ def c3_target_volume(vol: np.ndarray, seed: int = 3, rel: float = 0.1) -> np.nda
     r = philox4x32_10(i, z, z, z, seed, 6)[0]
     u = r.astype(np.float64) / 4294967296.0 * 2.0 - 1.0
     return (vol.astype(np.float64).reshape(-1) * (1.0 + rel * u)).astype(np.float32).reshape(vol.shape)
+
+
+# ---------------------------------------------------------------------------
+# Transport workload: fractal gradient-noise density, 4 views
+# ---------------------------------------------------------------------------
+_NOISE_LIB = None
+
+
+def _noise_lib():
+    """Build (gcc, OpenMP) and load the noise generator inputs_noise.c."""
+    global _NOISE_LIB
+    if _NOISE_LIB is None:
+        import ctypes
+        import os
+        import subprocess
+
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "inputs_noise.c")
+        lib = os.path.join(here, "libinputs_noise.so")
+        if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            tmp = lib + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+            os.replace(tmp, lib)
+        L = ctypes.CDLL(lib)
+        L.noise_volume.argtypes = [ctypes.c_int32, ctypes.c_uint32, ctypes.c_int32, ctypes.c_double,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+        L.noise_volume.restype = None
+        L.noise_at.argtypes = [ctypes.c_uint32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double]
+        L.noise_at.restype = ctypes.c_double
+        _NOISE_LIB = L
+    return _NOISE_LIB
+
+
+def noise_at(p, seed: int = 4, octaves: int = 6, base: float = 4.0) -> float:
+    """Fractal gradient noise at a point of the unit cube (unclamped)."""
+    return float(_noise_lib().noise_at(seed, octaves, base, float(p[0]), float(p[1]), float(p[2])))
+
+
+def c4_volume(n: int = 1024, seed: int = 4, octaves: int = 6, base: float = 4.0, optical_depth: float = 8.0):
+    """n^3 float32 extinction, index [z, y, x]: fractal gradient noise (octaves, base
+    frequency per unit cube) clamped at 0, scaled so the mean per cell is optical_depth / n.
+    Returns (volume, sigma_max)."""
+    import ctypes
+
+    vol = np.empty((n, n, n), np.float32)
+    total = ctypes.c_double()
+    _noise_lib().noise_volume(n, seed, octaves, base, vol.ctypes.data, ctypes.byref(total))
+    mean = total.value / vol.size
+    scale = np.float32((optical_depth / n) / mean)
+    vol *= scale
+    return vol, float(vol.max())
+
+
+C4_VIEWS = ((2048, 2048), (1024, 768), (512, 512), (3840, 2160))
+
+
+def c4_views(n: int = 1024, sizes=C4_VIEWS):
+    """Four cameras around the grid (40 deg vertical fov, aspect of their resolution),
+    as (cam float32[12], width, height, first global pixel index)."""
+    c = n / 2.0
+    out = []
+    base = 0
+    for v, (w, h) in enumerate(sizes):
+        ang = math.radians(35.0 + 90.0 * v)
+        eye = (c + 1.7 * n * math.sin(ang), c + 0.35 * n * (1 if v % 2 == 0 else -1), c - 1.7 * n * math.cos(ang))
+        cam = camera(eye, (c, c, c), (0.0, 1.0, 0.0), 40.0, w, h)
+        out.append((cam, w, h, base))
+        base += w * h
+    return out

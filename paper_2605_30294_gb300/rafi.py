@@ -86,6 +86,8 @@ _SIGS = {
                           _PU64, _PU64, _P, _u32],
     "rf_c0_make_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c2_make_bricks": [_P, _i32, _i32, _P, _P],
+    "rf_c4_render": [_P, _P, _i32, _i32, ctypes.c_float, _i32, _P, _P, _i32, _u32, _P, _i32, _u32, _P, _PU64,
+                     _PU64],
     "rf_c3_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _u32, _P, _PU64],
     "rf_c3_adjoint": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _P, _u32, _P, _PU64],
     "rf_c2_seed": [_P, _P, _P, _u64, _i32, _i32, _P],
@@ -351,6 +353,20 @@ def rf_c3_adjoint(ctx: int, bricks, cam, n: int, brick: int, width: int, height:
                                                 seed, ptr(ray_c), ptr(grad_image), ptr(grad_volume), max_rounds,
                                                 stream_handle(stream), ctypes.byref(rounds)))
     return rounds.value
+
+
+def rf_c4_render(ctx: int, bricks, n: int, brick: int, sigma_max: float, views, spp: int, seed: int, score,
+                 batched: bool = True, max_rounds: int = 1 << 20, stream=None):
+    """views: sequence of (cam[12], width, height, ...); returns (rounds, forwarded)."""
+    nv = len(views)
+    cams = (ctypes.c_float * (12 * nv))(*[float(x) for v in views for x in v[0]])
+    sizes = (ctypes.c_int32 * (2 * nv))(*[int(x) for v in views for x in (v[1], v[2])])
+    rounds, fwd = ctypes.c_uint64(), ctypes.c_uint64()
+    _check("rf_c4_render", lib().rf_c4_render(ctx, ptr(bricks), n, brick, sigma_max, nv, ctypes.cast(cams, _P),
+                                              ctypes.cast(sizes, _P), spp, seed, ptr(score), int(batched),
+                                              max_rounds, stream_handle(stream), ctypes.byref(rounds),
+                                              ctypes.byref(fwd)))
+    return rounds.value, fwd.value
 
 
 class Context:
