@@ -15,7 +15,9 @@ scatter phase rates from its round log; the plain per-round host loop
 (rf_c1_run) with the scatter kernel's roofline; the same run end to end
 through rf_c1_run_batched with host buffers; rays/s of the 64^3 marching
 workload; particle-steps/s of the streamline workload (512^3 field, 16
-uneven seed sets in one launch, batched and plain forms); the oracle timed
+uneven seed sets in one launch, batched and plain forms); rays/s of the
+differentiable renderer (forward and adjoint) and paths/s of the delta-tracking
+transport (1024^3, 512 ranks, four views at 16 spp); the oracle timed
 on a bounded sample (cpu_baseline); SM clocks sampled during the timed
 region and the number of kernels launched.
 
@@ -288,6 +290,75 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3):
     return res
 
 
+def c3_ea(torch, rafi, inputs, s, reps=5):
+    """Differentiable EA renderer: 256^3 over 2x2x2 ranks, 512x512 at 4 spp; forward and adjoint rays/s."""
+    from paper_2605_30294_gb300 import ea_autograd  # noqa: F401  (the autograd wrapper uses the same calls)
+
+    n, brick, w, h, spp = 256, 128, 512, 512, 4
+    vol = inputs.c0_volume(n)
+    cam = inputs.c0_camera(n, w, h)
+    dv = torch.from_numpy(vol.reshape(-1)).cuda()
+    bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+    rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
+    nr = w * h * spp
+    rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
+    img = torch.zeros(w * h, dtype=torch.float32, device="cuda")
+    gimg = torch.ones(w * h, dtype=torch.float32, device="cuda")
+    grad = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+    out = {"workload": "256^3 blob density, 2x2x2 ranks of 128^3, 512x512 at 4 spp (1,048,576 rays)"}
+    with rafi.Context(8, 64, nr) as ctx:
+        for name, fn in (("forward", lambda: rafi.rf_c3_render(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
+                                                                rayC, img, stream=s)),
+                         ("adjoint", lambda: rafi.rf_c3_adjoint(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
+                                                                 rayC, gimg, grad, stream=s))):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out[name] = {"ms": ms, "rays_per_s": nr / (ms * 1e-3)}
+    return out
+
+
+def c4_transport(torch, rafi, inputs, s):
+    """Delta tracking: 1024^3 noise (mean optical depth 8) over 8x8x8 ranks, 4 views at 16 spp."""
+    n, brick, spp = 1024, 128, 16
+    vol, smax = inputs.c4_volume(n)
+    views = inputs.c4_views(n)
+    bricks = torch.zeros(512 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+    dv = torch.from_numpy(vol.reshape(-1)).cuda()
+    rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
+    del dv, vol
+    torch.cuda.empty_cache()
+    npix = sum(w * h for _, w, h, _ in views)
+    paths = npix * spp
+    score = torch.zeros(npix, dtype=torch.float32, device="cuda")
+    out = {"workload": "1024^3 fractal gradient noise (6 octaves), mean optical depth 8, 8x8x8 ranks of 128^3, "
+                       "views 2048^2, 1024x768, 512^2, 3840x2160 at 16 spp, albedo 0.8, HG g=0.3, <= 64 bounces",
+           "paths": paths}
+    with rafi.Context(512, 64, paths) as ctx:
+        for batched in (True, False):
+            score.zero_()
+            rafi.rf_c4_render(ctx.handle, bricks, n, brick, smax, views, spp, 4, score, batched, stream=s)
+            score.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            rounds, fwd = rafi.rf_c4_render(ctx.handle, bricks, n, brick, smax, views, spp, 4, score, batched,
+                                            stream=s)
+            e1.record(s)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            out["batched" if batched else "plain"] = {"ms": sec * 1e3, "paths_per_s": paths / sec,
+                                                      "rays_forwarded_per_s": fwd / sec, "rounds": rounds}
+    out["batched_over_plain"] = out["plain"]["ms"] / out["batched"]["ms"]
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -395,7 +466,11 @@ def run_ours(args):
     ctx.close()
     del d_items, retired, h_items, h_ret
     torch.cuda.empty_cache()
-    streamlines = c2_streamlines(torch, rafi, inputs, s) if not args.skip_streamlines else None
+    streamlines = c2_streamlines(torch, rafi, inputs, s) if not args.skip_extra else None
+    torch.cuda.empty_cache()
+    ea = c3_ea(torch, rafi, inputs, s) if not args.skip_extra else None
+    torch.cuda.empty_cache()
+    transport = c4_transport(torch, rafi, inputs, s) if not args.skip_extra else None
 
     sec = ms / 1e3
     total_fwd = fwd
@@ -452,6 +527,8 @@ def run_ours(args):
         "rays_per_s": {"value": rays_s, "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
                        "ms_per_frame": c0_ms},
         "streamlines": streamlines,
+        "differentiable_ea": ea,
+        "delta_tracking": transport,
         "cpu_baseline": {"value": cpu_v, "unit": "items/s", "cores": 1, "kind": "oracle",
                          "sample": f"{BASELINE_ITEMS} items per destination law, round-by-round oracle, "
                                    f"{cpu_dt:.1f} s"},
@@ -471,7 +548,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--items", type=int, default=N_ITEMS)
-    ap.add_argument("--skip-streamlines", action="store_true", help="leave out the streamline workload")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="leave out the streamline, differentiable and transport workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
