@@ -10,7 +10,7 @@ persistent kernel, rf_c1_run_batched); inputs are resident in HBM before
 timing, and the 1 GiB queues are larger than L2.
 
 Also reported on the same line: the persistent kernel's roofline
-(algorithmic bytes over its CUDA-event time) and its per-round work and
+(algorithmic bytes over its CUDA-event time) and its per-round count and
 scatter phase rates from its round log; the plain per-round host loop
 (rf_c1_run) with the scatter kernel's roofline; the same run end to end
 through rf_c1_run_batched with host buffers; rays/s of the 64^3 marching
@@ -225,21 +225,29 @@ LOG_CAP = 4096  # rounds logged by the persistent kernel
 
 
 def phase_rates(log_rows, item_bytes, min_items=1 << 20):
-    """Per-round GB/s of the work and scatter phases from the persistent kernel's round log.
+    """Per-round rates of the persistent kernel from its round log.
 
-    A phase lasts until the barrier that ends it completes, so the slowest
-    CTA sets its time: work = round start -> first barrier done, scatter =
-    first barrier done -> second barrier done.
+    Round 0 steps the seeded queue in place (read and write every item) and
+    scatters it; every later round only counts the destinations of its
+    already-stepped queue (4 bytes an item) before its scatter, which reads
+    every queued item and writes it to its destination's segment, where the
+    next round's step is applied on arrival, or to the retirement sink.  A
+    phase lasts until the barrier that ends it completes, so the slowest CTA
+    sets its time: count (or step) = round start -> first barrier done,
+    scatter = first barrier done -> second barrier done.
     """
     lg = np.asarray(log_rows, dtype=np.float64)
     big = lg[:, 5] >= min_items
-    work_b = lg[:, 5] * 2 * item_bytes
-    scat_b = lg[:, 6] * 2 * item_bytes
+    first = np.arange(len(lg)) == 0
+    work_b = np.where(first, lg[:, 5] * 2 * item_bytes, lg[:, 5] * 4)
+    scat_b = lg[:, 5] * (2 * item_bytes + 4) + lg[:, 6] * 4
     work_t = (lg[:, 2] - lg[:, 0]) * 1e-9
     scat_t = (lg[:, 4] - lg[:, 2]) * 1e-9
     out = {"rounds": int(len(lg)), "rounds_ge_2^20": int(big.sum())}
     if big.any():
-        out["work_gbs_ge_2^20"] = float(work_b[big].sum() / work_t[big].sum() / 1e9)
+        later = big & ~first
+        if later.any():
+            out["count_us_per_round_ge_2^20"] = float(work_t[later].mean() * 1e6)
         out["scatter_gbs_ge_2^20"] = float(scat_b[big].sum() / scat_t[big].sum() / 1e9)
         per_round = scat_b[big] / scat_t[big] / 1e9
         out["scatter_gbs_ge_2^20_min_round"] = float(per_round.min())
@@ -248,6 +256,11 @@ def phase_rates(log_rows, item_bytes, min_items=1 << 20):
     small = ~big
     if small.any():
         out["us_per_round_lt_2^20"] = float((lg[small, 4] - lg[small, 0]).mean() * 1e-3)
+    # rounds of at most 1024 items run on one CTA; the ones between run on the whole grid
+    for name, sel in (("solo_le_1024", lg[:, 5] <= 1024), ("grid_lt_2^20", small & (lg[:, 5] > 1024))):
+        if sel.any():
+            out["rounds_" + name] = int(sel.sum())
+            out["us_per_round_" + name] = float((lg[sel, 4] - lg[sel, 0]).mean() * 1e-3)
     out["round_ms_total"] = float((lg[-1, 4] - lg[0, 0]) * 1e-6) if len(lg) else 0.0
     return out
 
@@ -403,13 +416,14 @@ def run_ours(args):
     s = torch.cuda.current_stream(dev)
     ctx = rafi.Context(RANKS, ITEM_BYTES, n)
 
-    def step(batched, round_log=None):
+    def step(batched, round_log=None, fuse=True):
         fwd = 0
         for mode in MODES:
             if batched:
                 st, cnt, rounds, f = rafi.rf_c1_run_batched(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired,
                                                             stream=s, round_log=round_log,
-                                                            round_log_cap=LOG_CAP if round_log is not None else 0)
+                                                            round_log_cap=LOG_CAP if round_log is not None else 0,
+                                                            step_on_arrival=fuse)
             else:
                 st, cnt, rounds, f = rafi.rf_c1_run(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired,
                                                     stream=s)
@@ -418,7 +432,7 @@ def run_ours(args):
             fwd += f
         return fwd
 
-    def timed(batched, steps):
+    def timed(batched, steps, fuse=True):
         rafi.rf_set_timing(ctx.handle, True)
         rafi.rf_get_timing(ctx.handle, reset=True)
         barrier()
@@ -428,7 +442,7 @@ def run_ours(args):
             e0.record(s)
             fwd = 0
             for _ in range(steps):
-                fwd += step(batched)
+                fwd += step(batched, fuse=fuse)
             e1.record(s)
             barrier()
         launches = rafi.rf_launch_count() - launches0
@@ -448,6 +462,9 @@ def run_ours(args):
     fwd, ms, tb, launches, clocks = timed(True, args.steps)
     p_steps = max(3, args.steps // 4)
     p_fwd, p_ms, tp, p_launches, p_clocks = timed(False, p_steps)
+    # the persistent form with the work step as its own pass (no step on arrival)
+    step(True, fuse=False)
+    u_fwd, u_ms, tu, _, _ = timed(True, p_steps, fuse=False)
 
     # per-round phase rates of the persistent kernel (one extra, untimed step)
     step(True, round_log=log)
@@ -503,22 +520,26 @@ def run_ours(args):
         return 0
 
     peak, peak_kind = peaks()
-    # persistent kernel: 2 x 64 B per item through the work phase (all items of every
-    # round) plus 2 x 64 B per item through the scatter phase (items delivered)
+    # persistent kernel: round 0 reads and writes every seeded item (its step);
+    # every round's scatter reads each queued item and writes it once (to its
+    # destination, stepped on arrival, or to the retirement sink).  The queued
+    # items of all rounds of a run are its n seeded items plus its deliveries.
     runs = tb.roundsLaunches
-    alg_bytes = 2 * ITEM_BYTES * (runs * n + 2 * fwd)
+    alg_bytes = 2 * ITEM_BYTES * (2 * runs * n + fwd)
     achieved = alg_bytes / (tb.roundsMs * 1e-3) / 1e9 if tb.roundsMs > 0 else 0.0
     p_bytes = tp.scatterItems * 2 * ITEM_BYTES
     p_ach = p_bytes / (tp.scatterMs * 1e-3) / 1e9 if tp.scatterMs > 0 else 0.0
     p_ach_l = (tp.scatterItemsLarge * 2 * ITEM_BYTES / (tp.scatterMsLarge * 1e-3) / 1e9
                if tp.scatterMsLarge > 0 else 0.0)
+    u_ach = (2 * ITEM_BYTES * (tu.roundsLaunches * n + 2 * u_fwd) / (tu.roundsMs * 1e-3) / 1e9
+             if tu.roundsMs > 0 else 0.0)
     cpu_v, cpu_fwd, cpu_dt = oracle_baseline()
     line = {
         "metric": METRIC, "value": total_fwd / sec, "unit": "items/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "items": n, "item_bytes": ITEM_BYTES, "ranks": RANKS,
-                   "form": "batched: all rounds in one persistent cooperative kernel per run",
+                   "form": "batched: all rounds in one persistent cooperative kernel per run, each step applied on arrival",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "no flush: the 1 GiB item queues exceed the 129 MB L2"},
         "roofline": {"bound": "hbm", "kernel": "rounds_kernel<C1Work>", "achieved": achieved, "peak": peak,
@@ -528,7 +549,12 @@ def run_ours(args):
                      "ms_total": tb.roundsMs},
         "phases_from_round_log": {**rates,
                                   "scatter_frac_ge_2^20": rates.get("scatter_gbs_ge_2^20", 0.0) / peak,
-                                  "work_frac_ge_2^20": rates.get("work_gbs_ge_2^20", 0.0) / peak},
+                                  "round_frac_ge_2^20": rates.get("round_gbs_ge_2^20", 0.0) / peak},
+        "batched_step_in_place": {
+            "value": u_fwd / (u_ms / 1e3), "ms_per_step": u_ms / p_steps, "steps": p_steps,
+            "form": "persistent kernel; each round steps every item in its queue slot, then scatters",
+            "roofline": {"achieved": u_ach, "frac": u_ach / peak,
+                         "alg_bytes": "2 x 64 B per queued item for the step pass, 2 x 64 B per delivery"}},
         "plain": {"value": p_fwd / (p_ms / 1e3), "ms_per_step": p_ms / p_steps, "steps": p_steps,
                   "form": "host loop: work kernel + count/scan/scatter/wrap-up kernels + one sync per round",
                   "roofline_scatter": {"achieved": p_ach, "frac": p_ach / peak,

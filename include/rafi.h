@@ -248,24 +248,32 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
                     int32_t deterministic, int32_t hostMemory, uint32_t maxRounds, void *stream,
                     uint64_t *rounds, uint64_t *forwarded);
 
-/* Batched form of rf_c1_run: the seed and its exchange as in rf_c1_run, then
- * every work round and exchange inside one persistent cooperative kernel
- * (phase 1: work step written back to the same queue slots, destination -1
- * for a retired item; bounded grid barrier; destination offsets and the next
- * active count; phase 3: stable scatter; bounded grid barrier), so no round
- * needs the host.  Queue order is deterministic: round k's incoming queue is
- * the one of rf_c1_run with deterministic != 0.  Rounds of at most 1024
- * items run on one CTA (the others return).  roundLog (device, 7 x
- * roundLogCap words, nullable) receives per round, as seen by CTA 0, the
- * %globaltimer ns at round start, end of its work phase, after the first
- * barrier, end of its scatter phase and after the second barrier, then the
- * incoming and the delivered item counts.  RF_ERR_TIMEOUT if a bounded wait
- * gave up.
+/* Batched form of rf_c1_run: the seed as in rf_c1_run, then every work
+ * round and exchange inside one persistent cooperative kernel, so no round
+ * needs the host.  Per round: destination counts per CTA range, bounded grid
+ * barrier, destination offsets and the next active count, stable scatter
+ * (retirement is one more destination: the retired items land, stably, in
+ * `retired`), bounded grid barrier.
+ * stepOnArrival != 0: the scatter applies the next round's work step to each
+ * item as it lands in its destination's segment, so an item crosses HBM once
+ * per round; the seed exchange is the kernel's first scatter (it applies
+ * round 0's step).  A run that stops at maxRounds scatters its last round
+ * plainly, leaving the unstepped queue.
+ * stepOnArrival == 0: the seed exchange runs first; each round's work step
+ * reads and writes back every item in its queue slot before the scatter.
+ * Queue order is deterministic either way: round k's incoming queue is the
+ * one of rf_c1_run with deterministic != 0.  Rounds of at most 1024 items
+ * run on one CTA (the others return).  roundLog (device, 7 x roundLogCap
+ * words, nullable) receives per round, as seen by CTA 0, the %globaltimer ns
+ * at round start, end of its work step (or count), after the first barrier,
+ * end of its scatter and after the second barrier, then the incoming and the
+ * delivered item counts.  RF_ERR_TIMEOUT if a bounded wait gave up.
  * Other arguments and results as rf_c1_run. */
 rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
                             int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,
-                            int32_t hostMemory, uint32_t maxRounds, void *stream, uint64_t *rounds,
-                            uint64_t *forwarded, unsigned long long *roundLog, uint32_t roundLogCap);
+                            int32_t hostMemory, int32_t stepOnArrival, uint32_t maxRounds, void *stream,
+                            uint64_t *rounds, uint64_t *forwarded, unsigned long long *roundLog,
+                            uint32_t roundLogCap);
 
 /* --- absorption marching through bricks (48-byte rays) ------------------- */
 

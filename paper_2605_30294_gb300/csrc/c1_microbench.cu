@@ -38,6 +38,20 @@ struct WorkArgs {
     int32_t mode, gx, gy, gz;
 };
 
+// Neighbour k of rank src on the gx x gy x gz torus (rank = x + gx (y + gy z)):
+// k = 0..5 for +x, -x, +y, -y, +z, -z, wrapping.
+__device__ __forceinline__ int32_t torus_neighbour(int32_t src, int32_t k, int32_t gx, int32_t gy, int32_t gz)
+{
+    int32_t x = src % gx, y = (src / gx) % gy, z = src / (gx * gy);
+    if (k == 0) x = (x + 1) % gx;
+    else if (k == 1) x = (x + gx - 1) % gx;
+    else if (k == 2) y = (y + 1) % gy;
+    else if (k == 3) y = (y + gy - 1) % gy;
+    else if (k == 4) z = (z + 1) % gz;
+    else z = (z + gz - 1) % gz;
+    return x + gx * (y + gy * z);
+}
+
 __device__ __forceinline__ int32_t choose_dest(int32_t mode, int32_t src, uint32_t r1, int32_t R,
                                                const uint32_t *thr, int32_t gx, int32_t gy, int32_t gz)
 {
@@ -52,15 +66,7 @@ __device__ __forceinline__ int32_t choose_dest(int32_t mode, int32_t src, uint32
         }
         return lo;
     }
-    int32_t x = src % gx, y = (src / gx) % gy, z = src / (gx * gy);
-    const int32_t k = (int32_t)(((unsigned long long)r1 * 6u) >> 32);
-    if (k == 0) x = (x + 1) % gx;
-    else if (k == 1) x = (x + gx - 1) % gx;
-    else if (k == 2) y = (y + 1) % gy;
-    else if (k == 3) y = (y + gy - 1) % gy;
-    else if (k == 4) z = (z + 1) % gz;
-    else z = (z + gz - 1) % gz;
-    return x + gx * (y + gy * z);
+    return torus_neighbour(src, (int32_t)(((unsigned long long)r1 * 6u) >> 32), gx, gy, gz);
 }
 
 // Per-rank work kernel: one thread per incoming item; the owning rank comes
@@ -145,24 +151,36 @@ struct C1Work {
     static constexpr int V = 4;
     static constexpr bool kAppendRetired = true;
     static constexpr bool kDynamicWork = false;
+    static constexpr bool kFuseStep = true;
     static constexpr int kMinBlocksPerSM = 3;
     static constexpr int kItemsPerThread = 2;
+    static constexpr unsigned kStepReadMask = 0x9u;   // the step reads words 0-1 and 12-15
+    static constexpr unsigned kStepWriteMask = 0x8u;  // and writes words 13-15
     const uint32_t *zipfThr;
     uint32_t seed;
     int32_t mode, gx, gy, gz, R;
 
-    __host__ __device__ uint32_t smemBytes() const { return (uint32_t)(R > 1 ? R : 1) * 4u; }
+    // shared memory: the Zipf thresholds, or the torus neighbour table [rank][6]
+    __host__ __device__ uint32_t smemBytes() const
+    {
+        return (uint32_t)(R > 1 ? R : 1) * (mode == RF_C1_NBR6 ? 6u : 1u) * 4u;
+    }
     __device__ void load_smem(void *s) const
     {
         uint32_t *t = static_cast<uint32_t *>(s);
         if (mode == RF_C1_ZIPF)
             for (int e = threadIdx.x; e < R - 1; e += blockDim.x) t[e] = zipfThr[e];
+        if (mode == RF_C1_NBR6)
+            for (int e = threadIdx.x; e < 6 * R; e += blockDim.x)
+                t[e] = (uint32_t)torus_neighbour(e / 6, e % 6, gx, gy, gz);
     }
     __device__ int32_t step(uint4 (&w)[4], int32_t rank, uint32_t round, const void *s) const
     {
         const uint4 r = philox4x32_10(make_uint4(w[0].x, w[0].y, w[3].w, round), make_uint2(seed, 1u));
         if (r.x < kRetire) return -1;
-        const int32_t d = choose_dest(mode, rank, r.y, R, static_cast<const uint32_t *>(s), gx, gy, gz);
+        const uint32_t *t = static_cast<const uint32_t *>(s);
+        const int32_t d = mode == RF_C1_NBR6 ? (int32_t)t[rank * 6 + (int32_t)(((unsigned long long)r.y * 6u) >> 32)]
+                                             : choose_dest(mode, rank, r.y, R, t, gx, gy, gz);
         w[3].z = (uint32_t)d;
         w[3].y ^= r.z;
         w[3].w += 1u;
@@ -380,8 +398,8 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
 
 extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode,
                                        double zipfS, int32_t gx, int32_t gy, int32_t gz, void *retired,
-                                       uint64_t *retiredCountOut, int32_t hostMemory, uint32_t maxRounds,
-                                       void *stream, uint64_t *rounds, uint64_t *forwarded,
+                                       uint64_t *retiredCountOut, int32_t hostMemory, int32_t stepOnArrival,
+                                       uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded,
                                        unsigned long long *roundLog, uint32_t roundLogCap)
 {
     using namespace rfi;
@@ -414,8 +432,11 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
     } else {
         if (rf_status st = rf_c1_seed(ctx, items, n, stream)) return st;
     }
-    // the seed exchange runs asynchronously; the persistent kernel starts from its result
-    if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
+    // with steps on arrival the persistent kernel delivers the seeded
+    // out-queue itself (a pre-round that applies round 0's step on arrival);
+    // otherwise the seed exchange runs first, asynchronously
+    if (!stepOnArrival)
+        if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
 
     C1Work w;
     w.zipfThr = ctx->zipfThr;
@@ -427,7 +448,7 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
     w.R = ctx->numRanks;
     unsigned long long res[4];
     rf_status st = launch_rounds(ctx, w, maxRounds, s, roundLog, roundLogCap, static_cast<uint4 *>(devRetired), n,
-                                 ctx->stagingCount, res);
+                                 ctx->stagingCount, res, stepOnArrival != 0, stepOnArrival != 0);
     if (st != RF_OK) return st;
     unsigned long long cnt = 0;
     RF_CUDA(cudaMemcpy(&cnt, ctx->stagingCount, sizeof cnt, cudaMemcpyDeviceToHost));

@@ -161,6 +161,9 @@ struct C2Work {
     static constexpr int V = 2;
     static constexpr bool kAppendRetired = false;
     static constexpr bool kDynamicWork = true;
+    static constexpr bool kFuseStep = false;
+    static constexpr unsigned kStepReadMask = 0x3u;  // every vector
+    static constexpr unsigned kStepWriteMask = 0x3u;
     static constexpr int kMinBlocksPerSM = 3;
     static constexpr int kItemsPerThread = 1;
     C2Params P;

@@ -183,6 +183,9 @@ struct C4Work {
     static constexpr int V = 4;
     static constexpr bool kAppendRetired = false;
     static constexpr bool kDynamicWork = true;
+    static constexpr bool kFuseStep = false;
+    static constexpr unsigned kStepReadMask = 0xfu;  // every vector
+    static constexpr unsigned kStepWriteMask = 0xfu;
     static constexpr int kMinBlocksPerSM = 3;
     static constexpr int kItemsPerThread = 1;
     TParams P;

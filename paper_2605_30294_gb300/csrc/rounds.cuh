@@ -49,9 +49,11 @@ struct RoundsArgs {
     uint4 *in;
     uint4 *out;
     int32_t *dest;             // capacity rounded up to 4 entries + 4 (bulk-copied in 16-byte units)
+    int32_t *dest2;            // the same size: second destination array (policies with kFuseStep)
     uint32_t *inOffset;        // numRanks + 1
     uint32_t *tot;             // gridDim.x rows of per-CTA destination counts (row stride: digits rounded to 4)
     unsigned int *total;       // 2 x digits: per-destination totals (round parity)
+    uint32_t *grpTot;          // 2 x kSyncGroups rows (stride as tot): per-group destination totals (round parity)
     GridSync *sync;
     unsigned long long *result;  // {rounds, forwarded, status, retired}
     unsigned long long *numActiveOut;  // items still active when the kernel returns
@@ -59,8 +61,10 @@ struct RoundsArgs {
     uint4 *retiredOut;         // retirement sink (policies with kAppendRetired)
     unsigned long long retiredCap;
     unsigned long long *retiredCountOut;
+    unsigned long long *seedCount;  // nullable: start from a seeded out-queue of this many items (kFuseStep)
     uint32_t maxRounds;
     uint32_t roundLogCap;
+    uint32_t fuseStep;  // apply steps on arrival (policies with kFuseStep)
     int32_t numRanks;
 };
 
@@ -212,11 +216,97 @@ __device__ inline uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
     return total;
 }
 
+// Item j of a staged tile is V contiguous 16-byte vectors.  When a warp
+// reads vector q of 32 consecutive items, each quarter warp (8 threads, one
+// shared-memory wavefront) lands on the same few bank groups: 4-way conflicts
+// for 64-byte items.  Each thread instead walks its item's vectors starting
+// at a per-thread offset (position q xor r, r = (j V / 8) mod V), which puts
+// the 8 threads of a quarter warp on 8 distinct 16-byte bank groups, and
+// permutes the registers back with selects.  V a power of two up to 8; other
+// V keep the plain order.
+template <int V>
+__device__ __forceinline__ uint32_t tile_rot(uint32_t j)
+{
+    if constexpr (V == 2 || V == 4 || V == 8) return (j * (uint32_t)V / 8u) & (uint32_t)(V - 1);
+    else return 0u;
+}
+
+// t[q] <- t[q xor r] for all q (the xor permutation, one swap stage per bit of r)
+template <int V>
+__device__ __forceinline__ void xor_permute(uint4 (&t)[V], uint32_t r)
+{
+    if constexpr (V == 2 || V == 4 || V == 8) {
+#pragma unroll
+        for (int b = 1; b < V; b <<= 1) {
+            const bool f = (r & (uint32_t)b) != 0u;
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                if (q & b) continue;
+                const uint4 x = t[q], y = t[q | b];
+                t[q] = f ? y : x;
+                t[q | b] = f ? x : y;
+            }
+        }
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void load_item_rot(const uint4 *s, uint32_t j, uint4 (&w)[V])
+{
+    const uint32_t r = tile_rot<V>(j);
+#pragma unroll
+    for (int q = 0; q < V; ++q) w[q] = s[j * V + ((uint32_t)q ^ r)];
+    xor_permute<V>(w, r);
+}
+
+template <int V>
+__device__ __forceinline__ void store_item_rot(uint4 *s, uint32_t j, const uint4 (&w)[V])
+{
+    const uint32_t r = tile_rot<V>(j);
+    uint4 t[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) t[q] = w[q];
+    xor_permute<V>(t, r);
+#pragma unroll
+    for (int q = 0; q < V; ++q) s[j * V + ((uint32_t)q ^ r)] = t[q];
+}
+
+// The vectors of an item a policy's step reads (W::kStepReadMask) and writes
+// (W::kStepWriteMask).  A step that touches the whole item walks it in the
+// rotated order; a partial one loads and stores only its own vectors (the
+// rest of w is left zero and never written back).
+template <class W>
+__device__ __forceinline__ void load_step(const uint4 *s, uint32_t j, uint4 (&w)[W::V])
+{
+    constexpr unsigned kAll = (1u << W::V) - 1u;
+    if constexpr ((W::kStepReadMask & kAll) == kAll) {
+        load_item_rot<W::V>(s, j, w);
+    } else {
+#pragma unroll
+        for (int q = 0; q < W::V; ++q)
+            w[q] = ((W::kStepReadMask >> q) & 1u) ? s[j * W::V + q] : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+template <class W>
+__device__ __forceinline__ void store_step(uint4 *s, uint32_t j, const uint4 (&w)[W::V])
+{
+    constexpr unsigned kAll = (1u << W::V) - 1u;
+    if constexpr ((W::kStepWriteMask & kAll) == kAll) {
+        store_item_rot<W::V>(s, j, w);
+    } else {
+#pragma unroll
+        for (int q = 0; q < W::V; ++q)
+            if ((W::kStepWriteMask >> q) & 1u) s[j * W::V + q] = w[q];
+    }
+}
+
 struct RoundsLayout {
     uint32_t items, dests, wc, cnt, start, base, tot, off, slotSrc, slotDst, tmp, flag, bar, work, total;
 };
 
 __host__ __device__ inline uint32_t rounds_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+inline size_t rounds_align_sz(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // items: two tile buffers (double buffering); the same bytes stage the
 // per-CTA count rows in phase 2.  dests: the tiles' destinations.  D =
@@ -253,6 +343,8 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
 //                                         phase hands out chunks dynamically
 //   static constexpr int kMinBlocksPerSM; resident CTAs per SM to compile for
 //   static constexpr int kItemsPerThread; tile = 256 x this many items
+//   static constexpr bool kFuseStep;      short, even per-item work: the scatter
+//                                         applies the next round's step on arrival
 //   uint32_t smemBytes() const;           its own shared memory
 //   void load_smem(void *s) const;        fill it (all threads; a barrier follows)
 //   int32_t step(uint4 (&w)[V], int32_t rank, uint32_t round, const void *s) const;
@@ -267,6 +359,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     constexpr uint32_t kTile = kRoundsBlock * kK;
     constexpr uint32_t kTileVecs = kTile * V;
     constexpr uint32_t kRetFlag = 0x80000000u;
+    constexpr bool kFuse = W::kFuseStep && !W::kDynamicWork;
     extern __shared__ __align__(128) unsigned char smem[];
     const int R = a.numRanks;
     const int D = R + (W::kAppendRetired ? 1 : 0);  // digits: ranks (+ retirement)
@@ -292,6 +385,9 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     const int G = gridDim.x, c = blockIdx.x;
     const int nbits = 32 - __clz(D);  // keys 0..D (D = no item)
     const uint32_t rowsPerStage = (2u * kTileVecs * 16u) / (uint32_t)(Dp * 4);
+    // prefix groups: kSyncGroups runs of consecutive CTAs
+    const int grpSize = (G + kSyncGroups - 1) / kSyncGroups;
+    const int grp = c / grpSize, grpStart = grp * grpSize;
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -355,19 +451,181 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         return true;
     };
 
-    uint32_t n = a.inOffset[R];
+    // A seeded start (kFuseStep policies): the out-queue P0 holds the seeded
+    // items with their first ranks as destinations; a pre-round delivers them
+    // (not counted as a round, its deliveries not as forwards), applying
+    // round 0's step on arrival.
+    bool pre = kFuse && a.fuseStep && a.seedCount != nullptr;
+    uint32_t n = pre ? (uint32_t)*a.seedCount : a.inOffset[R];
     unsigned long long forwarded = 0, retiredSoFar = 0;
-    uint32_t round = 0;
+    uint32_t round = 0, it = 0;  // it: iterations including the pre-round (parity of the round counters)
     bool failed = false;
+    // Step on arrival (policies with kFuseStep): the scatter of round k applies
+    // round k+1's step to each item as it lands in its destination's segment,
+    // so the next round starts from stepped items and only counts their
+    // destinations.  Stepped items live in one of two (items, destinations)
+    // pairs, P0 = (out, dest) and P1 = (in, dest2); xsel names the current one.
+    // `fresh`: the incoming queue holds unstepped items (round 0, or after a
+    // plain scatter), which phase 1 steps into P0.
+    bool fresh = !pre;
+    uint32_t xsel = 0u;
+    auto curItemsOf = [&](uint32_t x) { return x ? a.in : a.out; };
+    auto curDestOf = [&](uint32_t x) { return x ? a.dest2 : a.dest; };
 
-    for (;; ++round) {
-        if (n == 0 || round >= a.maxRounds) break;
+    // Ranks a staged tile (items sItems, destinations dts, cnt entries)
+    // stably by destination digit, applying round qs's step to every item
+    // bound for a rank when doFuse (its new destination replaces the staged
+    // one); fills dCnt, dStart (the tile's slots grouped by digit) and
+    // slotSrc / slotDst (position = dBase[d] + rank within d; the retirement
+    // flag for digit R).  With ownBases the tile is a whole round on its own:
+    // dBase[d] = dStart[d] for ranks and the retired count so far for R.
+    // Returns the number of valid items.  All threads; ends with a barrier.
+    auto rank_tile = [&](uint4 *sItems, int32_t *dts, uint32_t cnt, bool doFuse, uint32_t qs,
+                         bool ownBases) -> uint32_t {
+        int myD[kK];
+        uint32_t myR[kK];
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            const uint32_t idx = (uint32_t)(warp * 32 * kK + k * 32 + lane);
+            const int32_t d = idx < cnt ? dts[idx] : -1;
+            const bool valid = (uint32_t)d < (uint32_t)D;
+            const int key = valid ? d : D;
+            const unsigned peers = peers_of(key, nbits);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (valid && lane == leader) {
+                old = wc[warp * D + d];
+                wc[warp * D + d] = old + (uint32_t)__popc(peers);
+            }
+            old = __shfl_sync(0xFFFFFFFFu, old, leader);
+            __syncwarp();
+            myD[k] = valid ? d : -1;
+            myR[k] = old + (uint32_t)__popc(peers & lanemask_lt());
+            if (doFuse && valid && d < R) {
+                uint4 w[V];
+                if constexpr (W::kAppendRetired) load_step<W>(sItems, idx, w);
+                else load_item_rot<V>(sItems, idx, w);  // retire() takes the whole item
+                int32_t d2 = work.step(w, d, qs, sWork);
+                if (d2 >= 0) {
+                    store_step<W>(sItems, idx, w);
+                } else if (W::kAppendRetired) {
+                    d2 = R;
+                } else {
+                    work.retire(w);
+                }
+                dts[idx] = d2;
+            }
+        }
+        if (doFuse) fence_proxy_async_smem();  // generic writes before the buffer's next bulk load
+        __syncthreads();
+        for (int e = tid; e < D; e += kRoundsBlock) {
+            uint32_t sum = 0;
+#pragma unroll
+            for (int ww = 0; ww < kRoundsWarps; ++ww) {
+                const uint32_t v = wc[ww * D + e];
+                wc[ww * D + e] = sum;
+                sum += v;
+            }
+            dCnt[e] = sum;
+            dStart[e] = sum;
+        }
+        const uint32_t nValid = rounds_block_scan(dStart, D, tmp);
+        if (ownBases) {
+            for (int e = tid; e < D; e += kRoundsBlock)
+                dBase[e] = (W::kAppendRetired && e == R) ? (uint32_t)retiredSoFar : dStart[e];
+            __syncthreads();
+        }
+#pragma unroll
+        for (int k = 0; k < kK; ++k) {
+            if (myD[k] >= 0) {
+                const int d = myD[k];
+                const uint32_t within = wc[warp * D + d] + myR[k];
+                const uint32_t slot = dStart[d] + within;
+                slotSrc[slot] = (uint16_t)(warp * 32 * kK + k * 32 + lane);
+                slotDst[slot] = (dBase[d] + within) | (W::kAppendRetired && d == R ? kRetFlag : 0u);
+            }
+        }
+        __syncthreads();
+        return nValid;
+    };
+
+    for (;; ++it) {
+        if (n == 0 || (!pre && round >= a.maxRounds)) break;
         if (!solo && n <= kSoloItems) {
             solo = true;
             if (c != 0) break;
         }
+        if (kFuse && a.fuseStep && solo && !fresh && !pre && n <= kTile && round + 2u < a.maxRounds) {
+            // ---- on-chip tail: CTA 0 alone with the whole queue in shared memory.
+            // Each round ranks the stepped queue (tile A), applies the next
+            // round's step on arrival and writes the next queue into tile B;
+            // retired items go to the sink.  Two rounds before maxRounds the
+            // queue is handed back to P0 for the general path's plain last round.
+            if (tid == 0)
+                issue_bytes(0, sBuf, curItemsOf(xsel), n * kItemBytes, sDst, curDestOf(xsel), ((n + 3u) & ~3u) * 4u);
+            if (!wait(0)) {
+                failed = true;
+                break;
+            }
+            uint32_t A = 0;
+            while (n > 0 && round + 2u < a.maxRounds) {
+                const bool lr = a.roundLog && tid == 0 && round < a.roundLogCap;
+                if (lr) a.roundLog[7 * round + 0] = globaltimer();
+                for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
+                __syncwarp();
+                uint4 *iA = sBuf + A * kTileVecs, *iB = sBuf + (A ^ 1u) * kTileVecs;
+                int32_t *dA = sDst + A * (kTile + 4u), *dB = sDst + (A ^ 1u) * (kTile + 4u);
+                const uint32_t nValid = rank_tile(iA, dA, n, true, round + 1u, true);
+                const uint32_t nNext = W::kAppendRetired ? dStart[R] : nValid;
+                const uint32_t retiredNow = W::kAppendRetired ? dCnt[R] : 0u;
+                if (lr) a.roundLog[7 * round + 1] = a.roundLog[7 * round + 2] = globaltimer();
+                for (uint32_t slot = tid; slot < nValid; slot += kRoundsBlock) {
+                    const uint32_t dst = slotDst[slot];
+                    const uint32_t src = slotSrc[slot];
+                    const uint32_t rot = tile_rot<V>(src);
+                    const bool ret = W::kAppendRetired && (dst & kRetFlag);
+                    const uint32_t pos = dst & ~kRetFlag;
+                    uint4 *to = ret ? (pos < a.retiredCap ? a.retiredOut + (size_t)pos * V : nullptr) : iB + pos * V;
+                    if (to) {
+#pragma unroll
+                        for (int qq = 0; qq < V; ++qq) {
+                            const uint32_t p = (uint32_t)qq ^ rot;
+                            to[p] = iA[src * V + p];
+                        }
+                    }
+                    if (!ret) dB[pos] = dA[src];
+                }
+                __syncthreads();
+                if (lr) {
+                    a.roundLog[7 * round + 3] = a.roundLog[7 * round + 4] = globaltimer();
+                    a.roundLog[7 * round + 5] = n;
+                    a.roundLog[7 * round + 6] = nNext;
+                }
+                retiredSoFar += retiredNow;
+                forwarded += nNext;
+                n = nNext;
+                A ^= 1u;
+                ++round;
+            }
+            if (n > 0) {
+                // hand the stepped queue back in P0 and clear the round counters
+                uint4 *iA = sBuf + A * kTileVecs;
+                const int32_t *dA = sDst + A * (kTile + 4u);
+                for (uint32_t v = tid; v < n * V; v += kRoundsBlock) a.out[v] = iA[v];
+                for (uint32_t i = tid; i < n; i += kRoundsBlock) a.dest[i] = dA[i];
+                for (int e = tid; e < 2 * D; e += kRoundsBlock) a.total[e] = 0u;
+                for (int e = tid; e < 2 * kSyncGroups * Dp; e += kRoundsBlock) a.grpTot[e] = 0u;
+                xsel = 0u;
+            } else {
+                for (int e = tid; e <= R; e += kRoundsBlock) a.inOffset[e] = 0u;
+            }
+            fence_proxy_async_global();
+            __threadfence();
+            __syncthreads();
+            continue;
+        }
         const int g = solo ? 1 : G;
-        const bool logRound = a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
+        const bool logRound = !pre && a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
         if (logRound) a.roundLog[7 * round + 0] = globaltimer();
         for (int e = tid; e <= R; e += kRoundsBlock) sOff[e] = a.inOffset[e];
         for (int e = tid; e < D; e += kRoundsBlock) sTot[e] = 0u;
@@ -381,8 +639,17 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         // 32-item chunks from a round counter instead of a fixed range; each
         // CTA then counts its own range's destinations after the barrier.
         const bool dynamic = W::kDynamicWork && !solo;
+        // A run that stops at maxRounds must leave an unstepped queue in `in`:
+        // the last round scatters plainly, from P0, so the round before it
+        // fuses only when that lands its items in P0.
+        const uint32_t q = pre ? 0u : round + 1u;  // the round whose step the scatter may apply
+        const bool fuse = kFuse && a.fuseStep && q < a.maxRounds && !(q + 1u == a.maxRounds && xsel == 0u);
+        uint4 *const curItems = curItemsOf(xsel);
+        int32_t *const curDest = curDestOf(xsel);
+        uint4 *const nxtItems = fuse ? (xsel ? a.out : a.in) : a.in;
+        int32_t *const nxtDest = xsel ? a.dest : a.dest2;
         if (dynamic) {
-            unsigned int *ticket = &a.sync->work[round & 1u];
+            unsigned int *ticket = &a.sync->work[it & 1u];
             for (;;) {
                 uint32_t base = 0;
                 if (lane == 0) base = atomicAdd(ticket, 32u);
@@ -407,13 +674,13 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                     a.dest[i] = d;
                 }
             }
-            if (c == 0 && tid == 0) a.sync->work[(round + 1u) & 1u] = 0u;  // next round's counter
+            if (c == 0 && tid == 0) a.sync->work[(it + 1u) & 1u] = 0u;  // next round's counter
         }
-        if (!dynamic && tid == 0 && nt) {
+        if (!dynamic && fresh && tid == 0 && nt) {
             const uint32_t cnt0 = min(kTile, hi - lo);
             issue_bytes(0, sBuf, a.in + (size_t)lo * V, cnt0 * kItemBytes, nullptr, nullptr, 0u);
         }
-        for (uint32_t t = 0; !dynamic && t < nt; ++t) {
+        for (uint32_t t = 0; !dynamic && fresh && t < nt; ++t) {
             const int buf = t & 1;
             const uint32_t b = lo + t * kTile;
             const uint32_t cnt = min(kTile, hi - b);
@@ -435,13 +702,12 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 int32_t d = -1;
                 if (valid) {
                     uint4 w[V];
-#pragma unroll
-                    for (int q = 0; q < V; ++q) w[q] = sItems[j * V + q];
+                    if constexpr (W::kAppendRetired) load_step<W>(sItems, j, w);
+                    else load_item_rot<V>(sItems, j, w);  // retire() takes the whole item
                     const int32_t rank = rf::rankOf(sOff, R, b + j);
                     d = work.step(w, rank, round, sWork);
                     if (d >= 0) {
-#pragma unroll
-                        for (int q = 0; q < V; ++q) sItems[j * V + q] = w[q];
+                        store_step<W>(sItems, j, w);
                     } else if (W::kAppendRetired) {
                         d = R;  // the retirement digit: scattered to the sink in phase 3
                     } else {
@@ -458,28 +724,56 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             if (tid == 0) bulk_s2g(a.out + (size_t)b * V, sItems, cnt * kItemBytes);
         }
         if (tid == 0) bulk_wait_all();
-        if (logRound) a.roundLog[7 * round + 1] = globaltimer();
+        if (logRound && fresh) a.roundLog[7 * round + 1] = globaltimer();
         if (dynamic) {
             fence_proxy_async_global();
             if (!round_barrier()) {
                 failed = true;
                 break;
             }
-            // count the destinations of this CTA's range
-            for (uint32_t b = lo; b < hi; b += kRoundsBlock) {
-                const uint32_t i = b + tid;
-                const int32_t d = i < hi ? __ldcg(a.dest + i) : -1;
-                const int key = (uint32_t)d < (uint32_t)D ? d : D;
-                const unsigned peers = peers_of(key, nbits);
-                if (key < D && lane == __ffs(peers) - 1) atomicAdd(&sTot[key], (uint32_t)__popc(peers));
+        }
+        if (dynamic || !fresh) {
+            // count the destinations of this CTA's range into per-warp rows:
+            // 16-byte loads (lo is a multiple of 16 items), four in flight
+            // per thread; the padded array covers the last vector's tail
+            for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
+            __syncwarp();
+            const int4 *dv = reinterpret_cast<const int4 *>(curDest + lo);
+            const uint32_t nv = (hi - lo + 3u) / 4u;
+            for (uint32_t v0 = 0; v0 < nv; v0 += 4u * kRoundsBlock) {
+                int4 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t v = v0 + (uint32_t)u * kRoundsBlock + tid;
+                    x[u] = v < nv ? __ldcg(dv + v) : make_int4(-1, -1, -1, -1);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t i = lo + 4u * (v0 + (uint32_t)u * kRoundsBlock + tid);
+                    const int32_t e4[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        if (i + m < hi && (uint32_t)e4[m] < (uint32_t)D) atomicAdd(&wc[warp * D + e4[m]], 1u);
+                }
             }
             __syncthreads();
+            for (int e = tid; e < D; e += kRoundsBlock) {
+                uint32_t sum = 0;
+#pragma unroll
+                for (int ww = 0; ww < kRoundsWarps; ++ww) sum += wc[ww * D + e];
+                sTot[e] += sum;
+            }
+            __syncthreads();
+            if (logRound && !fresh) a.roundLog[7 * round + 1] = globaltimer();
         }
         if (!failed) {
             for (int e = tid; e < D; e += kRoundsBlock) {
                 const uint32_t v = sTot[e];
                 a.tot[(size_t)c * Dp + e] = v;
-                if (v) atomicAdd(&a.total[(round & 1u) * D + e], v);
+                if (v) {
+                    atomicAdd(&a.total[(it & 1u) * D + e], v);
+                    atomicAdd(&a.grpTot[((it & 1u) * kSyncGroups + grp) * Dp + e], v);
+                }
             }
         }
         fence_proxy_async_global();
@@ -491,24 +785,22 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
 
         // ---- phase 2: offsets, next count, this CTA's base per destination -----
         for (int e = tid; e < D; e += kRoundsBlock) {
-            dStart[e] = a.total[(round & 1u) * D + e];
+            dStart[e] = a.total[(it & 1u) * D + e];
             dBase[e] = 0u;
         }
-        const uint32_t retiredNow = W::kAppendRetired ? a.total[(round & 1u) * D + R] : 0u;
+        const uint32_t retiredNow = W::kAppendRetired ? a.total[(it & 1u) * D + R] : 0u;
         const uint32_t nNext = rounds_block_scan(dStart, R, tmp);  // ranks only
         if (W::kAppendRetired && tid == 0) dStart[R] = (uint32_t)retiredSoFar;
         {
-            // counts of CTAs 0 .. c-1, staged a block of rows at a time
+            // counts of CTAs 0 .. c-1: the totals of the groups before this
+            // CTA's group, then the rows of the CTAs before it in its group,
+            // staged by bulk copies (a CTA with nothing to scatter needs no base)
             const int groups = D >= kRoundsBlock ? 1 : kRoundsBlock / D;
-            // (a CTA with nothing to scatter needs no base)
-            const uint32_t rowsNeeded = nt ? (uint32_t)c : 0u;
-            for (uint32_t r0 = 0; r0 < rowsNeeded && !failed; r0 += rowsPerStage) {
-                const uint32_t rows = min(rowsPerStage, rowsNeeded - r0);
-                if (tid == 0) issue_bytes(0, sRows, a.tot + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
-                if (!wait(0)) {
-                    failed = true;
-                    break;
-                }
+            const uint32_t gRows = nt ? (uint32_t)grp : 0u;
+            const uint32_t mRows = nt ? (uint32_t)(c - grpStart) : 0u;
+            const uint32_t *gSrc = a.grpTot + (size_t)(it & 1u) * kSyncGroups * Dp;
+            const uint32_t *mSrc = a.tot + (size_t)grpStart * Dp;
+            auto add_rows = [&](uint32_t rows) {
                 for (int t = tid; t < groups * D; t += kRoundsBlock) {
                     const int e = t % D, g = t / D;
                     uint32_t sum = 0;
@@ -516,24 +808,49 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                     if (sum) atomicAdd(&dBase[e], sum);
                 }
                 __syncthreads();
+            };
+            if (gRows + mRows <= rowsPerStage) {
+                if (gRows + mRows) {
+                    if (tid == 0) {
+                        if (gRows)
+                            issue_bytes(0, sRows, gSrc, gRows * Dp * 4u, sRows + gRows * Dp, mSrc, mRows * Dp * 4u);
+                        else
+                            issue_bytes(0, sRows, mSrc, mRows * Dp * 4u, nullptr, nullptr, 0u);
+                    }
+                    if (!wait(0)) failed = true;
+                    else add_rows(gRows + mRows);
+                }
+            } else {
+                for (int seg = 0; seg < 2 && !failed; ++seg) {
+                    const uint32_t segRows = seg ? mRows : gRows;
+                    const uint32_t *src = seg ? mSrc : gSrc;
+                    for (uint32_t r0 = 0; r0 < segRows && !failed; r0 += rowsPerStage) {
+                        const uint32_t rows = min(rowsPerStage, segRows - r0);
+                        if (tid == 0) issue_bytes(0, sRows, src + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
+                        if (!wait(0)) failed = true;
+                        else add_rows(rows);
+                    }
+                }
             }
             __syncthreads();
             for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dStart[e];
         }
         if (c == 0) {
             for (int e = tid; e < R; e += kRoundsBlock) a.inOffset[e] = dStart[e];
-            for (int e = tid; e < D; e += kRoundsBlock) a.total[((round + 1u) & 1u) * D + e] = 0u;
+            for (int e = tid; e < D; e += kRoundsBlock) a.total[((it + 1u) & 1u) * D + e] = 0u;
+            for (int e = tid; e < kSyncGroups * Dp; e += kRoundsBlock)
+                a.grpTot[(size_t)((it + 1u) & 1u) * kSyncGroups * Dp + e] = 0u;
             if (tid == 0) a.inOffset[R] = nNext;
         }
-        forwarded += nNext;
+        if (!pre) forwarded += nNext;
         retiredSoFar += retiredNow;
         __syncthreads();
 
         // ---- phase 3: stable scatter of this CTA's range -----------------------
         auto issue3 = [&](int buf, uint32_t bb) {
             const uint32_t cc = min(kTile, hi - bb);
-            issue_bytes(buf, sBuf + buf * kTileVecs, a.out + (size_t)bb * V, cc * kItemBytes,
-                        sDst + buf * (kTile + 4u), a.dest + bb, ((cc + 3u) & ~3u) * 4u);
+            issue_bytes(buf, sBuf + buf * kTileVecs, curItems + (size_t)bb * V, cc * kItemBytes,
+                        sDst + buf * (kTile + 4u), curDest + bb, ((cc + 3u) & ~3u) * 4u);
         };
         if (tid == 0 && nt && !failed) issue3(0, lo);
         for (uint32_t t = 0; t < nt && !failed; ++t) {
@@ -546,64 +863,27 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 failed = true;
                 break;
             }
-            const int32_t *dts = sDst + buf * (kTile + 4u);
-            int myD[kK];
-            uint32_t myR[kK];
-#pragma unroll
-            for (int k = 0; k < kK; ++k) {
-                const uint32_t idx = (uint32_t)(warp * 32 * kK + k * 32 + lane);
-                const int32_t d = idx < cnt ? dts[idx] : -1;
-                const bool valid = (uint32_t)d < (uint32_t)D;
-                const int key = valid ? d : D;
-                const unsigned peers = peers_of(key, nbits);
-                const int leader = __ffs(peers) - 1;
-                uint32_t old = 0;
-                if (valid && lane == leader) {
-                    old = wc[warp * D + d];
-                    wc[warp * D + d] = old + (uint32_t)__popc(peers);
-                }
-                old = __shfl_sync(0xFFFFFFFFu, old, leader);
-                __syncwarp();
-                myD[k] = valid ? d : -1;
-                myR[k] = old + (uint32_t)__popc(peers & lanemask_lt());
-            }
-            __syncthreads();
-            for (int e = tid; e < D; e += kRoundsBlock) {
-                uint32_t sum = 0;
-#pragma unroll
-                for (int ww = 0; ww < kRoundsWarps; ++ww) {
-                    const uint32_t v = wc[ww * D + e];
-                    wc[ww * D + e] = sum;
-                    sum += v;
-                }
-                dCnt[e] = sum;
-                dStart[e] = sum;
-            }
-            const uint32_t nValid = rounds_block_scan(dStart, D, tmp);
-#pragma unroll
-            for (int k = 0; k < kK; ++k) {
-                if (myD[k] >= 0) {
-                    const int d = myD[k];
-                    const uint32_t within = wc[warp * D + d] + myR[k];
-                    const uint32_t slot = dStart[d] + within;
-                    slotSrc[slot] = (uint16_t)(warp * 32 * kK + k * 32 + lane);
-                    slotDst[slot] = (dBase[d] + within) | (W::kAppendRetired && d == R ? kRetFlag : 0u);
-                }
-            }
-            __syncthreads();
-            const uint4 *sItems = sBuf + buf * kTileVecs;
-            const uint32_t total = nValid * V;
-            for (uint32_t v = tid; v < total; v += kRoundsBlock) {
-                const uint32_t slot = v / V;
-                const uint32_t part = v - slot * V;
+            int32_t *dts = sDst + buf * (kTile + 4u);
+            uint4 *sItems = sBuf + buf * kTileVecs;
+            const uint32_t nValid = rank_tile(sItems, dts, cnt, fuse, q, false);
+            // one item per thread, in slot order; its vectors in the rotated
+            // order (spreads the staged reads over the banks)
+            for (uint32_t slot = tid; slot < nValid; slot += kRoundsBlock) {
                 const uint32_t dst = slotDst[slot];
-                const uint4 val = sItems[(uint32_t)slotSrc[slot] * V + part];
-                if (W::kAppendRetired && (dst & kRetFlag)) {
-                    const uint32_t r = dst & ~kRetFlag;
-                    if (r < a.retiredCap) a.retiredOut[(size_t)r * V + part] = val;
-                } else {
-                    a.in[(size_t)dst * V + part] = val;
+                const uint32_t src = slotSrc[slot];
+                const uint32_t rot = tile_rot<V>(src);
+                const bool ret = W::kAppendRetired && (dst & kRetFlag);
+                const uint32_t pos = dst & ~kRetFlag;
+                uint4 *to = ret ? (pos < a.retiredCap ? a.retiredOut + (size_t)pos * V : nullptr)
+                                : nxtItems + (size_t)pos * V;
+                if (to) {
+#pragma unroll
+                    for (int qq = 0; qq < V; ++qq) {
+                        const uint32_t p = (uint32_t)qq ^ rot;
+                        to[p] = sItems[src * V + p];
+                    }
                 }
+                if (kFuse && fuse && !ret) nxtDest[pos] = dts[src];
             }
             __syncthreads();
             for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dCnt[e];
@@ -620,6 +900,17 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         }
         if (logRound) a.roundLog[7 * round + 4] = globaltimer();
         n = nNext;
+        fresh = !fuse;
+        xsel = fuse ? xsel ^ 1u : 0u;
+        if (pre) pre = false;
+        else ++round;
+    }
+    if (a.seedCount && c == 0) {
+        // the seeded out-queue has been consumed; with nothing seeded the
+        // incoming queue is empty
+        if (pre)
+            for (int e = tid; e <= R; e += kRoundsBlock) a.inOffset[e] = 0u;
+        if (tid == 0) *a.seedCount = 0ull;
     }
     if (c == 0 && tid == 0) {
         a.result[0] = round;
@@ -632,13 +923,23 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
 }
 
 // Host side: one cooperative launch of rounds_kernel<W> over the context's
-// queues, starting from its current incoming queue.  res (host) receives
-// {rounds, forwarded, status, 0}.  Waits for the stream.
+// queues, starting from its current incoming queue, or (seeded) from its
+// out-queue with the items' first ranks as destinations.  res (host)
+// receives {rounds, forwarded, status, retired}.  Waits for the stream.
 template <class W>
 rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStream_t s,
                         unsigned long long *roundLog, uint32_t roundLogCap, uint4 *retiredOut,
-                        unsigned long long retiredCap, unsigned long long *retiredCountOut, unsigned long long res[4])
+                        unsigned long long retiredCap, unsigned long long *retiredCountOut, unsigned long long res[4],
+                        bool stepOnArrival = false, bool seeded = false)
 {
+    if ((seeded || stepOnArrival) && !W::kFuseStep) {
+        set_error("persistent rounds: the policy does not step on arrival");
+        return RF_ERR_ARG;
+    }
+    if (seeded && !stepOnArrival) {
+        set_error("persistent rounds: a seeded start needs steps on arrival");
+        return RF_ERR_ARG;
+    }
     const uint32_t itemBytes = 16u * W::V;
     if (ctx->itemBytes != itemBytes) {
         set_error("persistent rounds: the workload moves %u-byte items, the context %u", itemBytes,
@@ -671,9 +972,12 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     }
     const int G = ctx->numSMs * perSM;
     const size_t totBytes = (size_t)G * rounds_row_stride(D) * sizeof(uint32_t);
-    const size_t totalBytes = (size_t)2 * D * sizeof(unsigned int);
-    const size_t tailBytes = totalBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
-    if (rf_status st = ensure_rounds_scratch(ctx, totBytes + tailBytes)) return st;
+    const size_t totalBytes = rounds_align_sz((size_t)2 * D * sizeof(unsigned int), 16);
+    const size_t grpBytes = (size_t)2 * kSyncGroups * rounds_row_stride(D) * sizeof(uint32_t);
+    const size_t tailBytes = totalBytes + grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
+    // second destination array (step on arrival), padded like ctx->dest
+    const size_t dest2Bytes = W::kFuseStep ? rounds_align_sz((size_t)(ctx->capacity + 3) / 4 * 16 + 16, 256) : 0;
+    if (rf_status st = ensure_rounds_scratch(ctx, rounds_align_sz(totBytes + tailBytes, 256) + dest2Bytes)) return st;
     unsigned char *base = static_cast<unsigned char *>(ctx->roundsScratch);
     RoundsArgs a;
     a.in = static_cast<uint4 *>(ctx->in);
@@ -682,14 +986,18 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.inOffset = ctx->inOffset;
     a.tot = reinterpret_cast<uint32_t *>(base);
     a.total = reinterpret_cast<unsigned int *>(base + totBytes);
-    a.sync = reinterpret_cast<GridSync *>(base + totBytes + totalBytes);
-    a.result = reinterpret_cast<unsigned long long *>(base + totBytes + totalBytes + sizeof(GridSync));
+    a.grpTot = reinterpret_cast<uint32_t *>(base + totBytes + totalBytes);
+    a.sync = reinterpret_cast<GridSync *>(base + totBytes + totalBytes + grpBytes);
+    a.result = reinterpret_cast<unsigned long long *>(base + totBytes + totalBytes + grpBytes + sizeof(GridSync));
+    a.dest2 = W::kFuseStep ? reinterpret_cast<int32_t *>(base + rounds_align_sz(totBytes + tailBytes, 256)) : nullptr;
     a.numActiveOut = &ctx->dev->numActive;
     a.roundLog = roundLog;
     a.roundLogCap = roundLog ? roundLogCap : 0u;
     a.retiredOut = retiredOut;
     a.retiredCap = retiredOut ? retiredCap : 0ull;
     a.retiredCountOut = retiredCountOut;
+    a.seedCount = seeded ? &ctx->dev->outCount : nullptr;
+    a.fuseStep = stepOnArrival ? 1u : 0u;
     a.maxRounds = maxRounds;
     a.numRanks = R;
     RF_CUDA(cudaMemsetAsync(base + totBytes, 0, tailBytes, s));

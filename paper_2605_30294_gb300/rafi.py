@@ -82,7 +82,7 @@ _SIGS = {
     "rf_c1_work": [_P, _u32, _u32, _i32, _f64, _i32, _i32, _i32, _P, _P, _u64, _i32, _P],
     "rf_c1_run": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _i32, _u32, _P,
                   _PU64, _PU64],
-    "rf_c1_run_batched": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _u32, _P,
+    "rf_c1_run_batched": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _i32, _u32, _P,
                           _PU64, _PU64, _P, _u32],
     "rf_c0_make_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c2_make_bricks": [_P, _i32, _i32, _P, _P],
@@ -265,12 +265,13 @@ def rf_c1_run(ctx: int, items, n: int, seed: int, mode: int, zipf_s: float, grid
 
 def rf_c1_run_batched(ctx: int, items, n: int, seed: int, mode: int, zipf_s: float, grid, retired,
                       host_memory: bool = False, max_rounds: int = 100000, stream=None, round_log=None,
-                      round_log_cap: int = 0, allow=()):
+                      round_log_cap: int = 0, allow=(), step_on_arrival: bool = True):
     """Persistent-kernel microbenchmark; returns (status, retired_count, rounds, forwarded)."""
     gx, gy, gz = grid
     cnt, rounds, fwd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     st = lib().rf_c1_run_batched(ctx, ptr(items), n, seed, mode, zipf_s, gx, gy, gz, ptr(retired),
-                                 ctypes.byref(cnt), int(host_memory), max_rounds, stream_handle(stream),
+                                 ctypes.byref(cnt), int(host_memory), int(step_on_arrival), max_rounds,
+                                 stream_handle(stream),
                                  ctypes.byref(rounds), ctypes.byref(fwd), ptr(round_log), round_log_cap)
     _check("rf_c1_run_batched", st, allow)
     return st, cnt.value, rounds.value, fwd.value

@@ -151,7 +151,7 @@ def test_max_rounds_guard():
 # ---------------------------------------------------------------------------
 # batched form: all rounds in one persistent kernel
 # ---------------------------------------------------------------------------
-def _run_batched(items, seed, mode, host=False, max_rounds=100000, ctx=None, allow=()):
+def _run_batched(items, seed, mode, host=False, max_rounds=100000, ctx=None, allow=(), fuse=True):
     n = len(items)
     s = stream()
     own = ctx is None
@@ -160,23 +160,25 @@ def _run_batched(items, seed, mode, host=False, max_rounds=100000, ctx=None, all
         if host:
             retired = np.zeros((n, 16), np.uint32)
             st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, items.ctypes.data, n, seed, mode, 1.1, GRID,
-                                                          retired.ctypes.data, True, max_rounds, s, allow=allow)
+                                                          retired.ctypes.data, True, max_rounds, s, allow=allow,
+                                                          step_on_arrival=fuse)
             return retired[:cnt], rounds, fwd, st
         retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
         st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, to_dev(items), n, seed, mode, 1.1, GRID, retired,
-                                                      False, max_rounds, s, allow=allow)
+                                                      False, max_rounds, s, allow=allow, step_on_arrival=fuse)
         return retired[:cnt].cpu().numpy().view(np.uint32), rounds, fwd, st
     finally:
         if own:
             ctx.close()
 
 
+@pytest.mark.parametrize("fuse", [True, False], ids=["step_on_arrival", "step_in_place"])
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n", [1, 777, 20011, 300007])
-def test_batched_matches_oracle_multiset(mode, n):
+def test_batched_matches_oracle_multiset(mode, n, fuse):
     seed = 5
     items = inputs.c1_items(n, seed=seed)
-    got, rounds, fwd, st = _run_batched(items, seed, mode)
+    got, rounds, fwd, st = _run_batched(items, seed, mode, fuse=fuse)
     final, hops, _, _ = oracle.c1_walk(items, R, seed, mode, grid=GRID)
     assert st == rafi.RF_OK and len(got) == n
     assert rounds == int(hops.max()) + 1
@@ -184,27 +186,33 @@ def test_batched_matches_oracle_multiset(mode, n):
     np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
 
 
+@pytest.mark.parametrize("fuse", [True, False], ids=["step_on_arrival", "step_in_place"])
 @pytest.mark.parametrize("mode", MODES)
-def test_batched_round_queues_bit_exact(mode):
+@pytest.mark.parametrize("n,stops", [(50000, (0, 1, 2, 3, 7, 8)), (2000, (9, 15, 16, 30, 45))],
+                         ids=["grid_rounds", "one_cta_tail"])
+def test_batched_round_queues_bit_exact(mode, fuse, n, stops):
     # stopping after k rounds leaves round k's incoming queue, in the serial order
-    n, seed = 50000, 8
+    # (with steps on arrival: whether the last fused scatter lands in either
+    # queue, and, for the small run, after rounds kept in one CTA's shared memory)
+    seed = 8
     items = inputs.c1_items(n, seed=seed)
     s = stream()
-    for k in (0, 1, 3, 7):
+    for k in stops:
         want = oracle.c1_rounds(items, R, seed, mode, grid=GRID, dump_round=k)
         with rafi.Context(R, 64, n) as ctx:
             got, rounds, fwd, st = _run_batched(items, seed, mode, max_rounds=k, ctx=ctx,
-                                                allow=(rafi.RF_ERR_MAX_ROUNDS,))
+                                                allow=(rafi.RF_ERR_MAX_ROUNDS,), fuse=fuse)
             assert rounds == k
             assert fwd == int(want["active"][1:k + 1].sum())
             assert rafi.rf_num_active(ctx.handle) == int(want["active"][k])
             q, off = _queue(ctx, n, s)
         np.testing.assert_array_equal(off.astype(np.uint64), want["dump_offsets"])
         np.testing.assert_array_equal(q, want["dump_items"])
-        # the retired items so far are the oracle's first k rounds of retirements
+        # the retired items so far are the oracle's first k rounds of retirements,
+        # in its order (round by round, queue order within a round)
         ret = int(want["retired"][:k].sum())
         assert len(got) == ret
-        np.testing.assert_array_equal(canonical_rows(got), canonical_rows(want["retired_items"][:ret]))
+        np.testing.assert_array_equal(got, want["retired_items"][:ret])
 
 
 def test_batched_host_memory_and_round_log():
@@ -237,10 +245,15 @@ def test_batched_full_size_matches_plain():
     with rafi.Context(R, 64, n) as ctx:
         ra = torch.zeros((n, 16), dtype=torch.int32, device=dev())
         rb = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        rc = torch.zeros((n, 16), dtype=torch.int32, device=dev())
         for mode in MODES:
             st, ca, roa, fa = rafi.rf_c1_run(ctx.handle, d_items, n, seed, mode, 1.1, GRID, ra, stream=s)
             st, cb, rob, fb = rafi.rf_c1_run_batched(ctx.handle, d_items, n, seed, mode, 1.1, GRID, rb, stream=s)
-            assert (ca, roa, fa) == (cb, rob, fb) and ca == n
+            st, cc, roc, fc = rafi.rf_c1_run_batched(ctx.handle, d_items, n, seed, mode, 1.1, GRID, rc, stream=s,
+                                                     step_on_arrival=False)
+            assert (ca, roa, fa) == (cb, rob, fb) == (cc, roc, fc) and ca == n
+            # both batched forms retire in the same deterministic order
+            assert torch.equal(rb, rc)
             ka = canonical_rows(ra.cpu().numpy().view(np.uint32)[:, [0, 1, 13, 14, 15]])
             kb = canonical_rows(rb.cpu().numpy().view(np.uint32)[:, [0, 1, 13, 14, 15]])
             np.testing.assert_array_equal(ka, kb)
