@@ -47,6 +47,7 @@ GRID = (4, 4, 4)
 SEED = 1
 ITEM_BYTES = 64
 MODES = (0, 1, 2)  # uniform, Zipf 1.1, 6-neighbour torus
+LAW_NAMES = {0: "uniform", 1: "zipf_1.1", 2: "torus_6"}
 WORKLOAD = ("forwarding microbenchmark: 2^24 x 64-byte items (Philox payloads), 64 logical ranks, "
             "destinations uniform / Zipf s=1.1 / 6-neighbour 4x4x4 torus, retire p=0.1, seed 1; "
             "one step = the three runs, each seeded and run to zero active items")
@@ -257,10 +258,13 @@ def phase_rates(log_rows, item_bytes, min_items=1 << 20):
     if small.any():
         out["us_per_round_lt_2^20"] = float((lg[small, 4] - lg[small, 0]).mean() * 1e-3)
     # rounds of at most 1024 items run on one CTA; the ones between run on the whole grid
-    for name, sel in (("solo_le_1024", lg[:, 5] <= 1024), ("grid_lt_2^20", small & (lg[:, 5] > 1024))):
+    for name, sel in (("solo_le_1024", lg[:, 5] <= 1024), ("grid_lt_2^20", small & (lg[:, 5] > 1024)),
+                      ("ge_2^20", big)):
         if sel.any():
             out["rounds_" + name] = int(sel.sum())
             out["us_per_round_" + name] = float((lg[sel, 4] - lg[sel, 0]).mean() * 1e-3)
+            # as seen by CTA 0: count (or step), first barrier, offsets + scatter, second barrier
+            out["us_split_" + name] = [float(x) for x in np.diff(lg[sel, :5], axis=1).mean(axis=0) * 1e-3]
     out["round_ms_total"] = float((lg[-1, 4] - lg[0, 0]) * 1e-6) if len(lg) else 0.0
     return out
 
@@ -416,9 +420,12 @@ def run_ours(args):
     s = torch.cuda.current_stream(dev)
     ctx = rafi.Context(RANKS, ITEM_BYTES, n)
 
-    def step(batched, round_log=None, fuse=True):
+    def step(batched, round_log=None, fuse=True, per_mode=None):
         fwd = 0
         for mode in MODES:
+            if per_mode is not None:
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record(s)
             if batched:
                 st, cnt, rounds, f = rafi.rf_c1_run_batched(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired,
                                                             stream=s, round_log=round_log,
@@ -429,6 +436,9 @@ def run_ours(args):
                                                     stream=s)
             if cnt != n:
                 raise RuntimeError(f"mode {mode}: {cnt} of {n} items retired")
+            if per_mode is not None:
+                ev[1].record(s)
+                per_mode.setdefault(mode, []).append((ev, f))
             fwd += f
         return fwd
 
@@ -437,17 +447,25 @@ def run_ours(args):
         rafi.rf_get_timing(ctx.handle, reset=True)
         barrier()
         launches0 = rafi.rf_launch_count()
+        per_mode = {}
         with ClockSampler(gpu_id) as clocks:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             fwd = 0
             for _ in range(steps):
-                fwd += step(batched, fuse=fuse)
+                fwd += step(batched, fuse=fuse, per_mode=per_mode)
             e1.record(s)
             barrier()
         launches = rafi.rf_launch_count() - launches0
         t = rafi.rf_get_timing(ctx.handle, reset=True)
         rafi.rf_set_timing(ctx.handle, False)
+        # per destination law: ms per run and forwarded items/s (events around each run)
+        laws = {}
+        for mode, runs in per_mode.items():
+            ms_law = sum(ev[0].elapsed_time(ev[1]) for ev, _ in runs)
+            f_law = sum(f for _, f in runs)
+            laws[LAW_NAMES[mode]] = {"ms_per_run": ms_law / len(runs), "items_per_s": f_law / (ms_law * 1e-3)}
+        timed.laws = laws
         return fwd, e0.elapsed_time(e1), t, launches, clocks.summary()
 
     props = torch.cuda.get_device_properties(dev)
@@ -460,11 +478,13 @@ def run_ours(args):
         step(True)
         step(False)
     fwd, ms, tb, launches, clocks = timed(True, args.steps)
+    laws_batched = timed.laws
     p_steps = max(3, args.steps // 4)
     p_fwd, p_ms, tp, p_launches, p_clocks = timed(False, p_steps)
     # the persistent form with the work step as its own pass (no step on arrival)
     step(True, fuse=False)
     u_fwd, u_ms, tu, _, _ = timed(True, p_steps, fuse=False)
+    laws_in_place = timed.laws
 
     # per-round phase rates of the persistent kernel (one extra, untimed step)
     step(True, round_log=log)
@@ -550,8 +570,9 @@ def run_ours(args):
         "phases_from_round_log": {**rates,
                                   "scatter_frac_ge_2^20": rates.get("scatter_gbs_ge_2^20", 0.0) / peak,
                                   "round_frac_ge_2^20": rates.get("round_gbs_ge_2^20", 0.0) / peak},
+        "per_law": laws_batched,
         "batched_step_in_place": {
-            "value": u_fwd / (u_ms / 1e3), "ms_per_step": u_ms / p_steps, "steps": p_steps,
+            "value": u_fwd / (u_ms / 1e3), "ms_per_step": u_ms / p_steps, "steps": p_steps, "per_law": laws_in_place,
             "form": "persistent kernel; each round steps every item in its queue slot, then scatters",
             "roofline": {"achieved": u_ach, "frac": u_ach / peak,
                          "alg_bytes": "2 x 64 B per queued item for the step pass, 2 x 64 B per delivery"}},

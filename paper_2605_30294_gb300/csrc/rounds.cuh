@@ -866,24 +866,22 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             int32_t *dts = sDst + buf * (kTile + 4u);
             uint4 *sItems = sBuf + buf * kTileVecs;
             const uint32_t nValid = rank_tile(sItems, dts, cnt, fuse, q, false);
-            // one item per thread, in slot order; its vectors in the rotated
-            // order (spreads the staged reads over the banks)
-            for (uint32_t slot = tid; slot < nValid; slot += kRoundsBlock) {
+            // consecutive threads write consecutive 16-byte vectors of the
+            // destination-grouped tile (coalesced runs per destination)
+            const uint32_t total = nValid * V;
+            for (uint32_t v = tid; v < total; v += kRoundsBlock) {
+                const uint32_t slot = v / V;
+                const uint32_t part = v - slot * V;
                 const uint32_t dst = slotDst[slot];
                 const uint32_t src = slotSrc[slot];
-                const uint32_t rot = tile_rot<V>(src);
-                const bool ret = W::kAppendRetired && (dst & kRetFlag);
-                const uint32_t pos = dst & ~kRetFlag;
-                uint4 *to = ret ? (pos < a.retiredCap ? a.retiredOut + (size_t)pos * V : nullptr)
-                                : nxtItems + (size_t)pos * V;
-                if (to) {
-#pragma unroll
-                    for (int qq = 0; qq < V; ++qq) {
-                        const uint32_t p = (uint32_t)qq ^ rot;
-                        to[p] = sItems[src * V + p];
-                    }
+                const uint4 val = sItems[src * V + part];
+                if (W::kAppendRetired && (dst & kRetFlag)) {
+                    const uint32_t r = dst & ~kRetFlag;
+                    if (r < a.retiredCap) a.retiredOut[(size_t)r * V + part] = val;
+                } else {
+                    nxtItems[(size_t)dst * V + part] = val;
+                    if (kFuse && fuse && part == 0u) nxtDest[dst] = dts[src];
                 }
-                if (kFuse && fuse && !ret) nxtDest[pos] = dts[src];
             }
             __syncthreads();
             for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dCnt[e];
