@@ -262,8 +262,9 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
  * stepOnArrival == 0: the seed exchange runs first; each round's work step
  * reads and writes back every item in its queue slot before the scatter.
  * Queue order is deterministic either way: round k's incoming queue is the
- * one of rf_c1_run with deterministic != 0.  Rounds of at most 1024 items
- * run on one CTA (the others return).  roundLog (device, 7 x roundLogCap
+ * one of rf_c1_run with deterministic != 0.  Rounds of at most 2048 items
+ * run on one CTA (the others return); with steps on arrival, rounds of at
+ * most 512 items keep the whole queue in that CTA's shared memory.  roundLog (device, 7 x roundLogCap
  * words, nullable) receives per round, as seen by CTA 0, the %globaltimer ns
  * at round start, end of its work step (or count), after the first barrier,
  * end of its scatter and after the second barrier, then the incoming and the
@@ -392,6 +393,49 @@ rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int3
 rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, float sigmaMax, int32_t numViews,
                        const float *cams, const int32_t *sizes, int32_t spp, uint32_t seed, float *score,
                        int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded);
+
+/* --- multi-phase exchange with three item types (Sec. 5.5) -------------- */
+
+/* The communication pattern of the paper's distributed N-body code: three
+ * contexts of different item types on one stream.  A particle context moves
+ * 32-byte particles {x, y, z (uint32 fixed point on the periodic unit cube),
+ * vx, vy, vz (int32), m, id}; a node context moves 64-byte nodes {M, X, Y, Z
+ * (uint64: mass and mass-weighted coordinate sums), count, src, code (0 =
+ * root, 1 + o = octant o), level, 4 pad words}; a request context moves
+ * 16-byte requests {requester, target, code, level}.  All three have
+ * numRanks = gx * gy * gz ranks (powers of two); rank of a position = the
+ * top log2(g) bits of each coordinate, x fastest.  nodes (device) holds
+ * numRanks x 9 x 5 uint64: per rank its root, then octants 0..7 (the bit
+ * after the rank bits, x lowest), as {M, X, Y, Z, count}.
+ * Every call is asynchronous on stream except rf_mp_step.  Errors: RF_ERR_ARG
+ * for a context of the wrong item size, mismatched rank counts or devices, a
+ * grid that is not gx x gy x gz powers of two or NULL buffers. */
+
+/* Emit n particles (device, n x 32 bytes) into the particle context's
+ * out-queue, each to the rank owning its position. */
+rf_status rf_mp_seed(rf_ctx *particles, const void *items, uint64_t n, int32_t gx, int32_t gy, int32_t gz,
+                     void *stream);
+/* Migration: every incoming particle moves by its velocity (wrapping) and is
+ * forwarded to the rank owning its new position. */
+rf_status rf_mp_migrate(rf_ctx *particles, int32_t gx, int32_t gy, int32_t gz, void *stream);
+/* Local trees of the incoming particles of every rank into nodes (exact). */
+rf_status rf_mp_tree(rf_ctx *particles, int32_t gx, int32_t gy, int32_t gz, unsigned long long *nodes,
+                     void *stream);
+/* Every rank's root node emitted once to every other rank (numRanks - 1
+ * emits per rank) into the node context. */
+rf_status rf_mp_broadcast(rf_ctx *nodeCtx, const unsigned long long *nodes, void *stream);
+/* For every incoming root at rank r from a non-empty rank s that is one of
+ * r's 26 torus neighbours, a request {r, s, 0, 0} emitted to s. */
+rf_status rf_mp_request(rf_ctx *nodeCtx, rf_ctx *requestCtx, int32_t gx, int32_t gy, int32_t gz, void *stream);
+/* For every incoming request at rank s, its non-empty octant nodes (up to 8
+ * emits per request) emitted to the requester. */
+rf_status rf_mp_respond(rf_ctx *requestCtx, rf_ctx *nodeCtx, const unsigned long long *nodes, void *stream);
+/* One protocol step: migrate, exchange particles, trees, broadcast, exchange
+ * nodes, requests, exchange requests, replies, exchange nodes.  delivered
+ * (host, 4 words, nullable) = items delivered by the four exchanges.  Waits
+ * for the stream. */
+rf_status rf_mp_step(rf_ctx *particles, rf_ctx *nodeCtx, rf_ctx *requestCtx, int32_t gx, int32_t gy, int32_t gz,
+                     unsigned long long *nodes, void *stream, uint64_t delivered[4]);
 
 #ifdef __cplusplus
 }

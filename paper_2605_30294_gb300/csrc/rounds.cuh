@@ -124,35 +124,48 @@ __device__ __forceinline__ unsigned peers_of(int key, int nbits)
     return p;
 }
 
+__device__ __forceinline__ unsigned int atom_add_release(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // Bounded grid barrier for a cooperative launch (all CTAs resident), in two
 // levels: CTAs arrive on one of kSyncGroups group counters (separate cache
 // lines), the last CTA of a group arrives on the top counter, and the last
-// group releases everyone by bumping the generation.
+// group releases everyone by publishing the barrier's sequence number.
+// Counters only grow (the launch zeroes them): barrier number `seq` (0, 1,
+// ...) is complete on a group counter at members * (seq + 1) and on the top
+// counter at groups * (seq + 1), so no counter is reset and the critical
+// path is two atomics and one release store.  Arrivals are release
+// operations and the wait an acquire load, which orders every CTA's writes
+// before the barrier with every read after it.
 // Returns false when any CTA has given up; the caller must then return.
-__device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag)
+__device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned int seq)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int ok = 1;
-        const unsigned int g = ld_acquire(&gs->gen);
         const unsigned int G = gridDim.x;
         const unsigned int groups = G < (unsigned)kSyncGroups ? G : (unsigned)kSyncGroups;
         const unsigned int grp = blockIdx.x % groups;
         const unsigned int members = G / groups + (grp < G % groups ? 1u : 0u);
-        __threadfence();
         bool last = false;
-        if (atomicAdd(&gs->group[grp][0], 1u) + 1u == members) {
-            atomicExch(&gs->group[grp][0], 0u);
-            __threadfence();
-            last = atomicAdd(&gs->count, 1u) + 1u == groups;
-        }
+        if (atom_add_release(&gs->group[grp][0], 1u) + 1u == members * (seq + 1u))
+            last = atom_add_acq_rel(&gs->count, 1u) + 1u == groups * (seq + 1u);
         if (last) {
-            atomicExch(&gs->count, 0u);
-            __threadfence();
-            st_release(&gs->gen, g + 1u);
+            st_release(&gs->gen, seq + 1u);
         } else {
             const long long t0 = clock64();
-            while (ld_acquire(&gs->gen) == g) {
+            while (ld_acquire(&gs->gen) < seq + 1u) {
                 if (ld_acquire(&gs->abort)) {
                     ok = 0;
                     break;
@@ -162,7 +175,7 @@ __device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag)
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         if (ld_acquire(&gs->abort)) ok = 0;
@@ -366,7 +379,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     const int Dp = rounds_row_stride(D);
     const RoundsLayout L = rounds_layout(kItemBytes, D, work.smemBytes(), kTile);
     uint4 *sBuf = reinterpret_cast<uint4 *>(smem + L.items);  // two tiles of kTileVecs
-    uint32_t *sRows = reinterpret_cast<uint32_t *>(smem + L.items);
+    uint32_t *sRows = reinterpret_cast<uint32_t *>(smem + L.items) + kTileVecs * 4u;  // tile buffer 1
     int32_t *sDst = reinterpret_cast<int32_t *>(smem + L.dests);  // two tiles of kTile + 4
     uint32_t *wc = reinterpret_cast<uint32_t *>(smem + L.wc);
     uint32_t *dCnt = reinterpret_cast<uint32_t *>(smem + L.cnt);
@@ -384,7 +397,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, c = blockIdx.x;
     const int nbits = 32 - __clz(D);  // keys 0..D (D = no item)
-    const uint32_t rowsPerStage = (2u * kTileVecs * 16u) / (uint32_t)(Dp * 4);
+    const uint32_t rowsPerStage = (kTileVecs * 16u) / (uint32_t)(Dp * 4);
     // prefix groups: kSyncGroups runs of consecutive CTAs
     const int grpSize = (G + kSyncGroups - 1) / kSyncGroups;
     const int grp = c / grpSize, grpStart = grp * grpSize;
@@ -442,10 +455,11 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     };
     // Once a round is this small, CTA 0 finishes the run alone: the other CTAs
     // return and the round barriers become block barriers.
-    constexpr uint32_t kSoloItems = 2u * kTile;
+    constexpr uint32_t kSoloItems = 4u * kTile;
     bool solo = false;
+    unsigned int barrierSeq = 0;  // grid barriers passed (every CTA passes the same ones)
     auto round_barrier = [&]() -> bool {
-        if (!solo) return grid_barrier(a.sync, sFlag);
+        if (!solo) return grid_barrier(a.sync, sFlag, barrierSeq++);
         __threadfence();
         __syncthreads();
         return true;
@@ -648,6 +662,16 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         int32_t *const curDest = curDestOf(xsel);
         uint4 *const nxtItems = fuse ? (xsel ? a.out : a.in) : a.in;
         int32_t *const nxtDest = xsel ? a.dest : a.dest2;
+        // stage tile t of this CTA's range (items and destinations) into buffer buf
+        auto issue3 = [&](int buf, uint32_t bb) {
+            const uint32_t cc = min(kTile, hi - bb);
+            issue_bytes(buf, sBuf + buf * kTileVecs, curItems + (size_t)bb * V, cc * kItemBytes,
+                        sDst + buf * (kTile + 4u), curDest + bb, ((cc + 3u) & ~3u) * 4u);
+        };
+        // A stepped queue is final when the round starts: its first tile is
+        // staged now, so the copy overlaps the count pass and the barrier.
+        const bool prefetched = !fresh && !dynamic && nt > 0;
+        if (prefetched && tid == 0) issue3(0, lo);
         if (dynamic) {
             unsigned int *ticket = &a.sync->work[it & 1u];
             for (;;) {
@@ -813,11 +837,11 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 if (gRows + mRows) {
                     if (tid == 0) {
                         if (gRows)
-                            issue_bytes(0, sRows, gSrc, gRows * Dp * 4u, sRows + gRows * Dp, mSrc, mRows * Dp * 4u);
+                            issue_bytes(1, sRows, gSrc, gRows * Dp * 4u, sRows + gRows * Dp, mSrc, mRows * Dp * 4u);
                         else
-                            issue_bytes(0, sRows, mSrc, mRows * Dp * 4u, nullptr, nullptr, 0u);
+                            issue_bytes(1, sRows, mSrc, mRows * Dp * 4u, nullptr, nullptr, 0u);
                     }
-                    if (!wait(0)) failed = true;
+                    if (!wait(1)) failed = true;
                     else add_rows(gRows + mRows);
                 }
             } else {
@@ -826,8 +850,8 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                     const uint32_t *src = seg ? mSrc : gSrc;
                     for (uint32_t r0 = 0; r0 < segRows && !failed; r0 += rowsPerStage) {
                         const uint32_t rows = min(rowsPerStage, segRows - r0);
-                        if (tid == 0) issue_bytes(0, sRows, src + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
-                        if (!wait(0)) failed = true;
+                        if (tid == 0) issue_bytes(1, sRows, src + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
+                        if (!wait(1)) failed = true;
                         else add_rows(rows);
                     }
                 }
@@ -847,12 +871,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         __syncthreads();
 
         // ---- phase 3: stable scatter of this CTA's range -----------------------
-        auto issue3 = [&](int buf, uint32_t bb) {
-            const uint32_t cc = min(kTile, hi - bb);
-            issue_bytes(buf, sBuf + buf * kTileVecs, curItems + (size_t)bb * V, cc * kItemBytes,
-                        sDst + buf * (kTile + 4u), curDest + bb, ((cc + 3u) & ~3u) * 4u);
-        };
-        if (tid == 0 && nt && !failed) issue3(0, lo);
+        if (tid == 0 && nt && !failed && !prefetched) issue3(0, lo);
         for (uint32_t t = 0; t < nt && !failed; ++t) {
             const int buf = t & 1;
             const uint32_t b = lo + t * kTile;
@@ -902,6 +921,11 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         xsel = fuse ? xsel ^ 1u : 0u;
         if (pre) pre = false;
         else ++round;
+    }
+    // let any copy still in flight (a prefetch before a failed barrier) land
+    if (tid == 0) {
+        if (pend0) (void)mbar_wait_bounded(&bar[0], par0);
+        if (pend1) (void)mbar_wait_bounded(&bar[1], par1);
     }
     if (a.seedCount && c == 0) {
         // the seeded out-queue has been consumed; with nothing seeded the
