@@ -391,6 +391,33 @@ def c4_transport(torch, rafi, inputs, s):
     return out
 
 
+def multi_phase(torch, rafi, inputs, s, n=1 << 22, steps=5):
+    """Three contexts on one stream (particles 32 B, nodes 64 B, requests 16 B): one step =
+    migrate + exchange, local trees, root broadcast + exchange, requests + exchange,
+    replies + exchange (rf_mp_step, which reads each exchange's count back)."""
+    grid, R = (4, 4, 4), 64
+    p = inputs.mp_particles(n, seed=5)
+    nodes = torch.zeros((R, 9, 5), dtype=torch.int64, device="cuda")
+    with rafi.Context(R, 32, n) as pc, rafi.Context(R, 64, R * (R - 1) + R * 26 * 8) as nc, \
+            rafi.Context(R, 16, R * 26) as rc:
+        rafi.rf_mp_seed(pc.handle, torch.from_numpy(p.view(np.int32)).cuda(), n, grid, stream=s)
+        rafi.rf_exchange(pc.handle, s)
+        for _ in range(2):
+            rafi.rf_mp_step(pc.handle, nc.handle, rc.handle, grid, nodes, stream=s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        delivered = 0
+        e0.record(s)
+        for _ in range(steps):
+            delivered += sum(rafi.rf_mp_step(pc.handle, nc.handle, rc.handle, grid, nodes, stream=s))
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    return {"workload": f"{n} particles, 4x4x4 ranks, velocities up to 2^-6 of the cube per step",
+            "ms_per_step": ms, "particles_per_s": n / (ms * 1e-3),
+            "items_delivered_per_s": delivered / steps / (ms * 1e-3)}
+
+
 def run_ours(args):
     import torch
 
@@ -523,6 +550,8 @@ def run_ours(args):
     ea = c3_ea(torch, rafi, inputs, s) if not args.skip_extra else None
     torch.cuda.empty_cache()
     transport = c4_transport(torch, rafi, inputs, s) if not args.skip_extra else None
+    torch.cuda.empty_cache()
+    mp = multi_phase(torch, rafi, inputs, s) if not args.skip_extra else None
 
     sec = ms / 1e3
     total_fwd = fwd
@@ -592,6 +621,7 @@ def run_ours(args):
         "streamlines": streamlines,
         "differentiable_ea": ea,
         "delta_tracking": transport,
+        "multi_phase": mp,
         "cpu_baseline": {"value": cpu_v, "unit": "items/s", "cores": 1, "kind": "oracle",
                          "sample": f"{BASELINE_ITEMS} items per destination law, round-by-round oracle, "
                                    f"{cpu_dt:.1f} s"},

@@ -81,6 +81,14 @@ def _load():
             lib.or_c4_render_crop.restype = None
             lib.or_c4_hg_sample.argtypes = [P, ctypes.c_float, ctypes.c_float, P]
             lib.or_c4_hg_sample.restype = None
+            lib.or_mp_owner.argtypes = [u32, u32, u32, P]
+            lib.or_mp_owner.restype = i32
+            lib.or_mp_migrate.argtypes = [P, u64, P, P, P]
+            lib.or_mp_migrate.restype = None
+            lib.or_mp_tree.argtypes = [P, u64, P, P]
+            lib.or_mp_tree.restype = None
+            lib.or_mp_near.argtypes = [i32, i32, P]
+            lib.or_mp_near.restype = i32
             _lib = lib
     return _lib
 
@@ -327,4 +335,78 @@ def c4_hg_sample(d, xi: float, xphi: float) -> np.ndarray:
     d = _c(np.asarray(d, np.float32).reshape(3), np.float32)
     out = np.zeros(3, np.float32)
     _load().or_c4_hg_sample(_p(d), xi, xphi, _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Multi-phase exchange with three item types (Sec. 5.5's protocol:
+# migration, root broadcast, refinement requests, child replies)
+# --------------------------------------------------------------------------
+MP_ROOT_CODE = 0  # node code of a root; child octant o has code 1 + o
+
+
+def _lg(grid):
+    lg = [int(g).bit_length() - 1 for g in grid]
+    assert all(1 << l == g for l, g in zip(lg, grid)), "grid sides must be powers of two"
+    return np.array(lg, dtype=np.int32)
+
+
+def mp_owner(x: int, y: int, z: int, grid) -> int:
+    """Rank owning fixed-point position (x, y, z) on a grid of ranks."""
+    return int(_load().or_mp_owner(x, y, z, _p(_lg(grid))))
+
+
+def mp_migrate(particles: np.ndarray, grid):
+    """Move every particle (n x 8 uint32) by its velocity; returns (moved, owner)."""
+    p = _c(particles, np.uint32).reshape(-1, 8)
+    out = np.zeros_like(p)
+    owner = np.zeros(len(p), np.int32)
+    _load().or_mp_migrate(_p(p), len(p), _p(_lg(grid)), _p(out), _p(owner))
+    return out, owner
+
+
+def mp_tree(particles: np.ndarray, grid) -> np.ndarray:
+    """Per-rank nodes (R x 9 x 5 uint64: M, X, Y, Z, count; root then octants)."""
+    p = _c(particles, np.uint32).reshape(-1, 8)
+    lg = _lg(grid)
+    nodes = np.zeros((1 << int(lg.sum()), 9, 5), np.uint64)
+    _load().or_mp_tree(_p(p), len(p), _p(lg), _p(nodes))
+    return nodes
+
+
+def mp_near(r: int, s: int, grid) -> bool:
+    return bool(_load().or_mp_near(r, s, _p(_lg(grid))))
+
+
+def mp_node_item(nd, src: int, code: int) -> np.ndarray:
+    """The 64-byte node item: M, X, Y, Z as uint64 words, count, source rank, code, level."""
+    w = np.zeros(16, np.uint32)
+    w[0:8] = np.asarray(nd[:4], np.uint64).view(np.uint32)
+    w[8], w[9], w[10], w[11] = int(nd[4]), src, code, 0 if code == MP_ROOT_CODE else 1
+    return w
+
+
+def mp_protocol(particles: np.ndarray, grid):
+    """One step of the protocol, per rank: the migrated particles it owns, the
+    roots it receives (every other rank's), the requests it receives (from
+    near peers whose copy of its root is non-empty) and the children it
+    receives (the non-empty octants of every near peer it asked)."""
+    moved, owner = mp_migrate(particles, grid)
+    R = int(np.prod(grid))
+    nodes = mp_tree(moved, grid)
+    near = np.array([[mp_near(r, s, grid) for s in range(R)] for r in range(R)])
+    out = {"moved": moved, "owner": owner, "nodes": nodes,
+           "particles_at": [moved[owner == r] for r in range(R)], "roots_at": [], "requests_at": [],
+           "children_at": []}
+    for r in range(R):
+        out["roots_at"].append(np.array([mp_node_item(nodes[s, 0], s, MP_ROOT_CODE) for s in range(R) if s != r],
+                                        np.uint32).reshape(-1, 16))
+    asks = [[s for s in range(R) if near[r, s] and nodes[s, 0, 4] > 0] for r in range(R)]
+    for s in range(R):
+        out["requests_at"].append(np.array([[r, s, MP_ROOT_CODE, 0] for r in range(R) if s in asks[r]],
+                                           np.uint32).reshape(-1, 4))
+    for r in range(R):
+        out["children_at"].append(np.array([mp_node_item(nodes[s, 1 + o], s, 1 + o) for s in asks[r]
+                                            for o in range(8) if nodes[s, 1 + o, 4] > 0],
+                                           np.uint32).reshape(-1, 16))
     return out

@@ -797,3 +797,89 @@ void or_c4_hg_sample(const float *d, float xi, float xphi, float *out)
     out[0] = d[0]; out[1] = d[1]; out[2] = d[2];
     or_c4_hg(out, xi, xphi);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Multi-phase exchange with three item types (the protocol of Sec. 5.5:    */
+/* particle migration, then an essential-tree exchange in which each rank   */
+/* broadcasts its root multipole node, peers that need finer data send a    */
+/* refinement request back, and the owner answers with the child nodes).    */
+/* Synthetic and integer-only: positions are 32-bit fixed point on the      */
+/* periodic unit cube, split into a 2^lgx x 2^lgy x 2^lgz grid of ranks;    */
+/* a node is the mass, the mass-weighted coordinate sums and the particle   */
+/* count of one rank (the root) or of one octant of its box (a child).      */
+/* ------------------------------------------------------------------------ */
+
+/* rank owning position (x, y, z): the top lg bits of each coordinate */
+int32_t or_mp_owner(uint32_t x, uint32_t y, uint32_t z, const int32_t lg[3])
+{
+    const uint32_t bx = lg[0] ? x >> (32 - lg[0]) : 0u;
+    const uint32_t by = lg[1] ? y >> (32 - lg[1]) : 0u;
+    const uint32_t bz = lg[2] ? z >> (32 - lg[2]) : 0u;
+    const uint32_t gx = (uint32_t)1 << lg[0], gy = (uint32_t)1 << lg[1];
+    return (int32_t)(bx + gx * (by + gy * bz));
+}
+
+/* octant of a position inside its rank's box: the bit after the rank bits */
+static int32_t or_mp_octant(uint32_t x, uint32_t y, uint32_t z, const int32_t lg[3])
+{
+    return (int32_t)(((x >> (31 - lg[0])) & 1u) | (((y >> (31 - lg[1])) & 1u) << 1) |
+                     (((z >> (31 - lg[2])) & 1u) << 2));
+}
+
+/* Particle i (8 words: x, y, z, vx, vy, vz, m, id) moves by its velocity,
+ * wrapping around the periodic cube; owner[i] = rank of the new position. */
+void or_mp_migrate(const uint32_t *p, uint64_t n, const int32_t lg[3], uint32_t *out, int32_t *owner)
+{
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint32_t *a = p + 8 * i;
+        uint32_t *b = out + 8 * i;
+        for (int k = 0; k < 8; ++k) b[k] = a[k];
+        b[0] = a[0] + a[3];
+        b[1] = a[1] + a[4];
+        b[2] = a[2] + a[5];
+        owner[i] = or_mp_owner(b[0], b[1], b[2], lg);
+    }
+}
+
+/* Local trees: nodes[(r * 9 + c) * 5 + {0..4}] = {M, X, Y, Z, count} of rank
+ * r's particles (c = 0, the root) and of those in octant c - 1 of its box. */
+void or_mp_tree(const uint32_t *p, uint64_t n, const int32_t lg[3], uint64_t *nodes)
+{
+    const int32_t R = 1 << (lg[0] + lg[1] + lg[2]);
+    for (int64_t k = 0; k < (int64_t)R * 9 * 5; ++k) nodes[k] = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint32_t *a = p + 8 * i;
+        const int32_t r = or_mp_owner(a[0], a[1], a[2], lg);
+        const int32_t c[2] = {0, 1 + or_mp_octant(a[0], a[1], a[2], lg)};
+        for (int j = 0; j < 2; ++j) {
+            uint64_t *nd = nodes + ((uint64_t)r * 9 + (uint64_t)c[j]) * 5;
+            nd[0] += a[6];
+            nd[1] += (uint64_t)a[6] * a[0];
+            nd[2] += (uint64_t)a[6] * a[1];
+            nd[3] += (uint64_t)a[6] * a[2];
+            nd[4] += 1;
+        }
+    }
+}
+
+/* 1 if rank s is one of rank r's 26 torus neighbours (Chebyshev distance 1
+ * per axis with wrap-around, s != r); peers this close ask for children. */
+int32_t or_mp_near(int32_t r, int32_t s, const int32_t lg[3])
+{
+    if (r == s) return 0;
+    int32_t rc[3], sc[3];
+    int32_t t = r, u = s;
+    for (int k = 0; k < 3; ++k) {
+        const int32_t g = 1 << lg[k];
+        rc[k] = t % g;
+        sc[k] = u % g;
+        t /= g;
+        u /= g;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const int32_t g = 1 << lg[k];
+        const int32_t d = (rc[k] - sc[k] + g) % g;
+        if (d != 0 && d != 1 && d != g - 1) return 0;
+    }
+    return 1;
+}

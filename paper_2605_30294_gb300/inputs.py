@@ -293,3 +293,29 @@ def c4_views(n: int = 1024, sizes=C4_VIEWS):
         out.append((cam, w, h, base))
         base += w * h
     return out
+
+
+# ---------------------------------------------------------------------------
+# Multi-phase exchange: particles on the periodic fixed-point cube
+# ---------------------------------------------------------------------------
+def mp_particles(n: int, seed: int = 5, speed_bits: int = 26) -> np.ndarray:
+    """``n`` 32-byte particles (n x 8 uint32: x, y, z, vx, vy, vz, m, id).
+
+    Positions are uniform 32-bit fixed point; each velocity component is
+    uniform in [-2^speed_bits, 2^speed_bits) (stored as two's complement);
+    masses are 1..255; id = i.  Words from Philox(key {seed, 11}, counters
+    {i, 0, 0, 0} and {i, 1, 0, 0}).
+    """
+    i = np.arange(n, dtype=np.uint32)
+    z = np.zeros_like(i)
+    a = philox4x32_10(i, z, z, z, seed, 11)
+    b = philox4x32_10(i, np.ones_like(i), z, z, seed, 11)
+    out = np.empty((n, 8), np.uint32)
+    out[:, 0], out[:, 1], out[:, 2] = a[0], a[1], a[2]
+    half = np.int64(1) << speed_bits
+    for k in range(3):
+        v = (b[k].astype(np.int64) >> (32 - speed_bits - 1)) - half
+        out[:, 3 + k] = v.astype(np.int32).view(np.uint32)
+    out[:, 6] = 1 + (a[3] >> 24) % 255
+    out[:, 7] = i
+    return out

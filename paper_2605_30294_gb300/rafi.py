@@ -97,6 +97,13 @@ _SIGS = {
     "rf_c0_raygen": [_P, _P, _i32, _i32, _i32, _i32, _P, _P],
     "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
     "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
+    "rf_mp_seed": [_P, _P, _u64, _i32, _i32, _i32, _P],
+    "rf_mp_migrate": [_P, _i32, _i32, _i32, _P],
+    "rf_mp_tree": [_P, _i32, _i32, _i32, _P, _P],
+    "rf_mp_broadcast": [_P, _P, _P],
+    "rf_mp_request": [_P, _P, _i32, _i32, _i32, _P],
+    "rf_mp_respond": [_P, _P, _P, _P],
+    "rf_mp_step": [_P, _P, _P, _i32, _i32, _i32, _P, _P, _PU64],
 }
 _RESTYPE = {"rf_launch_count": _u64, "rf_last_error": ctypes.c_char_p}
 
@@ -393,3 +400,36 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# --- multi-phase exchange (three contexts) ---------------------------------
+def rf_mp_seed(ctx: int, particles, n: int, grid, stream=None) -> None:
+    _check("rf_mp_seed", lib().rf_mp_seed(ctx, ptr(particles), n, *grid, stream_handle(stream)))
+
+
+def rf_mp_migrate(ctx: int, grid, stream=None) -> None:
+    _check("rf_mp_migrate", lib().rf_mp_migrate(ctx, *grid, stream_handle(stream)))
+
+
+def rf_mp_tree(ctx: int, grid, nodes, stream=None) -> None:
+    _check("rf_mp_tree", lib().rf_mp_tree(ctx, *grid, ptr(nodes), stream_handle(stream)))
+
+
+def rf_mp_broadcast(node_ctx: int, nodes, stream=None) -> None:
+    _check("rf_mp_broadcast", lib().rf_mp_broadcast(node_ctx, ptr(nodes), stream_handle(stream)))
+
+
+def rf_mp_request(node_ctx: int, request_ctx: int, grid, stream=None) -> None:
+    _check("rf_mp_request", lib().rf_mp_request(node_ctx, request_ctx, *grid, stream_handle(stream)))
+
+
+def rf_mp_respond(request_ctx: int, node_ctx: int, nodes, stream=None) -> None:
+    _check("rf_mp_respond", lib().rf_mp_respond(request_ctx, node_ctx, ptr(nodes), stream_handle(stream)))
+
+
+def rf_mp_step(particle_ctx: int, node_ctx: int, request_ctx: int, grid, nodes, stream=None):
+    """One protocol step; returns the items delivered by its four exchanges."""
+    got = (ctypes.c_uint64 * 4)()
+    _check("rf_mp_step", lib().rf_mp_step(particle_ctx, node_ctx, request_ctx, *grid, ptr(nodes),
+                                          stream_handle(stream), got))
+    return tuple(int(v) for v in got)
