@@ -132,6 +132,31 @@ rf_status rf_get_device_queues(rf_ctx *ctx, rf_device_queues *out);
  *   rf_num_active / rf_stats. */
 rf_status rf_exchange(rf_ctx *ctx, void *stream, uint64_t *numActiveOut);
 
+/* Launch shape of rf_exchange: items per scatter tile (256 x K; the tile
+ * is staged in shared memory), and the grid sizes of the scatter and count
+ * kernels.  In rf_set_exchange_config a zero field means the default (the
+ * largest tile of at most 64 KiB, and as many CTAs as fit on the device). */
+typedef struct rf_exchange_config {
+    uint32_t tileItems;
+    int32_t scatterBlocks;
+    int32_t countBlocks;
+} rf_exchange_config;
+
+rf_status rf_get_exchange_config(rf_ctx *ctx, rf_exchange_config *out);
+/* RF_ERR_ARG if no scatter variant has that tile for the context's item
+ * size (tiles of 256 x K items, K from {16, 8, 4} for 16-byte items, {8, 4,
+ * 2} for 32, {4, 2, 1} for 48 and 64, {2, 1} for 128) or a grid is negative. */
+rf_status rf_set_exchange_config(rf_ctx *ctx, const rf_exchange_config *cfg);
+
+/* Autotuner: times count + scan + scatter of the current out-queue (left
+ * untouched; fill it with a representative round first) for every scatter
+ * tile of the item size and scatter grids of 1x, 2x and the resident number
+ * of CTAs per SM, trials timed runs each after one warm-up (CUDA events on
+ * stream), and keeps the fastest.  *best, *bestMs (nullable): the chosen
+ * configuration and its time.  The incoming queue is left empty.
+ * RF_ERR_ARG if the out-queue is empty or trials is outside 1..1000. */
+rf_status rf_tune_exchange(rf_ctx *ctx, void *stream, uint32_t trials, rf_exchange_config *best, float *bestMs);
+
 /* Total of the most recent exchange (numIncoming over all ranks, Sec. 3.3);
  * waits for that exchange's stream. */
 rf_status rf_num_active(rf_ctx *ctx, uint64_t *out);

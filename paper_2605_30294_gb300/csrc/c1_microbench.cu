@@ -21,8 +21,6 @@
 
 namespace rfi {
 
-rf_status configure_exchange(rf_ctx *ctx);
-
 namespace {
 
 constexpr int kBlock = 256;
@@ -151,6 +149,7 @@ struct C1Work {
     static constexpr int V = 4;
     static constexpr bool kAppendRetired = true;
     static constexpr bool kDynamicWork = false;
+    static constexpr bool kGridStride = false;
     static constexpr bool kFuseStep = true;
     static constexpr int kMinBlocksPerSM = 3;
     static constexpr int kItemsPerThread = 2;

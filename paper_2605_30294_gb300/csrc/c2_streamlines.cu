@@ -161,6 +161,7 @@ struct C2Work {
     static constexpr int V = 2;
     static constexpr bool kAppendRetired = false;
     static constexpr bool kDynamicWork = true;
+    static constexpr bool kGridStride = false;
     static constexpr bool kFuseStep = false;
     static constexpr unsigned kStepReadMask = 0x3u;  // every vector
     static constexpr unsigned kStepWriteMask = 0x3u;

@@ -183,10 +183,11 @@ struct C4Work {
     static constexpr int V = 4;
     static constexpr bool kAppendRetired = false;
     static constexpr bool kDynamicWork = true;
+    static constexpr bool kGridStride = false;
     static constexpr bool kFuseStep = false;
     static constexpr unsigned kStepReadMask = 0xfu;  // every vector
     static constexpr unsigned kStepWriteMask = 0xfu;
-    static constexpr int kMinBlocksPerSM = 3;
+    static constexpr int kMinBlocksPerSM = 4;
     static constexpr int kItemsPerThread = 1;
     TParams P;
     __host__ __device__ uint32_t smemBytes() const { return 0u; }

@@ -40,7 +40,6 @@ rf_status cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? RF_ERR_OOM : RF_ERR_CUDA;
 }
 
-rf_status configure_exchange(rf_ctx *ctx);  // exchange.cu
 
 void time_begin(rf_ctx *ctx, int slot, cudaStream_t s)
 {
@@ -126,6 +125,7 @@ void free_queues(rf_ctx *ctx)
     ctx->in = ctx->out = nullptr;
     ctx->dest = nullptr;
     ctx->tileHist = nullptr;
+    ctx->tileHistTiles = 0;
     ctx->staging = nullptr;
 }
 
@@ -139,7 +139,7 @@ rf_status alloc_queues(rf_ctx *ctx, uint64_t capacity)
     RF_CUDA(cudaMalloc(&ctx->out, qbytes));
     // padded to whole 16-byte units (+16 bytes) so a tile of destinations can be bulk-copied
     RF_CUDA(cudaMalloc(&ctx->dest, ((size_t)capacity + 3) / 4 * 16 + 16));
-    RF_CUDA(cudaMalloc(&ctx->tileHist, (size_t)ctx->numRanks * ctx->maxTiles * sizeof(uint32_t)));
+    if (rf_status hs = ensure_tile_hist(ctx)) return hs;
     RF_CUDA(cudaMemset(ctx->inOffset, 0, (size_t)(ctx->numRanks + 1) * sizeof(uint32_t)));
     RF_CUDA(cudaMemset(ctx->count, 0, (size_t)ctx->numRanks * sizeof(uint32_t)));
     RF_CUDA(cudaMemset(ctx->dev, 0, sizeof(DevState)));

@@ -389,21 +389,57 @@ struct ScatterChoice {
     uint32_t k;
 };
 
-ScatterChoice pick_scatter(uint32_t itemBytes)
+// The scatter variants built for an item size (K = items per thread, tile =
+// 256 K items), largest tile first; the first is the default.  A tile stays
+// within 64 KiB of shared memory.
+constexpr int kMaxVariants = 3;
+
+int scatter_variants(uint32_t itemBytes, ScatterChoice out[kMaxVariants])
 {
-    const uint32_t v = itemBytes / 16u;
-    switch (v) {
-    case 1: return {scatter_kernel<1, 16>, 16};
-    case 2: return {scatter_kernel<2, 8>, 8};
-    case 3: return {scatter_kernel<3, 4>, 4};
-    case 4: return {scatter_kernel<4, 4>, 4};
-    case 8: return {scatter_kernel<8, 2>, 2};
-    default: break;
+    switch (itemBytes / 16u) {
+    case 1:
+        out[0] = {scatter_kernel<1, 16>, 16};
+        out[1] = {scatter_kernel<1, 8>, 8};
+        out[2] = {scatter_kernel<1, 4>, 4};
+        return 3;
+    case 2:
+        out[0] = {scatter_kernel<2, 8>, 8};
+        out[1] = {scatter_kernel<2, 4>, 4};
+        out[2] = {scatter_kernel<2, 2>, 2};
+        return 3;
+    case 3:
+        out[0] = {scatter_kernel<3, 4>, 4};
+        out[1] = {scatter_kernel<3, 2>, 2};
+        out[2] = {scatter_kernel<3, 1>, 1};
+        return 3;
+    case 4:
+        out[0] = {scatter_kernel<4, 4>, 4};
+        out[1] = {scatter_kernel<4, 2>, 2};
+        out[2] = {scatter_kernel<4, 1>, 1};
+        return 3;
+    case 8:
+        out[0] = {scatter_kernel<8, 2>, 2};
+        out[1] = {scatter_kernel<8, 1>, 1};
+        return 2;
+    default:
+        break;
     }
-    // generic: the largest K in {1, 2, 4} with a tile of at most 64 KiB
-    if (256u * 4u * itemBytes <= 65536u) return {scatter_kernel<0, 4>, 4};
-    if (256u * 2u * itemBytes <= 65536u) return {scatter_kernel<0, 2>, 2};
-    return {scatter_kernel<0, 1>, 1};
+    int m = 0;
+    if (256u * 4u * itemBytes <= 65536u) out[m++] = {scatter_kernel<0, 4>, 4};
+    if (256u * 2u * itemBytes <= 65536u) out[m++] = {scatter_kernel<0, 2>, 2};
+    out[m++] = {scatter_kernel<0, 1>, 1};
+    return m;
+}
+
+// The variant with K items per thread (k = 0: the default); {nullptr, 0} if none.
+ScatterChoice pick_scatter(uint32_t itemBytes, uint32_t k = 0)
+{
+    ScatterChoice v[kMaxVariants];
+    const int m = scatter_variants(itemBytes, v);
+    if (k == 0) return v[0];
+    for (int i = 0; i < m; ++i)
+        if (v[i].k == k) return v[i];
+    return {nullptr, 0u};
 }
 
 ExArgs make_args(rf_ctx *ctx)
@@ -426,10 +462,16 @@ ExArgs make_args(rf_ctx *ctx)
 
 }  // namespace
 
-// Chooses the tile size and grid shapes for a context (called by rf_create / rf_resize).
+// Chooses the tile size and grid shapes for a context (called by rf_create /
+// rf_resize and when a configuration is set): the requested ones where the
+// context holds a request, else the defaults.
 rf_status configure_exchange(rf_ctx *ctx)
 {
-    ScatterChoice c = pick_scatter(ctx->itemBytes);
+    ScatterChoice c = pick_scatter(ctx->itemBytes, ctx->reqScatterK);
+    if (!c.fn) {
+        set_error("no scatter variant with %u items per thread for %u-byte items", ctx->reqScatterK, ctx->itemBytes);
+        return RF_ERR_ARG;
+    }
     ctx->tileItems = 256u * c.k;
     const uint64_t tiles = (ctx->capacity + ctx->tileItems - 1) / ctx->tileItems;
     ctx->maxTiles = (uint32_t)((tiles + 3) / 4 * 4);
@@ -449,18 +491,33 @@ rf_status configure_exchange(rf_ctx *ctx)
         set_error("scatter kernel does not fit on an SM (%zu bytes of shared memory)", ctx->scatterSmem);
         return RF_ERR_ARG;
     }
-    ctx->scatterBlocks = ctx->numSMs * perSM;
+    ctx->scatterBlocks = ctx->reqScatterBlocks > 0 ? ctx->reqScatterBlocks : ctx->numSMs * perSM;
     int cperSM = 0;
     RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cperSM, count_kernel, kBlock,
                                                           (size_t)ctx->numRanks * 4u));
-    ctx->countBlocks = ctx->numSMs * (cperSM < 1 ? 1 : cperSM);
+    ctx->countBlocks = ctx->reqCountBlocks > 0 ? ctx->reqCountBlocks : ctx->numSMs * (cperSM < 1 ? 1 : cperSM);
     return RF_OK;
 }
 
-rf_status launch_exchange(rf_ctx *ctx, cudaStream_t s)
+// Per-tile histograms for the configured tile: grown (never shrunk) when a
+// smaller tile needs more of them.  Waits for the device before freeing.
+rf_status ensure_tile_hist(rf_ctx *ctx)
+{
+    if (ctx->tileHist && ctx->tileHistTiles >= ctx->maxTiles) return RF_OK;
+    RF_CUDA(cudaDeviceSynchronize());
+    cudaFree(ctx->tileHist);
+    ctx->tileHist = nullptr;
+    ctx->tileHistTiles = 0;
+    RF_CUDA(cudaMalloc(&ctx->tileHist, (size_t)ctx->numRanks * ctx->maxTiles * sizeof(uint32_t)));
+    ctx->tileHistTiles = ctx->maxTiles;
+    return RF_OK;
+}
+
+// count, scan and scatter of the out-queue into the incoming queue (no wrap-up)
+rf_status launch_partition(rf_ctx *ctx, cudaStream_t s)
 {
     const ExArgs a = make_args(ctx);
-    const ScatterChoice c = pick_scatter(ctx->itemBytes);
+    const ScatterChoice c = pick_scatter(ctx->itemBytes, ctx->tileItems / 256u);
     const int maxTiles = (int)ctx->maxTiles;
     const int cb = ctx->countBlocks < maxTiles ? ctx->countBlocks : maxTiles;
     const int sb = ctx->scatterBlocks < maxTiles ? ctx->scatterBlocks : maxTiles;
@@ -479,7 +536,13 @@ rf_status launch_exchange(rf_ctx *ctx, cudaStream_t s)
     c.fn<<<sb, kBlock, ctx->scatterSmem, s>>>(a);
     RF_LAUNCHED("scatter_kernel");
     time_end(ctx, kTimeScatter, s);
+    return RF_OK;
+}
 
+rf_status launch_exchange(rf_ctx *ctx, cudaStream_t s)
+{
+    if (rf_status st = launch_partition(ctx, s)) return st;
+    const ExArgs a = make_args(ctx);
     wrapup_kernel<<<1, kBlock, 0, s>>>(a);
     RF_LAUNCHED("wrapup_kernel");
     return RF_OK;
@@ -504,6 +567,154 @@ extern "C" rf_status rf_exchange(rf_ctx *ctx, void *stream, uint64_t *numActiveO
     st = rfi::sync_state(ctx);
     *numActiveOut = ctx->host->numActive;
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Exchange configuration and its autotuner: tile size (items per scatter
+// tile) and the grid sizes of the count and scatter kernels.
+// ---------------------------------------------------------------------------
+namespace {
+
+rf_status apply_config(rf_ctx *ctx, uint32_t k, int scatterBlocks, int countBlocks)
+{
+    const uint32_t oldK = ctx->reqScatterK;
+    const int oldS = ctx->reqScatterBlocks, oldC = ctx->reqCountBlocks;
+    ctx->reqScatterK = k;
+    ctx->reqScatterBlocks = scatterBlocks;
+    ctx->reqCountBlocks = countBlocks;
+    rf_status st = rfi::configure_exchange(ctx);
+    if (st == RF_OK) st = rfi::ensure_tile_hist(ctx);
+    if (st != RF_OK) {
+        ctx->reqScatterK = oldK;
+        ctx->reqScatterBlocks = oldS;
+        ctx->reqCountBlocks = oldC;
+        (void)rfi::configure_exchange(ctx);
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" rf_status rf_get_exchange_config(rf_ctx *ctx, rf_exchange_config *out)
+{
+    if (!ctx || !out) {
+        rfi::set_error("rf_get_exchange_config: NULL argument");
+        return RF_ERR_ARG;
+    }
+    out->tileItems = ctx->tileItems;
+    out->scatterBlocks = ctx->scatterBlocks;
+    out->countBlocks = ctx->countBlocks;
+    return RF_OK;
+}
+
+extern "C" rf_status rf_set_exchange_config(rf_ctx *ctx, const rf_exchange_config *cfg)
+{
+    using namespace rfi;
+    if (!ctx || !cfg) {
+        set_error("rf_set_exchange_config: NULL argument");
+        return RF_ERR_ARG;
+    }
+    if (cfg->tileItems % 256u || cfg->scatterBlocks < 0 || cfg->countBlocks < 0 || cfg->scatterBlocks > (1 << 20) ||
+        cfg->countBlocks > (1 << 20) ||
+        (cfg->tileItems && !pick_scatter(ctx->itemBytes, cfg->tileItems / 256u).fn)) {
+        set_error("rf_set_exchange_config: tile of %u items, grids %d / %d not available for %u-byte items",
+                  cfg->tileItems, cfg->scatterBlocks, cfg->countBlocks, ctx->itemBytes);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    return apply_config(ctx, cfg->tileItems / 256u, cfg->scatterBlocks, cfg->countBlocks);
+}
+
+extern "C" rf_status rf_tune_exchange(rf_ctx *ctx, void *stream, uint32_t trials, rf_exchange_config *best,
+                                      float *bestMs)
+{
+    using namespace rfi;
+    if (!ctx || trials < 1 || trials > 1000) {
+        set_error("rf_tune_exchange: NULL context or trials outside 1..1000");
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RF_CUDA(cudaStreamSynchronize(s));
+    if (ctx->pending) {
+        if (rf_status st = sync_state(ctx)) (void)st;
+    }
+    DevState saved;
+    RF_CUDA(cudaMemcpy(&saved, ctx->dev, sizeof saved, cudaMemcpyDeviceToHost));
+    if (saved.outCount == 0) {
+        set_error("rf_tune_exchange: the out-queue is empty; emit a representative round first");
+        return RF_ERR_ARG;
+    }
+    ScatterChoice v[kMaxVariants];
+    const int nv = scatter_variants(ctx->itemBytes, v);
+    // room for the smallest tile's histograms up front
+    const uint32_t oldK = ctx->reqScatterK;
+    const int oldS = ctx->reqScatterBlocks, oldC = ctx->reqCountBlocks;
+    if (rf_status st = apply_config(ctx, v[nv - 1].k, 0, 0)) return st;
+
+    cudaEvent_t e0, e1;
+    RF_CUDA(cudaEventCreate(&e0));
+    RF_CUDA(cudaEventCreate(&e1));
+    float bestT = -1.0f;
+    uint32_t bestK = v[0].k;
+    int bestGrid = 0;
+    rf_status st = RF_OK;
+    for (int i = 0; i < nv && st == RF_OK; ++i) {
+        const size_t smem = scatter_layout(256u * v[i].k, ctx->itemBytes, ctx->numRanks).total;
+        int perSM = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, v[i].fn, kBlock, smem) != cudaSuccess || perSM < 1)
+            continue;
+        const int grids[3] = {ctx->numSMs, 2 * ctx->numSMs, perSM * ctx->numSMs};
+        for (int j = 0; j < 3 && st == RF_OK; ++j) {
+            if (j == 1 && grids[1] >= grids[2]) continue;
+            if (j == 2 && grids[2] == grids[0]) continue;
+            st = apply_config(ctx, v[i].k, grids[j], 0);
+            float tmin = -1.0f;
+            for (uint32_t t = 0; t <= trials && st == RF_OK; ++t) {
+                if (cudaMemsetAsync(ctx->count, 0, (size_t)ctx->numRanks * sizeof(uint32_t), s) != cudaSuccess ||
+                    cudaEventRecord(e0, s) != cudaSuccess) {
+                    st = cuda_fail(cudaGetLastError(), "rf_tune_exchange");
+                    break;
+                }
+                st = launch_partition(ctx, s);
+                if (st != RF_OK) break;
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    st = cuda_fail(cudaGetLastError(), "rf_tune_exchange");
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (t > 0 && (tmin < 0.0f || ms < tmin)) tmin = ms;  // the first run is a warm-up
+            }
+            if (st == RF_OK && tmin >= 0.0f && (bestT < 0.0f || tmin < bestT)) {
+                bestT = tmin;
+                bestK = v[i].k;
+                bestGrid = grids[j];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the out-queue is untouched; the incoming queue is left empty
+    saved.numActive = 0ull;
+    cudaMemset(ctx->count, 0, (size_t)ctx->numRanks * sizeof(uint32_t));
+    cudaMemset(ctx->inOffset, 0, (size_t)(ctx->numRanks + 1) * sizeof(uint32_t));
+    cudaMemcpy(ctx->dev, &saved, sizeof saved, cudaMemcpyHostToDevice);
+    *ctx->host = saved;
+    ctx->pending = false;
+    if (st != RF_OK || bestT < 0.0f) {
+        (void)apply_config(ctx, oldK, oldS, oldC);
+        if (st == RF_OK) {
+            set_error("rf_tune_exchange: no scatter variant fits the device");
+            st = RF_ERR_ARG;
+        }
+        return st;
+    }
+    if (rf_status as = apply_config(ctx, bestK, bestGrid, 0)) return as;
+    RF_CUDA(cudaDeviceSynchronize());
+    if (best) rf_get_exchange_config(ctx, best);
+    if (bestMs) *bestMs = bestT;
+    return RF_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -563,11 +774,12 @@ rf_status static_setup(int dev, unsigned char **base)
         RF_CUDA(cudaGetSymbolAddress(&p, g_partition_scratch));
         int optin = 0;
         RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        const ExKernel variants[] = {scatter_kernel<1, 16>, scatter_kernel<2, 8>, scatter_kernel<3, 4>,
-                                     scatter_kernel<4, 4>,  scatter_kernel<8, 2>, scatter_kernel<0, 4>,
-                                     scatter_kernel<0, 2>,  scatter_kernel<0, 1>};
-        for (ExKernel f : variants)
-            RF_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        for (uint32_t bytes : {16u, 32u, 48u, 64u, 128u, 80u, 160u, 512u}) {
+            ScatterChoice v[kMaxVariants];
+            const int m = scatter_variants(bytes, v);
+            for (int i = 0; i < m; ++i)
+                RF_CUDA(cudaFuncSetAttribute(v[i].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+        }
         g_static_base[dev] = p;
     }
     *base = static_cast<unsigned char *>(g_static_base[dev]);

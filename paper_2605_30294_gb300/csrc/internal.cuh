@@ -54,6 +54,9 @@ struct rf_ctx {
     uint32_t *inOffset = nullptr;  // numRanks + 1
     uint32_t *count = nullptr;     // numRanks
     uint32_t *tileHist = nullptr;  // numRanks x maxTiles, digit-major
+    uint32_t tileHistTiles = 0;    // tiles tileHist has room for
+    uint32_t reqScatterK = 0;      // requested exchange configuration (0: default)
+    int reqScatterBlocks = 0, reqCountBlocks = 0;
     rfi::DevState *dev = nullptr;
     rfi::DevState *host = nullptr;  // pinned mirror of *dev
     void *staging = nullptr;        // lazily allocated: capacity items (host-memory runs)
@@ -116,6 +119,11 @@ rf_status sync_state(rf_ctx *ctx);
 
 // Launch count / scan / scatter / wrap-up for the context's out-queue.
 rf_status launch_exchange(rf_ctx *ctx, cudaStream_t s);
+
+// Tile size and grid shapes of the exchange from the context's request (or
+// the defaults), and room for the per-tile histograms of that tile.
+rf_status configure_exchange(rf_ctx *ctx);
+rf_status ensure_tile_hist(rf_ctx *ctx);
 
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);

@@ -352,8 +352,10 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
 //   static constexpr int V;               16-byte vectors per item
 //   static constexpr bool kAppendRetired; retired items go, stably, to the
 //                                         retirement sink (else: retire())
-//   static constexpr bool kDynamicWork;   long, uneven per-item work: the work
-//                                         phase hands out chunks dynamically
+//   static constexpr bool kDynamicWork;   long per-item work: a work phase of its
+//                                         own over the whole queue, before the scatter
+//   static constexpr bool kGridStride;    (kDynamicWork) items by grid stride rather
+//                                         than dynamically handed-out chunks
 //   static constexpr int kMinBlocksPerSM; resident CTAs per SM to compile for
 //   static constexpr int kItemsPerThread; tile = 256 x this many items
 //   static constexpr bool kFuseStep;      short, even per-item work: the scatter
@@ -673,11 +675,20 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         const bool prefetched = !fresh && !dynamic && nt > 0;
         if (prefetched && tid == 0) issue3(0, lo);
         if (dynamic) {
+            // W::kGridStride: thread t of the grid takes items t, t + 256 G, ...
+            // (no atomics; for steps of similar cost).  Otherwise each warp
+            // takes 32-item chunks from the round's counter.
             unsigned int *ticket = &a.sync->work[it & 1u];
+            uint32_t strided = (uint32_t)c * kRoundsBlock + (uint32_t)warp * 32u;
             for (;;) {
                 uint32_t base = 0;
-                if (lane == 0) base = atomicAdd(ticket, 32u);
-                base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                if (W::kGridStride) {
+                    base = strided;
+                    strided += (uint32_t)G * kRoundsBlock;
+                } else {
+                    if (lane == 0) base = atomicAdd(ticket, 32u);
+                    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+                }
                 if (base >= n) break;
                 const uint32_t i = base + lane;
                 if (i < n) {
@@ -986,8 +997,20 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         return RF_ERR_ARG;
     }
     RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dynMax));
+    // Shared memory carve-out: just what W::kMinBlocksPerSM CTAs need, so the
+    // rest of the SM's on-chip memory stays L1 for the workload's gathers.
+    int smPerSM = 0;
+    RF_CUDA(cudaDeviceGetAttribute(&smPerSM, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    const long long need = (long long)W::kMinBlocksPerSM * ((long long)L.total + fa.sharedSizeBytes + 1024);
+    const int carve = smPerSM > 0 ? (int)((100 * need + smPerSM - 1) / smPerSM) : 100;
+    RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve < 100 ? carve : 100));
     int perSM = 0;
     RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
+    if (perSM < W::kMinBlocksPerSM) {
+        // the hint did not leave room for the intended occupancy: let the driver choose
+        RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, -1));
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
+    }
     if (perSM < 1) {
         set_error("persistent rounds: the kernel does not fit on an SM");
         return RF_ERR_ARG;

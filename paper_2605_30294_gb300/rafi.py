@@ -97,6 +97,9 @@ _SIGS = {
     "rf_c0_raygen": [_P, _P, _i32, _i32, _i32, _i32, _P, _P],
     "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
     "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
+    "rf_get_exchange_config": [_P, _P],
+    "rf_set_exchange_config": [_P, _P],
+    "rf_tune_exchange": [_P, _P, _u32, _P, _P],
     "rf_mp_seed": [_P, _P, _u64, _i32, _i32, _i32, _P],
     "rf_mp_migrate": [_P, _i32, _i32, _i32, _P],
     "rf_mp_tree": [_P, _i32, _i32, _i32, _P, _P],
@@ -433,3 +436,35 @@ def rf_mp_step(particle_ctx: int, node_ctx: int, request_ctx: int, grid, nodes, 
     _check("rf_mp_step", lib().rf_mp_step(particle_ctx, node_ctx, request_ctx, *grid, ptr(nodes),
                                           stream_handle(stream), got))
     return tuple(int(v) for v in got)
+
+
+# --- exchange configuration and autotuner ----------------------------------
+class ExchangeConfig(ctypes.Structure):
+    _fields_ = [("tileItems", ctypes.c_uint32), ("scatterBlocks", ctypes.c_int32), ("countBlocks", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (int(self.tileItems), int(self.scatterBlocks), int(self.countBlocks))
+
+
+def rf_get_exchange_config(ctx: int):
+    """(tileItems, scatterBlocks, countBlocks) of the context's exchange."""
+    cfg = ExchangeConfig()
+    _check("rf_get_exchange_config", lib().rf_get_exchange_config(ctx, ctypes.byref(cfg)))
+    return cfg.as_tuple()
+
+
+def rf_set_exchange_config(ctx: int, tile_items: int = 0, scatter_blocks: int = 0, count_blocks: int = 0,
+                           allow=()) -> int:
+    cfg = ExchangeConfig(tile_items, scatter_blocks, count_blocks)
+    st = lib().rf_set_exchange_config(ctx, ctypes.byref(cfg))
+    _check("rf_set_exchange_config", st, allow)
+    return st
+
+
+def rf_tune_exchange(ctx: int, stream=None, trials: int = 3):
+    """Tune on the current out-queue; returns ((tileItems, scatterBlocks, countBlocks), ms)."""
+    cfg = ExchangeConfig()
+    ms = ctypes.c_float()
+    _check("rf_tune_exchange", lib().rf_tune_exchange(ctx, stream_handle(stream), trials, ctypes.byref(cfg),
+                                                      ctypes.byref(ms)))
+    return cfg.as_tuple(), float(ms.value)

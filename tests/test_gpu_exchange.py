@@ -183,3 +183,72 @@ def test_timing_counters():
         assert t.scatterLaunches == 1 and t.scatterItems == n and t.scatterMs > 0
         assert t.scatterLaunchesLarge == 1 and t.scatterItemsLarge == n
         assert rafi.rf_launch_count() - launches == 5  # add_count + count + scan + scatter + wrap-up
+
+
+# ---------------------------------------------------------------------------
+# exchange configuration and autotuner
+# ---------------------------------------------------------------------------
+TILES = {16: (4096, 2048, 1024), 32: (2048, 1024, 512), 48: (1024, 512, 256), 64: (1024, 512, 256),
+         128: (512, 256)}
+
+
+def _exchange_with(ctx, R, ib, items, dest, s):
+    n = len(dest)
+    rafi.rf_push(ctx.handle, to_dev(items), to_dev(dest), n, False, s)
+    st, na = rafi.rf_exchange(ctx.handle, s)
+    out = zeros_u8(n, ib)
+    off = torch.zeros(R + 1, dtype=torch.int32, device=torch.device("cuda:0"))
+    rafi.rf_snapshot(ctx.handle, out, off, s)
+    torch.cuda.synchronize()
+    return na, out[:na].cpu().numpy(), off.cpu().numpy().astype(np.uint64)
+
+
+@pytest.mark.parametrize("ib", sorted(TILES))
+def test_every_exchange_config_gives_the_stable_partition(ib):
+    R, n = 64, 100003
+    rng = np.random.default_rng(ib)
+    items = _items(n, ib, ib + 1)
+    dest = rng.integers(0, R, size=n).astype(np.int32)
+    want, woff, _, _ = oracle.partition(items, dest, R)
+    s = stream()
+    with rafi.Context(R, ib, n) as ctx:
+        default = rafi.rf_get_exchange_config(ctx.handle)
+        assert default[0] == TILES[ib][0]
+        for tile in TILES[ib]:
+            for grid in (0, 7, 152):
+                rafi.rf_set_exchange_config(ctx.handle, tile, grid, grid)
+                assert rafi.rf_get_exchange_config(ctx.handle)[0] == tile
+                na, got, off = _exchange_with(ctx, R, ib, items, dest, s)
+                assert na == n
+                np.testing.assert_array_equal(off, woff)
+                np.testing.assert_array_equal(got, want)
+        # a tile no variant has is refused and leaves the configuration as it was
+        before = rafi.rf_get_exchange_config(ctx.handle)
+        st = rafi.rf_set_exchange_config(ctx.handle, 256 * 3, 0, 0, allow=(rafi.RF_ERR_ARG,))
+        assert st == rafi.RF_ERR_ARG and rafi.rf_get_exchange_config(ctx.handle) == before
+
+
+def test_tuner_keeps_the_out_queue_and_picks_a_variant():
+    R, ib, n = 64, 64, 1 << 20
+    rng = np.random.default_rng(11)
+    items = _items(n, ib, 12)
+    dest = rng.integers(0, R, size=n).astype(np.int32)
+    want, woff, _, _ = oracle.partition(items, dest, R)
+    s = stream()
+    with rafi.Context(R, ib, n) as ctx:
+        rafi.rf_push(ctx.handle, to_dev(items), to_dev(dest), n, False, s)
+        cfg, ms = rafi.rf_tune_exchange(ctx.handle, s, trials=2)
+        assert cfg[0] in TILES[ib] and cfg[1] > 0 and ms > 0
+        assert rafi.rf_get_exchange_config(ctx.handle) == cfg
+        assert rafi.rf_num_active(ctx.handle) == 0  # the incoming queue is left empty
+        st, na = rafi.rf_exchange(ctx.handle, s)
+        out = zeros_u8(n, ib)
+        off = torch.zeros(R + 1, dtype=torch.int32, device=torch.device("cuda:0"))
+        rafi.rf_snapshot(ctx.handle, out, off, s)
+        torch.cuda.synchronize()
+        assert na == n
+        np.testing.assert_array_equal(off.cpu().numpy().astype(np.uint64), woff)
+        np.testing.assert_array_equal(out.cpu().numpy(), want)
+        # an empty out-queue has nothing to tune on
+        with pytest.raises(rafi.RafiError):
+            rafi.rf_tune_exchange(ctx.handle, s)
