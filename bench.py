@@ -155,6 +155,19 @@ def oracle_baseline(steps=1):
     return fwd / dt, fwd, dt
 
 
+def reduce_over_ranks(dist, device, sec: float, units: int, e2e_s: float, e2e_units: int):
+    """Replicas: the job's time is the slowest rank's, its work every rank's.
+    Returns (max seconds, summed units, max end-to-end seconds, summed end-to-end units)."""
+    import torch
+
+    tt = torch.tensor([sec, float(units), e2e_s, float(e2e_units)], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = tt.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), int(sm[1]), float(mx[2]), int(sm[3])
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -556,13 +569,7 @@ def run_ours(args):
     sec = ms / 1e3
     total_fwd = fwd
     if pg:
-        tt = torch.tensor([sec, float(fwd), e2e_s, float(e2e_fwd)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
-        sm = tt.clone()
-        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
-        sec, e2e_s = float(mx[0]), float(mx[2])
-        total_fwd, e2e_fwd = int(sm[1]), int(sm[3])
+        sec, total_fwd, e2e_s, e2e_fwd = reduce_over_ranks(pg, dev, sec, fwd, e2e_s, e2e_fwd)
     if rank != 0:
         if pg:
             pg.destroy_process_group()

@@ -287,7 +287,10 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
  * stepOnArrival == 0: the seed exchange runs first; each round's work step
  * reads and writes back every item in its queue slot before the scatter.
  * Queue order is deterministic either way: round k's incoming queue is the
- * one of rf_c1_run with deterministic != 0.  Rounds of at most 2048 items
+ * one of rf_c1_run with deterministic != 0.  With hostMemory != 0 and a
+ * page-locked (device-mapped) retired buffer the kernel writes the retired
+ * items straight into it during the run; other host buffers are filled from
+ * a device staging buffer after it.  Rounds of at most 2048 items
  * run on one CTA (the others return); with steps on arrival, rounds of at
  * most 512 items keep the whole queue in that CTA's shared memory.  roundLog (device, 7 x roundLogCap
  * words, nullable) receives per round, as seen by CTA 0, the %globaltimer ns

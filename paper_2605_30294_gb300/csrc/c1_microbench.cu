@@ -417,15 +417,36 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
         if (rf_status st = ensure_zipf(ctx, zipfS)) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void *devRetired = retired;
+    bool direct = false;
     if (hostMemory) {
-        if (rf_status st = ensure_staging(ctx)) return st;
-        devRetired = ctx->staging;
+        // A host buffer the device can address (page-locked memory is mapped
+        // into the device's address space under unified addressing) receives
+        // the retired items straight from the kernel over the host link,
+        // overlapped with the rounds; any other host buffer gets them through
+        // a device staging buffer and one copy after the run.
+        cudaPointerAttributes pa;
+        if (n && cudaPointerGetAttributes(&pa, retired) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            devRetired = pa.devicePointer;
+            direct = true;
+        } else {
+            (void)cudaGetLastError();
+            if (rf_status st = ensure_staging(ctx)) return st;
+            devRetired = ctx->staging;
+        }
     }
     RF_CUDA(cudaMemsetAsync(ctx->stagingCount, 0, sizeof(unsigned long long), s));
     rf_device_queues q;
     rf_get_device_queues(ctx, &q);
+    // With steps on arrival the kernel's first scatter reads 16-byte aligned
+    // device items where the caller keeps them; only their first ranks are
+    // written.  Otherwise the items are copied into the out-queue first.
+    const bool inPlace = !hostMemory && stepOnArrival && ((uintptr_t)items & 15u) == 0;
     if (hostMemory) {
         if (n) RF_CUDA(cudaMemcpyAsync(q.out, items, (size_t)n * 64u, cudaMemcpyHostToDevice, s));
+        seed_dest_kernel<<<grid_for(ctx, n, 8), kBlock, 0, s>>>((uint32_t)n, q);
+        RF_LAUNCHED("seed_dest_kernel");
+    } else if (inPlace) {
         seed_dest_kernel<<<grid_for(ctx, n, 8), kBlock, 0, s>>>((uint32_t)n, q);
         RF_LAUNCHED("seed_dest_kernel");
     } else {
@@ -447,11 +468,12 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
     w.R = ctx->numRanks;
     unsigned long long res[4];
     rf_status st = launch_rounds(ctx, w, maxRounds, s, roundLog, roundLogCap, static_cast<uint4 *>(devRetired), n,
-                                 ctx->stagingCount, res, stepOnArrival != 0, stepOnArrival != 0);
+                                 ctx->stagingCount, res, stepOnArrival != 0, stepOnArrival != 0,
+                                 inPlace ? items : nullptr);
     if (st != RF_OK) return st;
     unsigned long long cnt = 0;
     RF_CUDA(cudaMemcpy(&cnt, ctx->stagingCount, sizeof cnt, cudaMemcpyDeviceToHost));
-    if (hostMemory && cnt)
+    if (hostMemory && !direct && cnt)
         RF_CUDA(cudaMemcpyAsync(retired, ctx->staging, (size_t)(cnt < n ? cnt : n) * 64u, cudaMemcpyDeviceToHost, s));
     RF_CUDA(cudaStreamSynchronize(s));
     *retiredCountOut = cnt;

@@ -62,6 +62,7 @@ struct RoundsArgs {
     unsigned long long retiredCap;
     unsigned long long *retiredCountOut;
     unsigned long long *seedCount;  // nullable: start from a seeded out-queue of this many items (kFuseStep)
+    const uint4 *seedItems;         // nullable: the seeded items, read in place instead of from the out-queue
     uint32_t maxRounds;
     uint32_t roundLogCap;
     uint32_t fuseStep;  // apply steps on arrival (policies with kFuseStep)
@@ -496,8 +497,9 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     // flag for digit R).  With ownBases the tile is a whole round on its own:
     // dBase[d] = dStart[d] for ranks and the retired count so far for R.
     // Returns the number of valid items.  All threads; ends with a barrier.
+    // carryPrev: first add the previous tile's counts (still in dCnt) to dBase.
     auto rank_tile = [&](uint4 *sItems, int32_t *dts, uint32_t cnt, bool doFuse, uint32_t qs,
-                         bool ownBases) -> uint32_t {
+                         bool ownBases, bool carryPrev) -> uint32_t {
         int myD[kK];
         uint32_t myR[kK];
 #pragma unroll
@@ -542,6 +544,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 wc[ww * D + e] = sum;
                 sum += v;
             }
+            if (carryPrev) dBase[e] += dCnt[e];
             dCnt[e] = sum;
             dStart[e] = sum;
         }
@@ -591,7 +594,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 __syncwarp();
                 uint4 *iA = sBuf + A * kTileVecs, *iB = sBuf + (A ^ 1u) * kTileVecs;
                 int32_t *dA = sDst + A * (kTile + 4u), *dB = sDst + (A ^ 1u) * (kTile + 4u);
-                const uint32_t nValid = rank_tile(iA, dA, n, true, round + 1u, true);
+                const uint32_t nValid = rank_tile(iA, dA, n, true, round + 1u, true, false);
                 const uint32_t nNext = W::kAppendRetired ? dStart[R] : nValid;
                 const uint32_t retiredNow = W::kAppendRetired ? dCnt[R] : 0u;
                 if (lr) a.roundLog[7 * round + 1] = a.roundLog[7 * round + 2] = globaltimer();
@@ -660,7 +663,8 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         // fuses only when that lands its items in P0.
         const uint32_t q = pre ? 0u : round + 1u;  // the round whose step the scatter may apply
         const bool fuse = kFuse && a.fuseStep && q < a.maxRounds && !(q + 1u == a.maxRounds && xsel == 0u);
-        uint4 *const curItems = curItemsOf(xsel);
+        // the pre-round may read the seeded items where the caller keeps them
+        const uint4 *const curItems = (pre && a.seedItems) ? a.seedItems : curItemsOf(xsel);
         int32_t *const curDest = curDestOf(xsel);
         uint4 *const nxtItems = fuse ? (xsel ? a.out : a.in) : a.in;
         int32_t *const nxtDest = xsel ? a.dest : a.dest2;
@@ -895,7 +899,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             }
             int32_t *dts = sDst + buf * (kTile + 4u);
             uint4 *sItems = sBuf + buf * kTileVecs;
-            const uint32_t nValid = rank_tile(sItems, dts, cnt, fuse, q, false);
+            const uint32_t nValid = rank_tile(sItems, dts, cnt, fuse, q, false, t > 0);
             // consecutive threads write consecutive 16-byte vectors of the
             // destination-grouped tile (coalesced runs per destination)
             const uint32_t total = nValid * V;
@@ -913,8 +917,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                     if (kFuse && fuse && part == 0u) nxtDest[dst] = dts[src];
                 }
             }
-            __syncthreads();
-            for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dCnt[e];
+            __syncthreads();  // the buffer is read before its next bulk load is issued
         }
         fence_proxy_async_global();
         if (logRound) {
@@ -963,7 +966,7 @@ template <class W>
 rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStream_t s,
                         unsigned long long *roundLog, uint32_t roundLogCap, uint4 *retiredOut,
                         unsigned long long retiredCap, unsigned long long *retiredCountOut, unsigned long long res[4],
-                        bool stepOnArrival = false, bool seeded = false)
+                        bool stepOnArrival = false, bool seeded = false, const void *seedItems = nullptr)
 {
     if ((seeded || stepOnArrival) && !W::kFuseStep) {
         set_error("persistent rounds: the policy does not step on arrival");
@@ -1042,6 +1045,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.retiredCap = retiredOut ? retiredCap : 0ull;
     a.retiredCountOut = retiredCountOut;
     a.seedCount = seeded ? &ctx->dev->outCount : nullptr;
+    a.seedItems = seeded ? static_cast<const uint4 *>(seedItems) : nullptr;
     a.fuseStep = stepOnArrival ? 1u : 0u;
     a.maxRounds = maxRounds;
     a.numRanks = R;

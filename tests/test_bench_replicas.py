@@ -1,0 +1,65 @@
+"""The multi-GPU form of bench.py is replicas only: every rank runs the whole
+workload, the job's time is the slowest rank's and its work the sum over
+ranks.  These tests run that reduction, and the reference arm's rank
+handling, as two gloo ranks on the CPU (127.0.0.1)."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+
+    assert bench.dist_env() == (world, rank, rank)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank r took 1 + r seconds for 100 (r + 1) units, end to end 2 + r seconds for 10 units
+        got = bench.reduce_over_ranks(dist, torch.device("cpu"), 1.0 + rank, 100 * (rank + 1), 2.0 + rank, 10)
+        out[rank] = got
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_take_the_slowest_rank_and_sum_the_work():
+    world = 2
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert out[r] == (2.0, 300, 3.0, 20)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class Args:
+        steps, warmup = 1, 0
+
+    assert bench.run_reference(Args()) == 0
+    assert capsys.readouterr().out == ""

@@ -237,6 +237,27 @@ def test_batched_host_memory_and_round_log():
     assert int(lg[:, 6].sum()) == fwd
 
 
+@pytest.mark.parametrize("fuse", [True, False], ids=["step_on_arrival", "step_in_place"])
+def test_batched_pinned_host_buffers(fuse):
+    # page-locked host buffers: the kernel writes the retired items straight
+    # into the host buffer; the result equals the device-memory run's
+    n, seed = 200003, 12
+    items = inputs.c1_items(n, seed=seed)
+    s = stream()
+    h_items = torch.from_numpy(items.view(np.int32)).pin_memory()
+    h_ret = torch.zeros((n, 16), dtype=torch.int32).pin_memory()
+    d_ret = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+    with rafi.Context(R, 64, n) as ctx:
+        for mode in MODES:
+            h_ret.zero_()
+            st, ch, rh, fh = rafi.rf_c1_run_batched(ctx.handle, h_items.data_ptr(), n, seed, mode, 1.1, GRID,
+                                                    h_ret.data_ptr(), True, stream=s, step_on_arrival=fuse)
+            st, cd, rd, fd = rafi.rf_c1_run_batched(ctx.handle, to_dev(items), n, seed, mode, 1.1, GRID, d_ret,
+                                                    False, stream=s, step_on_arrival=fuse)
+            assert (ch, rh, fh) == (cd, rd, fd) and ch == n
+            np.testing.assert_array_equal(h_ret.numpy(), d_ret.cpu().numpy())
+
+
 def test_batched_full_size_matches_plain():
     n, seed = 1 << 24, 1
     items = inputs.c1_items(n, seed=seed)
