@@ -139,42 +139,55 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsign
     return old;
 }
 
-// Bounded grid barrier for a cooperative launch (all CTAs resident), in two
-// levels: CTAs arrive on one of kSyncGroups group counters (separate cache
-// lines), the last CTA of a group arrives on the top counter, and the last
-// group releases everyone by publishing the barrier's sequence number.
+// Bounded grid barrier for a cooperative launch (all CTAs resident).
 // Counters only grow (the launch zeroes them): barrier number `seq` (0, 1,
-// ...) is complete on a group counter at members * (seq + 1) and on the top
-// counter at groups * (seq + 1), so no counter is reset and the critical
-// path is two atomics and one release store.  Arrivals are release
-// operations and the wait an acquire load, which orders every CTA's writes
+// ...) is complete once the counter reaches G * (seq + 1), so nothing is
+// ever reset.  kFlatBarrier: every CTA adds to one counter and waits for it
+// to reach the target (one atomic and one load on the critical path).
+// Otherwise, in two levels: CTAs arrive on one of kSyncGroups group
+// counters (separate cache lines), the last of a group on the top counter,
+// and the last group publishes the sequence number.  Arrivals are release
+// operations and the waits acquire loads, which orders every CTA's writes
 // before the barrier with every read after it.
 // Returns false when any CTA has given up; the caller must then return.
+constexpr bool kFlatBarrier = true;
+
 __device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned int seq)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int ok = 1;
         const unsigned int G = gridDim.x;
-        const unsigned int groups = G < (unsigned)kSyncGroups ? G : (unsigned)kSyncGroups;
-        const unsigned int grp = blockIdx.x % groups;
-        const unsigned int members = G / groups + (grp < G % groups ? 1u : 0u);
+        unsigned int *watch;
+        unsigned int target;
         bool last = false;
-        if (atom_add_release(&gs->group[grp][0], 1u) + 1u == members * (seq + 1u))
-            last = atom_add_acq_rel(&gs->count, 1u) + 1u == groups * (seq + 1u);
-        if (last) {
-            st_release(&gs->gen, seq + 1u);
+        if (kFlatBarrier) {
+            watch = &gs->count;
+            target = G * (seq + 1u);
+            last = atom_add_release(watch, 1u) + 1u == target;
         } else {
+            const unsigned int groups = G < (unsigned)kSyncGroups ? G : (unsigned)kSyncGroups;
+            const unsigned int grp = blockIdx.x % groups;
+            const unsigned int members = G / groups + (grp < G % groups ? 1u : 0u);
+            watch = &gs->gen;
+            target = seq + 1u;
+            if (atom_add_release(&gs->group[grp][0], 1u) + 1u == members * (seq + 1u))
+                last = atom_add_acq_rel(&gs->count, 1u) + 1u == groups * (seq + 1u);
+            if (last) st_release(&gs->gen, seq + 1u);
+        }
+        if (!last) {
             const long long t0 = clock64();
-            while (ld_acquire(&gs->gen) < seq + 1u) {
-                if (ld_acquire(&gs->abort)) {
-                    ok = 0;
-                    break;
-                }
-                if (clock64() - t0 > kSpinLimitCycles) {
-                    atomicExch(&gs->abort, 1u);
-                    ok = 0;
-                    break;
+            for (unsigned int k = 0; ld_acquire(watch) < target; ++k) {
+                if ((k & 15u) == 15u) {
+                    if (ld_acquire(&gs->abort)) {
+                        ok = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > kSpinLimitCycles) {
+                        atomicExch(&gs->abort, 1u);
+                        ok = 0;
+                        break;
+                    }
                 }
                 __nanosleep(20);
             }
