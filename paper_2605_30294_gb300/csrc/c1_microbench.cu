@@ -159,27 +159,32 @@ struct C1Work {
     uint32_t seed;
     int32_t mode, gx, gy, gz, R;
 
-    // shared memory: the Zipf thresholds, or the torus neighbour table [rank][6]
+    // shared memory: the Zipf thresholds, or (up to 256 ranks) the torus
+    // neighbour table [rank][6] in bytes, small enough to keep three CTAs per SM
+    __host__ __device__ bool nbrTable() const { return mode == RF_C1_NBR6 && R <= 256; }
     __host__ __device__ uint32_t smemBytes() const
     {
-        return (uint32_t)(R > 1 ? R : 1) * (mode == RF_C1_NBR6 ? 6u : 1u) * 4u;
+        return nbrTable() ? ((uint32_t)R * 6u + 15u) / 16u * 16u : (uint32_t)(R > 1 ? R : 1) * 4u;
     }
     __device__ void load_smem(void *s) const
     {
-        uint32_t *t = static_cast<uint32_t *>(s);
-        if (mode == RF_C1_ZIPF)
+        if (mode == RF_C1_ZIPF) {
+            uint32_t *t = static_cast<uint32_t *>(s);
             for (int e = threadIdx.x; e < R - 1; e += blockDim.x) t[e] = zipfThr[e];
-        if (mode == RF_C1_NBR6)
+        }
+        if (nbrTable()) {
+            uint8_t *t = static_cast<uint8_t *>(s);
             for (int e = threadIdx.x; e < 6 * R; e += blockDim.x)
-                t[e] = (uint32_t)torus_neighbour(e / 6, e % 6, gx, gy, gz);
+                t[e] = (uint8_t)torus_neighbour(e / 6, e % 6, gx, gy, gz);
+        }
     }
     __device__ int32_t step(uint4 (&w)[4], int32_t rank, uint32_t round, const void *s) const
     {
         const uint4 r = philox4x32_10(make_uint4(w[0].x, w[0].y, w[3].w, round), make_uint2(seed, 1u));
         if (r.x < kRetire) return -1;
-        const uint32_t *t = static_cast<const uint32_t *>(s);
-        const int32_t d = mode == RF_C1_NBR6 ? (int32_t)t[rank * 6 + (int32_t)(((unsigned long long)r.y * 6u) >> 32)]
-                                             : choose_dest(mode, rank, r.y, R, t, gx, gy, gz);
+        const int32_t d =
+            nbrTable() ? (int32_t)static_cast<const uint8_t *>(s)[rank * 6 + (int32_t)(((unsigned long long)r.y * 6u) >> 32)]
+                       : choose_dest(mode, rank, r.y, R, static_cast<const uint32_t *>(s), gx, gy, gz);
         w[3].z = (uint32_t)d;
         w[3].y ^= r.z;
         w[3].w += 1u;
