@@ -110,6 +110,15 @@ typedef struct rf_phase_times {
  * *out is set on success and must be released with rf_destroy. */
 rf_status rf_create(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, rf_ctx **out);
 
+/* rf_create over queues the caller owns (for example torch tensors): in and
+ * outQueue hold capacity x itemBytes bytes each, dest ((capacity + 3) / 4 *
+ * 4 + 4) int32 entries; all device memory, 16-byte aligned, alive until
+ * rf_destroy, which leaves them alone.  The context allocates only its
+ * offsets, counters and scratch.  rf_resize is refused (RF_ERR_ARG).
+ * RF_ERR_ARG for NULL, misaligned or non-device buffers. */
+rf_status rf_create_with_buffers(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, void *in, void *outQueue,
+                                 int32_t *dest, rf_ctx **out);
+
 /* Release every allocation of the context (synchronises the device). NULL is a no-op. */
 rf_status rf_destroy(rf_ctx *ctx);
 

@@ -117,9 +117,11 @@ namespace {
 
 void free_queues(rf_ctx *ctx)
 {
-    cudaFree(ctx->in);
-    cudaFree(ctx->out);
-    cudaFree(ctx->dest);
+    if (!ctx->callerQueues) {
+        cudaFree(ctx->in);
+        cudaFree(ctx->out);
+        cudaFree(ctx->dest);
+    }
     cudaFree(ctx->tileHist);
     cudaFree(ctx->staging);
     ctx->in = ctx->out = nullptr;
@@ -135,10 +137,12 @@ rf_status alloc_queues(rf_ctx *ctx, uint64_t capacity)
     rf_status st = configure_exchange(ctx);
     if (st != RF_OK) return st;
     const size_t qbytes = (size_t)capacity * ctx->itemBytes;
-    RF_CUDA(cudaMalloc(&ctx->in, qbytes));
-    RF_CUDA(cudaMalloc(&ctx->out, qbytes));
-    // padded to whole 16-byte units (+16 bytes) so a tile of destinations can be bulk-copied
-    RF_CUDA(cudaMalloc(&ctx->dest, ((size_t)capacity + 3) / 4 * 16 + 16));
+    if (!ctx->callerQueues) {
+        RF_CUDA(cudaMalloc(&ctx->in, qbytes));
+        RF_CUDA(cudaMalloc(&ctx->out, qbytes));
+        // padded to whole 16-byte units (+16 bytes) so a tile of destinations can be bulk-copied
+        RF_CUDA(cudaMalloc(&ctx->dest, ((size_t)capacity + 3) / 4 * 16 + 16));
+    }
     if (rf_status hs = ensure_tile_hist(ctx)) return hs;
     RF_CUDA(cudaMemset(ctx->inOffset, 0, (size_t)(ctx->numRanks + 1) * sizeof(uint32_t)));
     RF_CUDA(cudaMemset(ctx->count, 0, (size_t)ctx->numRanks * sizeof(uint32_t)));
@@ -184,7 +188,41 @@ using namespace rfi;
 
 extern "C" {
 
+namespace {
+rf_status create_ctx(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, void *inBuf, void *outBuf,
+                     int32_t *destBuf, rf_ctx **out);
+}
+
 rf_status rf_create(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, rf_ctx **out)
+{
+    return create_ctx(numRanks, itemBytes, capacity, nullptr, nullptr, nullptr, out);
+}
+
+rf_status rf_create_with_buffers(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, void *in, void *outQueue,
+                                 int32_t *dest, rf_ctx **out)
+{
+    if (!in || !outQueue || !dest || ((uintptr_t)in & 15u) || ((uintptr_t)outQueue & 15u) ||
+        ((uintptr_t)dest & 15u)) {
+        set_error("rf_create_with_buffers: the queue buffers must be non-NULL and 16-byte aligned");
+        if (out) *out = nullptr;
+        return RF_ERR_ARG;
+    }
+    cudaPointerAttributes pa;
+    for (const void *p : {static_cast<const void *>(in), static_cast<const void *>(outQueue),
+                          static_cast<const void *>(dest)}) {
+        if (cudaPointerGetAttributes(&pa, p) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+            (void)cudaGetLastError();
+            set_error("rf_create_with_buffers: the queue buffers must be device memory");
+            if (out) *out = nullptr;
+            return RF_ERR_ARG;
+        }
+    }
+    return create_ctx(numRanks, itemBytes, capacity, in, outQueue, dest, out);
+}
+
+namespace {
+rf_status create_ctx(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, void *inBuf, void *outBuf,
+                     int32_t *destBuf, rf_ctx **out)
 {
     if (!out) {
         set_error("rf_create: out is NULL");
@@ -210,6 +248,12 @@ rf_status rf_create(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, rf_
     }
     ctx->numRanks = numRanks;
     ctx->itemBytes = itemBytes;
+    if (inBuf) {
+        ctx->callerQueues = true;
+        ctx->in = inBuf;
+        ctx->out = outBuf;
+        ctx->dest = destBuf;
+    }
     rf_status st = RF_OK;
     do {
         cudaError_t e = cudaGetDevice(&ctx->device);
@@ -246,6 +290,7 @@ rf_status rf_create(int32_t numRanks, uint32_t itemBytes, uint64_t capacity, rf_
     *out = ctx;
     return RF_OK;
 }
+}  // namespace
 
 rf_status rf_destroy(rf_ctx *ctx)
 {
@@ -271,6 +316,10 @@ rf_status rf_resize(rf_ctx *ctx, uint64_t capacity)
     if (rf_status st = check_ctx(ctx, "rf_resize")) return st;
     if (capacity == 0 || capacity > RF_MAX_CAPACITY) {
         set_error("rf_resize: capacity %llu outside [1, 2^31 - 1]", (unsigned long long)capacity);
+        return RF_ERR_ARG;
+    }
+    if (ctx->callerQueues) {
+        set_error("rf_resize: the queues belong to the caller (rf_create_with_buffers); create a new context");
         return RF_ERR_ARG;
     }
     DeviceGuard g(ctx->device);

@@ -51,6 +51,7 @@ struct rf_ctx {
     void *in = nullptr;
     void *out = nullptr;
     int32_t *dest = nullptr;
+    bool callerQueues = false;  // in, out and dest belong to the caller (rf_create_with_buffers)
     uint32_t *inOffset = nullptr;  // numRanks + 1
     uint32_t *count = nullptr;     // numRanks
     uint32_t *tileHist = nullptr;  // numRanks x maxTiles, digit-major

@@ -97,6 +97,7 @@ _SIGS = {
     "rf_c0_raygen": [_P, _P, _i32, _i32, _i32, _i32, _P, _P],
     "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
     "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
+    "rf_create_with_buffers": [_i32, _u32, _u64, _P, _P, _P, _P],
     "rf_get_exchange_config": [_P, _P],
     "rf_set_exchange_config": [_P, _P],
     "rf_tune_exchange": [_P, _P, _u32, _P, _P],
@@ -383,8 +384,13 @@ def rf_c4_render(ctx: int, bricks, n: int, brick: int, sigma_max: float, views, 
 class Context:
     """Owning handle of an rf_ctx (host context of Sec. 3.4)."""
 
-    def __init__(self, num_ranks: int, item_bytes: int, capacity: int):
-        self.handle = rf_create(num_ranks, item_bytes, capacity)
+    def __init__(self, num_ranks: int, item_bytes: int, capacity: int, buffers=None):
+        """buffers: optional (in_queue, out_queue, dest) device buffers the caller owns."""
+        if buffers is None:
+            self.handle = rf_create(num_ranks, item_bytes, capacity)
+        else:
+            self.handle = rf_create_with_buffers(num_ranks, item_bytes, capacity, *buffers)
+        self.buffers = buffers  # keeps caller-owned queues alive while the context uses them
         self.num_ranks, self.item_bytes, self.capacity = num_ranks, item_bytes, capacity
 
     def close(self):
@@ -468,3 +474,11 @@ def rf_tune_exchange(ctx: int, stream=None, trials: int = 3):
     _check("rf_tune_exchange", lib().rf_tune_exchange(ctx, stream_handle(stream), trials, ctypes.byref(cfg),
                                                       ctypes.byref(ms)))
     return cfg.as_tuple(), float(ms.value)
+
+
+def rf_create_with_buffers(num_ranks: int, item_bytes: int, capacity: int, in_queue, out_queue, dest) -> int:
+    """A context over caller-owned device queues; returns its handle (close it with rf_destroy)."""
+    h = ctypes.c_void_p()
+    _check("rf_create_with_buffers", lib().rf_create_with_buffers(num_ranks, item_bytes, capacity, ptr(in_queue),
+                                                                  ptr(out_queue), ptr(dest), ctypes.byref(h)))
+    return h.value

@@ -252,3 +252,33 @@ def test_tuner_keeps_the_out_queue_and_picks_a_variant():
         # an empty out-queue has nothing to tune on
         with pytest.raises(rafi.RafiError):
             rafi.rf_tune_exchange(ctx.handle, s)
+
+
+def test_context_over_caller_owned_queues():
+    R, ib, n = 64, 64, 30011
+    rng = np.random.default_rng(21)
+    items = _items(n, ib, 22)
+    dest = rng.integers(0, R, size=n).astype(np.int32)
+    want, woff, _, _ = oracle.partition(items, dest, R)
+    cuda = torch.device("cuda:0")
+    q_in = torch.zeros((n, ib), dtype=torch.uint8, device=cuda)
+    q_out = torch.zeros((n, ib), dtype=torch.uint8, device=cuda)
+    q_dest = torch.zeros((n + 3) // 4 * 4 + 4, dtype=torch.int32, device=cuda)
+    s = stream()
+    with rafi.Context(R, ib, n, buffers=(q_in, q_out, q_dest)) as ctx:
+        q = rafi.rf_get_device_queues(ctx.handle)
+        assert (q.in_, q.out, q.dest) == (q_in.data_ptr(), q_out.data_ptr(), q_dest.data_ptr())
+        na, got, off = _exchange_with(ctx, R, ib, items, dest, s)
+        assert na == n
+        np.testing.assert_array_equal(off, woff)
+        np.testing.assert_array_equal(got, want)
+        # the delivered queue is the caller's tensor
+        np.testing.assert_array_equal(q_in.cpu().numpy(), want)
+        with pytest.raises(rafi.RafiError):
+            rafi.rf_resize(ctx.handle, 2 * n)
+    # destroying the context leaves the caller's buffers usable
+    q_in.fill_(7)
+    torch.cuda.synchronize()
+    assert int(q_in[0, 0]) == 7
+    with pytest.raises(rafi.RafiError):
+        rafi.rf_create_with_buffers(R, ib, n, q_in[:, 1:], q_out, q_dest)  # misaligned
