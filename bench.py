@@ -200,17 +200,26 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def rounds_kernel_traffic():
     """DRAM bytes per full-size launch of the persistent kernel from the committed ncu
-    summary, or None when the kernel's sources changed since it was captured."""
-    import hashlib
-
+    summary, or None when the kernel's code changed since it was captured."""
     p = os.path.join(ROOT, "profiles", "rounds_kernel_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
+    return d.get("bytes_per_full_size_launch") if d.get("code_sha256") == rounds_kernel_code_hash() else None
+
+
+def rounds_kernel_code_hash() -> str:
+    """sha256 of the persistent kernel's sources with comments and blank space
+    removed (a change of comments leaves the captured counters valid)."""
+    import hashlib
+    import re
+
     srcs = ("paper_2605_30294_gb300/csrc/rounds.cuh", "paper_2605_30294_gb300/csrc/c1_microbench.cu")
-    h = hashlib.sha256(b"".join(open(os.path.join(ROOT, x), "rb").read() for x in srcs)).hexdigest()
-    return d.get("bytes_per_full_size_launch") if d.get("sources_sha256") == h else None
+    text = "".join(open(os.path.join(ROOT, x)).read() for x in srcs)
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return hashlib.sha256(re.sub(r"\s+", "", text).encode()).hexdigest()
 
 
 def c0_rays_per_s(torch, rafi, inputs, s, reps=20):

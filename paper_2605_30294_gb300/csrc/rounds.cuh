@@ -7,12 +7,12 @@
 // CTAs of one cooperative launch stay resident and run the rounds
 // themselves:
 //
-//   phase 1  each CTA takes a contiguous range of the incoming queue, stages
-//            it tile by tile with a bulk async copy, applies the workload's
-//            step to every item and writes the tile back to the same slots of
-//            the out-queue with one bulk store (destination -1 for an item
-//            that retired: the paper's first single-array queue, Sec. 3.2),
-//            counting destinations per CTA;
+//   phase 1  the workload's step over the incoming queue, written back to
+//            the same slots of the out-queue with each item's destination
+//            (the paper's first single-array queue, Sec. 3.2): tile by tile
+//            over a contiguous range per CTA, or in dynamically handed-out
+//            chunks for policies with long, uneven steps; then each CTA
+//            counts the destinations of its range;
 //   barrier  (bounded spin)
 //   phase 2  per-destination totals -> segment offsets (Sec. 4.2.2) and the
 //            next active count (Sec. 4.2.3); each CTA's base per destination =
@@ -21,9 +21,14 @@
 //            stably and grouped by destination, into the incoming queue;
 //   barrier  then the next round, until no item is active.
 //
-// Because the out slot of an item is its input slot and every step is
-// stable, queue order never depends on scheduling: round k's incoming queue
-// equals the one of a serial round-by-round simulation.
+// Step on arrival (policies with kFuseStep): phase 3 applies the next
+// round's step to each item as it lands, so later rounds skip phase 1 and
+// only count the destinations the scatter wrote; each item crosses HBM once
+// per round.
+//
+// Because every step is per item and every scatter stable, queue order never
+// depends on scheduling: round k's incoming queue equals the one of a serial
+// round-by-round simulation.
 //
 // Every wait is bounded; a wait that gives up raises an abort flag that all
 // CTAs check at the next barrier, and the kernel returns with a timeout status.
