@@ -321,7 +321,7 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3):
         for spr, nrep in ((0, reps), (1, 1)):
             key = "brick_exit" if spr == 0 else "one_step_per_round"
             res[key] = {}
-            for batched in (True, False):
+            for batched in (1, 0, 2):
                 for _ in range(2 if spr == 0 else 1):
                     rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, spr, out,
                                    batched, stream=s)
@@ -337,10 +337,11 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3):
                 torch.cuda.synchronize()
                 sec = e0.elapsed_time(e1) / 1e3 / nrep
                 steps = int(out[:, 4].cpu().numpy().view(np.uint32).astype(np.int64).sum())
-                res[key]["batched" if batched else "plain"] = {
+                res[key][("plain", "batched", "graph")[batched]] = {
                     "ms_per_run": sec * 1e3, "particle_steps_per_s": steps / sec,
                     "items_forwarded_per_s": fwd / nrep / sec, "rounds": rounds, "particle_steps": steps}
             res[key]["batched_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["batched"]["ms_per_run"]
+            res[key]["graph_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["graph"]["ms_per_run"]
     return res
 
 
@@ -395,7 +396,7 @@ def c4_transport(torch, rafi, inputs, s):
                        "views 2048^2, 1024x768, 512^2, 3840x2160 at 16 spp, albedo 0.8, HG g=0.3, <= 64 bounces",
            "paths": paths}
     with rafi.Context(512, 64, paths) as ctx:
-        for batched in (True, False):
+        for batched in (1, 0, 2):
             score.zero_()
             rafi.rf_c4_render(ctx.handle, bricks, n, brick, smax, views, spp, 4, score, batched, stream=s)
             score.zero_()
@@ -407,9 +408,10 @@ def c4_transport(torch, rafi, inputs, s):
             e1.record(s)
             torch.cuda.synchronize()
             sec = e0.elapsed_time(e1) / 1e3
-            out["batched" if batched else "plain"] = {"ms": sec * 1e3, "paths_per_s": paths / sec,
-                                                      "rays_forwarded_per_s": fwd / sec, "rounds": rounds}
+            out[("plain", "batched", "graph")[batched]] = {"ms": sec * 1e3, "paths_per_s": paths / sec,
+                                                           "rays_forwarded_per_s": fwd / sec, "rounds": rounds}
     out["batched_over_plain"] = out["plain"]["ms"] / out["batched"]["ms"]
+    out["graph_over_plain"] = out["plain"]["ms"] / out["graph"]["ms"]
     return out
 
 

@@ -377,8 +377,10 @@ rf_status rf_c2_trace(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, fl
 
 /* Seed, exchange, then rounds of trace + exchange until no particle is
  * active.  batched == 0: the plain host loop (rf_c2_trace + rf_exchange per
- * round); batched != 0: all rounds in one persistent cooperative kernel (the
- * batched form of rf_c1_run_batched).  out (device) receives every particle
+ * round); batched == 1: all rounds in one persistent cooperative kernel (the
+ * batched form of rf_c1_run_batched); batched == 2: the trace kernel and the
+ * exchange kernels captured once into a CUDA graph whose conditional while
+ * node repeats them on the device while particles are active.  out (device) receives every particle
  * by id; *rounds = trace rounds, *forwarded = particles delivered by them. */
 rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const uint32_t *setIds, uint64_t n,
                     int32_t N, int32_t B, float h, uint32_t maxSteps, uint32_t stepsPerRound, void *out,
@@ -425,8 +427,9 @@ rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int3
  * null collision moves on with e + 1.  u(r) = top 24 bits / 2^24.  Paths are
  * forwarded to the rank owning their next tentative collision point (VoPaT,
  * Sec. 5.1, Fig. 1).  score (device, total pixels; the caller zeroes it)
- * receives the number of escaped paths per pixel.  batched != 0: all rounds
- * in one persistent kernel.  *rounds, *forwarded as rf_c2_run. */
+ * receives the number of escaped paths per pixel.  batched: 0 host loop, 1
+ * persistent kernel, 2 CUDA graph loop, as rf_c2_run.  *rounds, *forwarded
+ * as rf_c2_run. */
 rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, float sigmaMax, int32_t numViews,
                        const float *cams, const int32_t *sizes, int32_t spp, uint32_t seed, float *score,
                        int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded);

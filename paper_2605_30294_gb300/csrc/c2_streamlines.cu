@@ -352,7 +352,19 @@ rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const 
     if (rf_status st = rf_c2_seed(ctx, seeds, setIds, n, N, B, stream)) return st;
     const C2Params P = make_params(bricks, N, B, h, maxSteps, stepsPerRound, out, n);
     uint64_t active = 0, fwd = 0, r = 0;
-    if (batched) {
+    if (batched == 2) {
+        // graph form: the trace kernel and the exchange repeated by a while node
+        if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
+        rf_status st = run_graph_loop(ctx, s, maxRounds, [&](cudaStream_t cs) -> rf_status {
+            rf_device_queues q;
+            rf_get_device_queues(ctx, &q);
+            trace_kernel<<<grid_for(ctx, ctx->capacity), kBlock, 0, cs>>>(P, q);
+            RF_LAUNCHED("c2 trace_kernel");
+            return launch_exchange(ctx, cs);
+        }, &r, &fwd);
+        if (st != RF_OK) return st;
+        active = ctx->host->numActive;
+    } else if (batched) {
         if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
         C2Work w;
         w.P = P;

@@ -349,7 +349,17 @@ extern "C" rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, i
     set_count_kernel<<<1, 32, 0, s>>>(q.outCount, total);
     RF_LAUNCHED("c4 set_count_kernel");
     uint64_t active = 0, fwd = 0, r = 0;
-    if (batched) {
+    if (batched == 2) {
+        // graph form: the tracking kernel and the exchange repeated by a while node
+        if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
+        rf_status st = run_graph_loop(ctx, s, maxRounds, [&](cudaStream_t cs) -> rf_status {
+            track_kernel<<<grid_for(ctx, ctx->capacity), kBlock, 0, cs>>>(P, q);
+            RF_LAUNCHED("c4 track_kernel");
+            return launch_exchange(ctx, cs);
+        }, &r, &fwd);
+        if (st != RF_OK) return st;
+        active = ctx->host->numActive;
+    } else if (batched) {
         if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
         C4Work w;
         w.P = P;

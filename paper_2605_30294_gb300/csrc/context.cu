@@ -304,6 +304,7 @@ rf_status rf_destroy(rf_ctx *ctx)
     cudaFree(ctx->stagingCount);
     cudaFree(ctx->zipfThr);
     cudaFree(ctx->roundsScratch);
+    cudaFree(ctx->loopState);
     if (ctx->host) cudaFreeHost(ctx->host);
     for (int i = 0; i < 2 * kTimeSlots; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <functional>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -67,6 +68,7 @@ struct rf_ctx {
     bool pending = false;  // an exchange's read-back has not been waited for
 
     void *roundsScratch = nullptr;  // lazily allocated scratch of the persistent round kernel
+    void *loopState = nullptr;      // lazily allocated: rounds / forwarded / limit of the graph loop
     size_t roundsScratchBytes = 0;
 
     uint32_t *zipfThr = nullptr;  // numRanks words: Zipf table of the microbenchmark
@@ -125,6 +127,15 @@ rf_status launch_exchange(rf_ctx *ctx, cudaStream_t s);
 // the defaults), and room for the per-tile histograms of that tile.
 rf_status configure_exchange(rf_ctx *ctx);
 rf_status ensure_tile_hist(rf_ctx *ctx);
+
+// The graph form of the round loop: `round` enqueues one round's kernels
+// (work, then the exchange) on the stream it is given; they are captured
+// once into the body of a CUDA graph while node that repeats them, with no
+// host round trip, while the exchange reports active items and fewer than
+// maxRounds rounds have run.  Starts from the context's last exchange (which
+// must be enqueued on s before); waits for s.  *rounds, *forwarded (host).
+rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
+                         const std::function<rf_status(cudaStream_t)> &round, uint64_t *rounds, uint64_t *forwarded);
 
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);

@@ -52,7 +52,7 @@ def check_against_oracle(got, want, idx=None):
     assert rel.max() <= 1e-5, rel.max()
 
 
-@pytest.mark.parametrize("batched", [False, True])
+@pytest.mark.parametrize("batched", [0, 1, 2], ids=["host_loop", "persistent", "graph"])
 @pytest.mark.parametrize("spr", [0, 1])
 def test_streamlines_match_oracle(batched, spr):
     n, brick = 64, 16
@@ -98,9 +98,11 @@ def test_uneven_seed_sets_in_one_launch():
     np.testing.assert_array_equal(got["set"], set_ids)
     want = oracle.c2_trace(f, seeds, brick, 0.25, 2000)
     check_against_oracle(got, want)
-    plain = run_gpu(f, n, brick, seeds, set_ids=set_ids, batched=False)
-    np.testing.assert_array_equal(plain["pos"].view(np.uint32), got["pos"].view(np.uint32))
-    assert plain["forwarded"] == got["forwarded"] and plain["rounds"] == got["rounds"]
+    for form in (0, 2):  # the host loop and the graph loop give the same particles
+        other = run_gpu(f, n, brick, seeds, set_ids=set_ids, batched=form)
+        np.testing.assert_array_equal(other["pos"].view(np.uint32), got["pos"].view(np.uint32))
+        np.testing.assert_array_equal(other["steps"], got["steps"])
+        assert other["forwarded"] == got["forwarded"] and other["rounds"] == got["rounds"]
 
 
 def test_full_size_sampled():

@@ -57,12 +57,14 @@ def test_partition_independence_and_forms():
     views = inputs.c4_views(n, SMALL_VIEWS)
     a = gpu_render(vol, smax, views, 128, spp)[0]
     b = gpu_render(vol, smax, views, 32, spp)[0]
-    c, rc, fc = gpu_render(vol, smax, views, 16, spp, batched=True)
-    d, rd, fd = gpu_render(vol, smax, views, 16, spp, batched=False)
+    c, rc, fc = gpu_render(vol, smax, views, 16, spp, batched=1)
+    d, rd, fd = gpu_render(vol, smax, views, 16, spp, batched=0)
+    e, re_, fe = gpu_render(vol, smax, views, 16, spp, batched=2)  # the graph loop
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(a, c)
     np.testing.assert_array_equal(c, d)
-    assert (rc, fc) == (rd, fd)
+    np.testing.assert_array_equal(c, e)
+    assert (rc, fc) == (rd, fd) == (re_, fe)
 
 
 def test_full_size_crop():
