@@ -57,7 +57,6 @@ struct RoundsArgs {
     int32_t *dest2;            // the same size: second destination array (policies with kFuseStep)
     uint32_t *inOffset;        // numRanks + 1
     uint32_t *tot;             // gridDim.x rows of per-CTA destination counts (row stride: digits rounded to 4)
-    unsigned int *total;       // 2 x digits: per-destination totals (round parity)
     uint32_t *grpTot;          // 2 x kSyncGroups rows (stride as tot): per-group destination totals (round parity)
     GridSync *sync;
     unsigned long long *result;  // {rounds, forwarded, status, retired}
@@ -394,6 +393,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     constexpr uint32_t kTileVecs = kTile * V;
     constexpr uint32_t kRetFlag = 0x80000000u;
     constexpr bool kFuse = W::kFuseStep && !W::kDynamicWork;
+    static_assert((W::kStepReadMask & ((1u << V) - 1u)) != 0u, "a step reads part of its item");
     extern __shared__ __align__(128) unsigned char smem[];
     const int R = a.numRanks;
     const int D = R + (W::kAppendRetired ? 1 : 0);  // digits: ranks (+ retirement)
@@ -650,7 +650,6 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 const int32_t *dA = sDst + A * (kTile + 4u);
                 for (uint32_t v = tid; v < n * V; v += kRoundsBlock) a.out[v] = iA[v];
                 for (uint32_t i = tid; i < n; i += kRoundsBlock) a.dest[i] = dA[i];
-                for (int e = tid; e < 2 * D; e += kRoundsBlock) a.total[e] = 0u;
                 for (int e = tid; e < 2 * kSyncGroups * Dp; e += kRoundsBlock) a.grpTot[e] = 0u;
                 xsel = 0u;
             } else {
@@ -827,10 +826,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             for (int e = tid; e < D; e += kRoundsBlock) {
                 const uint32_t v = sTot[e];
                 a.tot[(size_t)c * Dp + e] = v;
-                if (v) {
-                    atomicAdd(&a.total[(it & 1u) * D + e], v);
-                    atomicAdd(&a.grpTot[((it & 1u) * kSyncGroups + grp) * Dp + e], v);
-                }
+                if (v) atomicAdd(&a.grpTot[((it & 1u) * kSyncGroups + grp) * Dp + e], v);
             }
         }
         fence_proxy_async_global();
@@ -841,60 +837,64 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         if (logRound) a.roundLog[7 * round + 2] = globaltimer();
 
         // ---- phase 2: offsets, next count, this CTA's base per destination -----
-        for (int e = tid; e < D; e += kRoundsBlock) {
-            dStart[e] = a.total[(it & 1u) * D + e];
-            dBase[e] = 0u;
-        }
-        const uint32_t retiredNow = W::kAppendRetired ? a.total[(it & 1u) * D + R] : 0u;
-        const uint32_t nNext = rounds_block_scan(dStart, R, tmp);  // ranks only
-        if (W::kAppendRetired && tid == 0) dStart[R] = (uint32_t)retiredSoFar;
+        // One bulk copy stages every group's totals and the rows of the CTAs
+        // before this one in its group: per destination, the total is the sum
+        // of the group rows, and this CTA's base the sum of the group rows
+        // before its group plus the member rows (in chunks when they do not
+        // fit the buffer).
         {
-            // counts of CTAs 0 .. c-1: the totals of the groups before this
-            // CTA's group, then the rows of the CTAs before it in its group,
-            // staged by bulk copies (a CTA with nothing to scatter needs no base)
-            const int groups = D >= kRoundsBlock ? 1 : kRoundsBlock / D;
-            const uint32_t gRows = nt ? (uint32_t)grp : 0u;
-            const uint32_t mRows = nt ? (uint32_t)(c - grpStart) : 0u;
+            const uint32_t nGroups = (uint32_t)((G + grpSize - 1) / grpSize);
+            const uint32_t mRows = (uint32_t)(c - grpStart);
             const uint32_t *gSrc = a.grpTot + (size_t)(it & 1u) * kSyncGroups * Dp;
             const uint32_t *mSrc = a.tot + (size_t)grpStart * Dp;
-            auto add_rows = [&](uint32_t rows) {
-                for (int t = tid; t < groups * D; t += kRoundsBlock) {
-                    const int e = t % D, g = t / D;
-                    uint32_t sum = 0;
-                    for (uint32_t rr = g; rr < rows; rr += groups) sum += sRows[rr * Dp + e];
-                    if (sum) atomicAdd(&dBase[e], sum);
+            for (int e = tid; e < D; e += kRoundsBlock) {
+                dStart[e] = 0u;
+                dBase[e] = 0u;
+            }
+            const uint32_t allRows = nGroups + mRows;
+            for (uint32_t r0 = 0; r0 < allRows && !failed; r0 += rowsPerStage) {
+                const uint32_t rows = min(rowsPerStage, allRows - r0);
+                if (tid == 0) {
+                    // rows r0 .. r0 + rows - 1 of [group rows, member rows]
+                    const uint32_t g0 = r0 < nGroups ? min(rows, nGroups - r0) : 0u;
+                    const uint32_t m0 = r0 < nGroups ? 0u : r0 - nGroups;
+                    if (g0 == 0)
+                        issue_bytes(1, sRows, mSrc + (size_t)m0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
+                    else if (g0 == rows)
+                        issue_bytes(1, sRows, gSrc + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
+                    else
+                        issue_bytes(1, sRows, gSrc + (size_t)r0 * Dp, g0 * Dp * 4u, sRows + g0 * Dp, mSrc,
+                                    (rows - g0) * Dp * 4u);
+                }
+                if (!wait(1)) {
+                    failed = true;
+                    break;
+                }
+                for (int e = tid; e < D; e += kRoundsBlock) {
+                    uint32_t tot = 0, before = 0;
+                    for (uint32_t rr = 0; rr < rows; ++rr) {
+                        const uint32_t row = r0 + rr;
+                        const uint32_t v = sRows[rr * Dp + e];
+                        if (row < nGroups) {
+                            tot += v;
+                            if (row < (uint32_t)grp) before += v;
+                        } else {
+                            before += v;
+                        }
+                    }
+                    dStart[e] += tot;
+                    dBase[e] += before;
                 }
                 __syncthreads();
-            };
-            if (gRows + mRows <= rowsPerStage) {
-                if (gRows + mRows) {
-                    if (tid == 0) {
-                        if (gRows)
-                            issue_bytes(1, sRows, gSrc, gRows * Dp * 4u, sRows + gRows * Dp, mSrc, mRows * Dp * 4u);
-                        else
-                            issue_bytes(1, sRows, mSrc, mRows * Dp * 4u, nullptr, nullptr, 0u);
-                    }
-                    if (!wait(1)) failed = true;
-                    else add_rows(gRows + mRows);
-                }
-            } else {
-                for (int seg = 0; seg < 2 && !failed; ++seg) {
-                    const uint32_t segRows = seg ? mRows : gRows;
-                    const uint32_t *src = seg ? mSrc : gSrc;
-                    for (uint32_t r0 = 0; r0 < segRows && !failed; r0 += rowsPerStage) {
-                        const uint32_t rows = min(rowsPerStage, segRows - r0);
-                        if (tid == 0) issue_bytes(1, sRows, src + (size_t)r0 * Dp, rows * Dp * 4u, nullptr, nullptr, 0u);
-                        if (!wait(1)) failed = true;
-                        else add_rows(rows);
-                    }
-                }
             }
-            __syncthreads();
-            for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dStart[e];
         }
+        const uint32_t retiredNow = W::kAppendRetired ? dStart[R] : 0u;
+        const uint32_t nNext = rounds_block_scan(dStart, R, tmp);  // ranks only
+        if (W::kAppendRetired && tid == 0) dStart[R] = (uint32_t)retiredSoFar;
+        __syncthreads();
+        for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dStart[e];
         if (c == 0) {
             for (int e = tid; e < R; e += kRoundsBlock) a.inOffset[e] = dStart[e];
-            for (int e = tid; e < D; e += kRoundsBlock) a.total[((it + 1u) & 1u) * D + e] = 0u;
             for (int e = tid; e < kSyncGroups * Dp; e += kRoundsBlock)
                 a.grpTot[(size_t)((it + 1u) & 1u) * kSyncGroups * Dp + e] = 0u;
             if (tid == 0) a.inOffset[R] = nNext;
@@ -1038,9 +1038,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     }
     const int G = ctx->numSMs * perSM;
     const size_t totBytes = (size_t)G * rounds_row_stride(D) * sizeof(uint32_t);
-    const size_t totalBytes = rounds_align_sz((size_t)2 * D * sizeof(unsigned int), 16);
     const size_t grpBytes = (size_t)2 * kSyncGroups * rounds_row_stride(D) * sizeof(uint32_t);
-    const size_t tailBytes = totalBytes + grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
+    const size_t tailBytes = grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
     // second destination array (step on arrival), padded like ctx->dest
     const size_t dest2Bytes = W::kFuseStep ? rounds_align_sz((size_t)(ctx->capacity + 3) / 4 * 16 + 16, 256) : 0;
     if (rf_status st = ensure_rounds_scratch(ctx, rounds_align_sz(totBytes + tailBytes, 256) + dest2Bytes)) return st;
@@ -1051,10 +1050,9 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.dest = ctx->dest;
     a.inOffset = ctx->inOffset;
     a.tot = reinterpret_cast<uint32_t *>(base);
-    a.total = reinterpret_cast<unsigned int *>(base + totBytes);
-    a.grpTot = reinterpret_cast<uint32_t *>(base + totBytes + totalBytes);
-    a.sync = reinterpret_cast<GridSync *>(base + totBytes + totalBytes + grpBytes);
-    a.result = reinterpret_cast<unsigned long long *>(base + totBytes + totalBytes + grpBytes + sizeof(GridSync));
+    a.grpTot = reinterpret_cast<uint32_t *>(base + totBytes);
+    a.sync = reinterpret_cast<GridSync *>(base + totBytes + grpBytes);
+    a.result = reinterpret_cast<unsigned long long *>(base + totBytes + grpBytes + sizeof(GridSync));
     a.dest2 = W::kFuseStep ? reinterpret_cast<int32_t *>(base + rounds_align_sz(totBytes + tailBytes, 256)) : nullptr;
     a.numActiveOut = &ctx->dev->numActive;
     a.roundLog = roundLog;
