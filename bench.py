@@ -230,18 +230,20 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
     bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
     rafi.rf_c0_make_bricks(dvol, n, brick, bricks, s)
     image = torch.zeros(w * h, dtype=torch.float32, device="cuda")
+    out = {}
     with rafi.Context(8, 48, w * h) as ctx:
-        for _ in range(3):
-            rafi.rf_c0_render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(reps):
-            rafi.rf_c0_render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
-        e1.record(s)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-    return w * h / (ms * 1e-3), ms
+        for name, render in (("host_loop", rafi.rf_c0_render), ("graph", rafi.rf_c0_render_graph)):
+            for _ in range(3):
+                render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
+            e1.record(s)
+            torch.cuda.synchronize()
+            out[name] = e0.elapsed_time(e1) / reps
+    return w * h / (out["host_loop"] * 1e-3), out["host_loop"], w * h / (out["graph"] * 1e-3), out["graph"]
 
 
 LOG_CAP = 4096  # rounds logged by the persistent kernel
@@ -565,7 +567,7 @@ def run_ours(args):
     barrier()
     e2e_s = time.perf_counter() - t0
 
-    rays_s, c0_ms = c0_rays_per_s(torch, rafi, inputs, s)
+    rays_s, c0_ms, rays_g, c0_ms_g = c0_rays_per_s(torch, rafi, inputs, s)
     ctx.close()
     del d_items, retired, h_items, h_ret
     torch.cuda.empty_cache()
@@ -635,7 +637,9 @@ def run_ours(args):
                 "h2d_bytes_per_step": len(MODES) * n * ITEM_BYTES,
                 "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8)},
         "rays_per_s": {"value": rays_s, "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
-                       "ms_per_frame": c0_ms},
+                       "ms_per_frame": c0_ms, "form": "host loop (rf_c0_render)",
+                       "graph": {"value": rays_g, "ms_per_frame": c0_ms_g,
+                                 "form": "rounds in a kept CUDA graph (rf_c0_render_graph)"}},
         "streamlines": streamlines,
         "differentiable_ea": ea,
         "delta_tracking": transport,

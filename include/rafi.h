@@ -342,6 +342,16 @@ rf_status rf_c0_render(rf_ctx *ctx, const float *bricks, const float *cam, int32
                        int32_t W, int32_t H, float *image, int32_t *hopLog, int32_t maxHops,
                        int32_t *hopCount, uint32_t maxRounds, void *stream, uint64_t *rounds);
 
+/* rf_c0_render as a CUDA graph: raygen and its exchange, then a conditional
+ * while node repeating { march; exchange } on the device while rays are
+ * active, with no host round trip per round.  The instantiated graph stays
+ * in the context and is relaunched while every argument is unchanged (a
+ * changed argument, rf_resize or an exchange configuration rebuilds it).
+ * Same arguments, results and errors as rf_c0_render. */
+rf_status rf_c0_render_graph(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W,
+                             int32_t H, float *image, int32_t *hopLog, int32_t maxHops, int32_t *hopCount,
+                             uint32_t maxRounds, void *stream, uint64_t *rounds);
+
 /* --- streamlines through bricks (32-byte particles) ------------------------ */
 
 /* Particle: {x, y, z (float bits), id} {steps, hops, set, status}; status 1 =

@@ -10,6 +10,8 @@
 //
 // Built with -fmad=false: positions, owners and tau follow the written
 // operation order exactly.
+#include <cstring>
+
 #include "internal.cuh"
 #include "rafi_device.cuh"
 
@@ -313,6 +315,71 @@ rf_status rf_c0_render(rf_ctx *ctx, const float *bricks, const float *cam, int32
         ++r;
     }
     if (rounds) *rounds = r;
+    return RF_OK;
+}
+
+rf_status rf_c0_render_graph(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W,
+                             int32_t H, float *image, int32_t *hopLog, int32_t maxHops, int32_t *hopCount,
+                             uint32_t maxRounds, void *stream, uint64_t *rounds)
+{
+    if (rf_status st = check_c0(ctx, N, B, "rf_c0_render_graph")) return st;
+    if (!cam || !image || !bricks || W < 1 || H < 1 || (uint64_t)W * H > ctx->capacity ||
+        (hopLog && (!hopCount || maxHops < 1))) {
+        set_error("rf_c0_render_graph: bad arguments");
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    Cam c;
+    for (int a = 0; a < 3; ++a) {
+        c.eye[a] = cam[a];
+        c.corner[a] = cam[3 + a];
+        c.du[a] = cam[6 + a];
+        c.dv[a] = cam[9 + a];
+    }
+    rf_device_queues q;
+    rf_get_device_queues(ctx, &q);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int blocks = (W * H + kBlock - 1) / kBlock;
+    // every pointer and value the captured kernels take
+    struct Key {
+        const float *bricks;
+        float cam[12];
+        int32_t N, B, W, H, maxHops;
+        float *image;
+        int32_t *hopLog, *hopCount;
+    } key;
+    memset(&key, 0, sizeof key);
+    key.bricks = bricks;
+    for (int a = 0; a < 12; ++a) key.cam[a] = cam[a];
+    key.N = N;
+    key.B = B;
+    key.W = W;
+    key.H = H;
+    key.maxHops = maxHops;
+    key.image = image;
+    key.hopLog = hopLog;
+    key.hopCount = hopCount;
+    uint64_t r = 0;
+    rf_status st = run_graph_loop(
+        ctx, s, maxRounds,
+        [&](cudaStream_t cs) -> rf_status {
+            if (rf_status ms = rf_c0_march(ctx, bricks, N, B, image, hopLog, maxHops, hopCount, cs)) return ms;
+            return launch_exchange(ctx, cs);
+        },
+        &r, nullptr,
+        [&](cudaStream_t cs) -> rf_status {
+            raygen_kernel<<<blocks, kBlock, 0, cs>>>(c, N, B, W, H, image, hopCount, q);
+            RF_LAUNCHED("raygen_kernel");
+            return launch_exchange(ctx, cs);
+        },
+        &key, sizeof key);
+    if (st != RF_OK) return st;
+    if (rounds) *rounds = r;
+    if (ctx->host->numActive) {
+        set_error("rf_c0_render_graph: %llu rays still active after %u rounds",
+                  (unsigned long long)ctx->host->numActive, maxRounds);
+        return RF_ERR_MAX_ROUNDS;
+    }
     return RF_OK;
 }
 

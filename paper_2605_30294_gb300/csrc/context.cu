@@ -297,6 +297,7 @@ rf_status rf_destroy(rf_ctx *ctx)
     if (!ctx) return RF_OK;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
+    drop_graph_loop(ctx);
     free_queues(ctx);
     cudaFree(ctx->inOffset);
     cudaFree(ctx->count);
@@ -326,6 +327,7 @@ rf_status rf_resize(rf_ctx *ctx, uint64_t capacity)
     DeviceGuard g(ctx->device);
     RF_CUDA(cudaDeviceSynchronize());
     ctx->pending = false;
+    drop_graph_loop(ctx);
     free_queues(ctx);
     return alloc_queues(ctx, capacity);
 }

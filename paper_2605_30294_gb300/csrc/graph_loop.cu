@@ -4,12 +4,18 @@
 // round waits for the host; unlike the persistent kernel, each round's
 // kernels launch with their own grid shapes and occupancy.
 //
+//   prologue          (optional, a child graph) the kernels that seed the
+//                     queue and its first exchange
 //   init kernel       rounds = forwarded = 0; condition = (numActive > 0 and
 //                     maxRounds > 0), from the exchange that seeded the queue
 //   while (condition) the round's kernels as the caller enqueues them
 //                     (captured once), then the control kernel: rounds += 1,
 //                     forwarded += numActive, condition = (numActive > 0 and
 //                     rounds < maxRounds)
+//
+// A caller that passes a key keeps the instantiated graph in the context and
+// relaunches it while the key (every pointer and value its kernels take)
+// stays the same; the context holds one such graph at a time.
 #include <functional>
 
 #include "internal.cuh"
@@ -41,16 +47,50 @@ __global__ void loop_control_kernel(cudaGraphConditionalHandle h, const DevState
 
 }  // namespace
 
+void drop_graph_loop(rf_ctx *ctx)
+{
+    if (ctx->loopExec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(ctx->loopExec));
+    if (ctx->loopGraph) cudaGraphDestroy(static_cast<cudaGraph_t>(ctx->loopGraph));
+    ctx->loopExec = nullptr;
+    ctx->loopGraph = nullptr;
+    ctx->loopKey.clear();
+    ctx->loopLaunchesPerRound = 0;
+    ctx->loopLaunchesOnce = 0;
+}
+
 rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
-                         const std::function<rf_status(cudaStream_t)> &round, uint64_t *rounds, uint64_t *forwarded)
+                         const std::function<rf_status(cudaStream_t)> &round, uint64_t *rounds, uint64_t *forwarded,
+                         const std::function<rf_status(cudaStream_t)> &prologue, const void *key, size_t keyBytes)
 {
     if (!ctx->loopState) RF_CUDA(cudaMalloc(&ctx->loopState, 3 * sizeof(unsigned long long)));
+    std::string k;
+    if (key) {
+        // the caller's key, the round limit and the exchange's launch shape
+        const uint64_t shape[4] = {maxRounds, ctx->tileItems, (uint64_t)ctx->scatterBlocks,
+                                   (uint64_t)ctx->countBlocks};
+        k.assign(static_cast<const char *>(key), keyBytes);
+        k.append(reinterpret_cast<const char *>(shape), sizeof shape);
+    }
+    const unsigned long long launches0 = g_launches.load();
+    if (key && ctx->loopExec && ctx->loopKey == k) {
+        // the same loop as last time: relaunch the instantiated graph
+        RF_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(ctx->loopExec), s));
+        unsigned long long res[3] = {0, 0, 0};
+        RF_CUDA(cudaMemcpyAsync(res, ctx->loopState, sizeof res, cudaMemcpyDeviceToHost, s));
+        RF_CUDA(cudaMemcpyAsync(ctx->host, ctx->dev, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        RF_CUDA(cudaStreamSynchronize(s));
+        ctx->pending = false;
+        if (rounds) *rounds = res[0];
+        if (forwarded) *forwarded = res[1];
+        count_launch(ctx->loopLaunchesOnce + ctx->loopLaunchesPerRound * res[0]);
+        return RF_OK;
+    }
+    drop_graph_loop(ctx);
     cudaGraph_t graph = nullptr, body = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
     const bool timing = ctx->timing;
-    const unsigned long long launches0 = g_launches.load();
-    unsigned long long bodyLaunches = 0;
+    unsigned long long bodyLaunches = 0, onceLaunches = 1;
     rf_status st = RF_OK;
     auto fail = [&](cudaError_t e, const char *what) {
         st = cuda_fail(e, what);
@@ -62,6 +102,25 @@ rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
         cudaGraphConditionalHandle h;
         e = cudaGraphConditionalHandleCreate(&h, graph, 0u, 0u);
         if (e != cudaSuccess) { fail(e, "cudaGraphConditionalHandleCreate"); break; }
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { fail(e, "cudaStreamCreate"); break; }
+        ctx->timing = false;  // event records may not sit inside a conditional body
+        // the prologue, captured into a child graph
+        cudaGraphNode_t proNode = nullptr;
+        if (prologue) {
+            cudaGraph_t pro = nullptr;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+            if (e != cudaSuccess) { fail(e, "cudaStreamBeginCapture"); break; }
+            const unsigned long long p0 = g_launches.load();
+            rf_status ps = prologue(cap);
+            onceLaunches += g_launches.load() - p0;
+            e = cudaStreamEndCapture(cap, &pro);
+            if (ps != RF_OK) { st = ps; if (pro) cudaGraphDestroy(pro); break; }
+            if (e != cudaSuccess) { fail(e, "cudaStreamEndCapture(prologue)"); break; }
+            e = cudaGraphAddChildGraphNode(&proNode, graph, nullptr, 0, pro);
+            cudaGraphDestroy(pro);  // the node holds its own copy
+            if (e != cudaSuccess) { fail(e, "cudaGraphAddChildGraphNode"); break; }
+        }
         // init kernel node
         cudaKernelNodeParams kp = {};
         const DevState *stp = ctx->dev;
@@ -73,7 +132,7 @@ rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
         kp.blockDim = dim3(32);
         kp.kernelParams = initArgs;
         cudaGraphNode_t initNode;
-        e = cudaGraphAddKernelNode(&initNode, graph, nullptr, 0, &kp);
+        e = cudaGraphAddKernelNode(&initNode, graph, proNode ? &proNode : nullptr, proNode ? 1 : 0, &kp);
         if (e != cudaSuccess) { fail(e, "cudaGraphAddKernelNode(init)"); break; }
         // conditional while node after it
         cudaGraphNodeParams cp = {};
@@ -86,9 +145,6 @@ rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
         if (e != cudaSuccess) { fail(e, "cudaGraphAddNode(while)"); break; }
         body = cp.conditional.phGraph_out[0];
         // the round's kernels and the control kernel, captured into the body
-        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (e != cudaSuccess) { fail(e, "cudaStreamCreate"); break; }
-        ctx->timing = false;  // event records may not sit inside a conditional body
         e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) { fail(e, "cudaStreamBeginCaptureToGraph"); break; }
         const unsigned long long c0 = g_launches.load();
@@ -116,14 +172,24 @@ rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
         ctx->pending = false;
         if (rounds) *rounds = res[0];
         if (forwarded) *forwarded = res[1];
-        // launches: the init kernel, then the captured body once per round
+        // launches: the prologue and the init kernel, then the body once per round
         g_launches.store(launches0);
-        count_launch(1ull + bodyLaunches * res[0]);
+        count_launch(onceLaunches + bodyLaunches * res[0]);
+        if (key) {
+            ctx->loopExec = exec;
+            ctx->loopGraph = graph;
+            ctx->loopKey = k;
+            ctx->loopLaunchesPerRound = bodyLaunches;
+            ctx->loopLaunchesOnce = onceLaunches;
+            exec = nullptr;
+            graph = nullptr;
+        }
     } while (0);
     ctx->timing = timing;
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap) cudaStreamDestroy(cap);
+    if (st != RF_OK) g_launches.store(launches0);
     return st;
 }
 

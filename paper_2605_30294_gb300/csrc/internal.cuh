@@ -7,6 +7,7 @@
 
 #include <atomic>
 #include <functional>
+#include <string>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -69,6 +70,10 @@ struct rf_ctx {
 
     void *roundsScratch = nullptr;  // lazily allocated scratch of the persistent round kernel
     void *loopState = nullptr;      // lazily allocated: rounds / forwarded / limit of the graph loop
+    void *loopExec = nullptr;       // a kept graph loop (cudaGraphExec_t) and its graph, with its key
+    void *loopGraph = nullptr;
+    std::string loopKey;
+    unsigned long long loopLaunchesPerRound = 0, loopLaunchesOnce = 0;
     size_t roundsScratchBytes = 0;
 
     uint32_t *zipfThr = nullptr;  // numRanks words: Zipf table of the microbenchmark
@@ -134,8 +139,16 @@ rf_status ensure_tile_hist(rf_ctx *ctx);
 // host round trip, while the exchange reports active items and fewer than
 // maxRounds rounds have run.  Starts from the context's last exchange (which
 // must be enqueued on s before); waits for s.  *rounds, *forwarded (host).
+// prologue (may be empty) enqueues the kernels that seed the queue and its
+// first exchange; they run in the graph before the loop.  With a key, the
+// instantiated graph is kept in the context and relaunched while the key
+// (every pointer and value the captured kernels take) is unchanged.
 rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
-                         const std::function<rf_status(cudaStream_t)> &round, uint64_t *rounds, uint64_t *forwarded);
+                         const std::function<rf_status(cudaStream_t)> &round, uint64_t *rounds, uint64_t *forwarded,
+                         const std::function<rf_status(cudaStream_t)> &prologue = {}, const void *key = nullptr,
+                         size_t keyBytes = 0);
+// Release a kept graph loop (before the context's buffers change or go).
+void drop_graph_loop(rf_ctx *ctx);
 
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);

@@ -97,6 +97,7 @@ _SIGS = {
     "rf_c0_raygen": [_P, _P, _i32, _i32, _i32, _i32, _P, _P],
     "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
     "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
+    "rf_c0_render_graph": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
     "rf_create_with_buffers": [_i32, _u32, _u64, _P, _P, _P, _P],
     "rf_get_exchange_config": [_P, _P],
     "rf_set_exchange_config": [_P, _P],
@@ -316,6 +317,18 @@ def rf_c0_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: 
     _check("rf_c0_render", lib().rf_c0_render(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height,
                                               ptr(image), ptr(hop_log), max_hops, ptr(hop_count), max_rounds,
                                               stream_handle(stream), ctypes.byref(rounds)))
+    return rounds.value
+
+
+def rf_c0_render_graph(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, image, hop_log=None,
+                       max_hops: int = 0, hop_count=None, max_rounds: int = 64, stream=None) -> int:
+    """rf_c0_render with the rounds in a kept CUDA graph (conditional while node)."""
+    c = _cam(cam)
+    rounds = ctypes.c_uint64()
+    _check("rf_c0_render_graph", lib().rf_c0_render_graph(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width,
+                                                          height, ptr(image), ptr(hop_log), max_hops,
+                                                          ptr(hop_count), max_rounds, stream_handle(stream),
+                                                          ctypes.byref(rounds)))
     return rounds.value
 
 

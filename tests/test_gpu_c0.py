@@ -111,3 +111,37 @@ def test_raygen_then_manual_rounds():
     torch.cuda.synchronize()
     assert rounds == ref["rounds"]
     np.testing.assert_array_equal(image.cpu().numpy(), ref["T"])
+
+
+def test_graph_form_matches_host_loop_and_is_relaunched():
+    # the rounds in a kept CUDA graph (conditional while node) give the host
+    # loop's image bit for bit, also when the kept graph is relaunched and
+    # after an argument change rebuilds it
+    n, w, h, brick = 64, 128, 128, 32
+    vol = inputs.c0_volume(n)
+    cam = inputs.c0_camera(n, w, h)
+    want = render(vol, cam, n, brick, w, h)
+    s = stream()
+    bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device=dev())
+    rafi.rf_c0_make_bricks(to_dev(vol.reshape(-1)), n, brick, bricks, s)
+    image = torch.zeros(w * h, dtype=torch.float32, device=dev())
+    hop_log = torch.full((w * h, 16), -1, dtype=torch.int32, device=dev())
+    hop_count = torch.zeros(w * h, dtype=torch.int32, device=dev())
+    with rafi.Context(8, RAY_BYTES, w * h) as ctx:
+        for rep in range(3):
+            image.fill_(-1.0)
+            hop_log.fill_(-1)
+            rounds = rafi.rf_c0_render_graph(ctx.handle, bricks, cam, n, brick, w, h, image, hop_log, 16, hop_count,
+                                             stream=s)
+            torch.cuda.synchronize()
+            assert rounds == want["rounds"]
+            np.testing.assert_array_equal(image.cpu().numpy().view(np.uint32), want["T"].view(np.uint32))
+            np.testing.assert_array_equal(hop_log.cpu().numpy(), want["hops"])
+        # another camera: the kept graph is rebuilt
+        cam2 = inputs.camera((32.0, 90.0, -40.0), (32.0, 32.0, 32.0), (0.0, 1.0, 0.0), 40.0, w, h)
+        want2 = render(vol, cam2, n, brick, w, h)
+        rounds = rafi.rf_c0_render_graph(ctx.handle, bricks, cam2, n, brick, w, h, image, hop_log, 16, hop_count,
+                                         stream=s)
+        torch.cuda.synchronize()
+        assert rounds == want2["rounds"]
+        np.testing.assert_array_equal(image.cpu().numpy().view(np.uint32), want2["T"].view(np.uint32))
