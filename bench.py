@@ -479,7 +479,10 @@ def run_ours(args):
             if per_mode is not None:
                 ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 ev[0].record(s)
-            if batched:
+            if batched == "graph":
+                st, cnt, rounds, f = rafi.rf_c1_run_graph(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired,
+                                                          stream=s)
+            elif batched:
                 st, cnt, rounds, f = rafi.rf_c1_run_batched(ctx.handle, d_items, n, SEED, mode, 1.1, GRID, retired,
                                                             stream=s, round_log=round_log,
                                                             round_log_cap=LOG_CAP if round_log is not None else 0,
@@ -538,6 +541,10 @@ def run_ours(args):
     step(True, fuse=False)
     u_fwd, u_ms, tu, _, _ = timed(True, p_steps, fuse=False)
     laws_in_place = timed.laws
+    # the host loop's rounds in a CUDA graph (conditional while node)
+    step("graph")
+    g_fwd, g_ms, _, g_launches, _ = timed("graph", p_steps)
+    laws_graph = timed.laws
 
     # per-round phase rates of the persistent kernel (one extra, untimed step)
     step(True, round_log=log)
@@ -625,6 +632,10 @@ def run_ours(args):
             "form": "persistent kernel; each round steps every item in its queue slot, then scatters",
             "roofline": {"achieved": u_ach, "frac": u_ach / peak,
                          "alg_bytes": "2 x 64 B per queued item for the step pass, 2 x 64 B per delivery"}},
+        "graph_loop": {"value": g_fwd / (g_ms / 1e3), "ms_per_step": g_ms / p_steps, "steps": p_steps,
+                       "per_law": laws_graph, "gpu_launches": g_launches,
+                       "form": "the host loop's kernels captured once into a CUDA graph whose conditional "
+                               "while node repeats them on the device"},
         "plain": {"value": p_fwd / (p_ms / 1e3), "ms_per_step": p_ms / p_steps, "steps": p_steps,
                   "form": "host loop: work kernel + count/scan/scatter/wrap-up kernels + one sync per round",
                   "roofline_scatter": {"achieved": p_ach, "frac": p_ach / peak,

@@ -282,6 +282,16 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
                     int32_t deterministic, int32_t hostMemory, uint32_t maxRounds, void *stream,
                     uint64_t *rounds, uint64_t *forwarded);
 
+/* rf_c1_run (device buffers) with the rounds in a CUDA graph: the seed and
+ * its exchange, then a conditional while node repeating { work kernel;
+ * exchange } on the device while items are active (the hop of each round
+ * read from the device), with no host round trip per round.  Results and
+ * errors as rf_c1_run. */
+rf_status rf_c1_run_graph(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
+                          int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,
+                          int32_t deterministic, uint32_t maxRounds, void *stream, uint64_t *rounds,
+                          uint64_t *forwarded);
+
 /* Batched form of rf_c1_run: the seed as in rf_c1_run, then every work
  * round and exchange inside one persistent cooperative kernel, so no round
  * needs the host.  Per round: destination counts per CTA range, bounded grid

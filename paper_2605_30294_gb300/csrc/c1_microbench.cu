@@ -34,6 +34,7 @@ struct WorkArgs {
     unsigned long long retiredCap;
     uint32_t seed, hop;
     int32_t mode, gx, gy, gz;
+    const unsigned long long *hopPtr;  // nullable: the hop (round) comes from the device (graph loop)
 };
 
 // Neighbour k of rank src on the gx x gy x gz torus (rank = x + gx (y + gy z)):
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
         for (int e = threadIdx.x; e < R - 1; e += kBlock) sThr[e] = a.zipfThr[e];
     __syncthreads();
     const uint32_t n = sOff[R];
+    const uint32_t hop = a.hopPtr ? (uint32_t)*a.hopPtr : a.hop;
     if (DET && blockIdx.x == 0 && threadIdx.x == 0) *a.q.outCount = n;
 
     const uint4 *inq = static_cast<const uint4 *>(a.q.in);
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
             w1 = __ldg(p + 1);
             w2 = __ldg(p + 2);
             w3 = __ldg(p + 3);
-            const uint4 r = philox4x32_10(make_uint4(w0.x, w0.y, w3.w, a.hop), make_uint2(a.seed, 1u));
+            const uint4 r = philox4x32_10(make_uint4(w0.x, w0.y, w3.w, hop), make_uint2(a.seed, 1u));
             if (r.x < kRetire) {
                 retire = true;
             } else {
@@ -298,6 +300,38 @@ rf_status rf_c1_seed(rf_ctx *ctx, const void *items, uint64_t n, void *stream)
     return RF_OK;
 }
 
+namespace rfi {
+namespace {
+rf_status launch_c1_work(rf_ctx *ctx, uint32_t seed, uint32_t hop, const unsigned long long *hopPtr, int32_t mode,
+                         int32_t gx, int32_t gy, int32_t gz, void *retired, unsigned long long *retiredCount,
+                         uint64_t retiredCapacity, int32_t deterministic, cudaStream_t s)
+{
+    WorkArgs a;
+    rf_get_device_queues(ctx, &a.q);
+    a.zipfThr = ctx->zipfThr;
+    a.retired = static_cast<uint4 *>(retired);
+    a.retiredCount = retiredCount;
+    a.retiredCap = retiredCapacity;
+    a.seed = seed;
+    a.hop = hop;
+    a.hopPtr = hopPtr;
+    a.mode = mode;
+    a.gx = gx;
+    a.gy = gy;
+    a.gz = gz;
+    // the incoming count is only known on the device: size the grid for the
+    // capacity, up to 8 resident blocks per SM, and loop
+    const int grid = grid_for(ctx, ctx->capacity, 8);
+    time_begin(ctx, kTimeWork, s);
+    if (deterministic) work_kernel<true><<<grid, kBlock, 0, s>>>(a);
+    else work_kernel<false><<<grid, kBlock, 0, s>>>(a);
+    RF_LAUNCHED("work_kernel");
+    time_end(ctx, kTimeWork, s);
+    return RF_OK;
+}
+}  // namespace
+}  // namespace rfi
+
 rf_status rf_c1_work(rf_ctx *ctx, uint32_t seed, uint32_t hop, int32_t mode, double zipfS, int32_t gx, int32_t gy,
                      int32_t gz, void *retired, unsigned long long *retiredCount, uint64_t retiredCapacity,
                      int32_t deterministic, void *stream)
@@ -314,28 +348,8 @@ rf_status rf_c1_work(rf_ctx *ctx, uint32_t seed, uint32_t hop, int32_t mode, dou
     DeviceGuard g(ctx->device);
     if (mode == RF_C1_ZIPF)
         if (rf_status st = ensure_zipf(ctx, zipfS)) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    WorkArgs a;
-    rf_get_device_queues(ctx, &a.q);
-    a.zipfThr = ctx->zipfThr;
-    a.retired = static_cast<uint4 *>(retired);
-    a.retiredCount = retiredCount;
-    a.retiredCap = retiredCapacity;
-    a.seed = seed;
-    a.hop = hop;
-    a.mode = mode;
-    a.gx = gx;
-    a.gy = gy;
-    a.gz = gz;
-    // the incoming count is only known on the device: size the grid for the
-    // capacity, up to 8 resident blocks per SM, and loop
-    const int grid = grid_for(ctx, ctx->capacity, 8);
-    time_begin(ctx, kTimeWork, s);
-    if (deterministic) work_kernel<true><<<grid, kBlock, 0, s>>>(a);
-    else work_kernel<false><<<grid, kBlock, 0, s>>>(a);
-    RF_LAUNCHED("work_kernel");
-    time_end(ctx, kTimeWork, s);
-    return RF_OK;
+    return launch_c1_work(ctx, seed, hop, nullptr, mode, gx, gy, gz, retired, retiredCount, retiredCapacity,
+                          deterministic, static_cast<cudaStream_t>(stream));
 }
 
 rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
@@ -396,6 +410,57 @@ rf_status rf_c1_run(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, i
     if (rounds) *rounds = r;
     if (forwarded) *forwarded = fwd;
     return st == RF_ERR_MAX_ROUNDS ? st : RF_OK;
+}
+
+rf_status rf_c1_run_graph(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode, double zipfS,
+                          int32_t gx, int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountOut,
+                          int32_t deterministic, uint32_t maxRounds, void *stream, uint64_t *rounds,
+                          uint64_t *forwarded)
+{
+    if (rf_status st = check_c1(ctx, "rf_c1_run_graph")) return st;
+    if (n > ctx->capacity || (n && (!items || !retired)) || !retiredCountOut || mode < RF_C1_UNIFORM ||
+        mode > RF_C1_NBR6) {
+        set_error("rf_c1_run_graph: n %llu above capacity, NULL buffer or bad mode", (unsigned long long)n);
+        return RF_ERR_ARG;
+    }
+    if (mode == RF_C1_NBR6 && (gx < 1 || gy < 1 || gz < 1 || gx * gy * gz != ctx->numRanks)) {
+        set_error("rf_c1_run_graph: torus %dx%dx%d does not have %d ranks", gx, gy, gz, ctx->numRanks);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (mode == RF_C1_ZIPF)
+        if (rf_status st = ensure_zipf(ctx, zipfS)) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    RF_CUDA(cudaMemsetAsync(ctx->stagingCount, 0, sizeof(unsigned long long), s));
+    // the loop state's first word counts finished rounds: the hop of the next
+    if (!ctx->loopState) RF_CUDA(cudaMalloc(&ctx->loopState, 3 * sizeof(unsigned long long)));
+    const unsigned long long *hopPtr = static_cast<const unsigned long long *>(ctx->loopState);
+    uint64_t r = 0, fwd = 0;
+    rf_status st = run_graph_loop(
+        ctx, s, maxRounds,
+        [&](cudaStream_t cs) -> rf_status {
+            if (rf_status ws = launch_c1_work(ctx, seed, 0u, hopPtr, mode, gx, gy, gz, retired, ctx->stagingCount, n,
+                                              deterministic, cs))
+                return ws;
+            return launch_exchange(ctx, cs);
+        },
+        &r, &fwd,
+        [&](cudaStream_t cs) -> rf_status {
+            if (rf_status ss = rf_c1_seed(ctx, items, n, cs)) return ss;
+            return launch_exchange(ctx, cs);
+        });
+    if (st != RF_OK) return st;
+    unsigned long long cnt = 0;
+    RF_CUDA(cudaMemcpy(&cnt, ctx->stagingCount, sizeof cnt, cudaMemcpyDeviceToHost));
+    *retiredCountOut = cnt;
+    if (rounds) *rounds = r;
+    if (forwarded) *forwarded = fwd;
+    if (ctx->host->numActive) {
+        set_error("rf_c1_run_graph: %llu items still active after %u rounds", (unsigned long long)ctx->host->numActive,
+                  maxRounds);
+        return RF_ERR_MAX_ROUNDS;
+    }
+    return RF_OK;
 }
 
 }  // extern "C"

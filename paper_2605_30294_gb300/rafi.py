@@ -99,6 +99,7 @@ _SIGS = {
     "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
     "rf_c0_render_graph": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
     "rf_create_with_buffers": [_i32, _u32, _u64, _P, _P, _P, _P],
+    "rf_c1_run_graph": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _u32, _P, _PU64, _PU64],
     "rf_get_exchange_config": [_P, _P],
     "rf_set_exchange_config": [_P, _P],
     "rf_tune_exchange": [_P, _P, _u32, _P, _P],
@@ -495,3 +496,15 @@ def rf_create_with_buffers(num_ranks: int, item_bytes: int, capacity: int, in_qu
     _check("rf_create_with_buffers", lib().rf_create_with_buffers(num_ranks, item_bytes, capacity, ptr(in_queue),
                                                                   ptr(out_queue), ptr(dest), ctypes.byref(h)))
     return h.value
+
+
+def rf_c1_run_graph(ctx: int, items, n: int, seed: int, mode: int, zipf_s: float, grid, retired,
+                    deterministic: bool = True, max_rounds: int = 100000, stream=None, allow=()):
+    """Microbenchmark with the rounds in a CUDA graph; returns (status, retired_count, rounds, forwarded)."""
+    gx, gy, gz = grid
+    cnt, rounds, fwd = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    st = lib().rf_c1_run_graph(ctx, ptr(items), n, seed, mode, zipf_s, gx, gy, gz, ptr(retired), ctypes.byref(cnt),
+                               int(deterministic), max_rounds, stream_handle(stream), ctypes.byref(rounds),
+                               ctypes.byref(fwd))
+    _check("rf_c1_run_graph", st, allow)
+    return st, cnt.value, rounds.value, fwd.value

@@ -258,6 +258,40 @@ def test_batched_pinned_host_buffers(fuse):
             np.testing.assert_array_equal(h_ret.numpy(), d_ret.cpu().numpy())
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("deterministic", [True, False])
+def test_graph_form(mode, deterministic):
+    # the host loop's rounds inside a CUDA graph: same rounds and forwards, the
+    # oracle's final payloads; stopping after k rounds leaves round k's queue
+    n, seed = 20011, 13
+    items = inputs.c1_items(n, seed=seed)
+    final, hops, _, _ = oracle.c1_walk(items, R, seed, mode, grid=GRID)
+    s = stream()
+    retired = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+    with rafi.Context(R, 64, n) as ctx:
+        st, cnt, rounds, fwd = rafi.rf_c1_run_graph(ctx.handle, to_dev(items), n, seed, mode, 1.1, GRID, retired,
+                                                    deterministic, stream=s)
+        assert st == rafi.RF_OK and cnt == n
+        assert rounds == int(hops.max()) + 1 and fwd == int(hops.sum())
+        got = retired[:cnt].cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
+        k = 4
+        want = oracle.c1_rounds(items, R, seed, mode, grid=GRID, dump_round=k)
+        st, cnt, rounds, fwd = rafi.rf_c1_run_graph(ctx.handle, to_dev(items), n, seed, mode, 1.1, GRID, retired,
+                                                    deterministic, max_rounds=k, stream=s,
+                                                    allow=(rafi.RF_ERR_MAX_ROUNDS,))
+        assert st == rafi.RF_ERR_MAX_ROUNDS and rounds == k
+        assert rafi.rf_num_active(ctx.handle) == int(want["active"][k])
+        q, off = _queue(ctx, n, s)
+        np.testing.assert_array_equal(off.astype(np.uint64), want["dump_offsets"])
+        if deterministic:
+            np.testing.assert_array_equal(q, want["dump_items"])
+        else:
+            for r in range(R):
+                np.testing.assert_array_equal(canonical_rows(q[off[r]:off[r + 1]]),
+                                              canonical_rows(want["dump_items"][off[r]:off[r + 1]]))
+
+
 def test_batched_full_size_matches_plain():
     n, seed = 1 << 24, 1
     items = inputs.c1_items(n, seed=seed)
