@@ -12,7 +12,8 @@
 // adjoint ray carries the final C of its forward ray and dL/dC; walking the
 // same bricks it recomputes T_k and the running sum segment by segment (no
 // stored history, no division by 1 - alpha) and scatters dL/dC * dC/dsigma_k
-// with the trilinear weights into the gradient grid (atomic adds).
+// with the trilinear weights into the gradient grid (atomic adds, summed per
+// ray over consecutive samples that share their eight corners).
 //
 // Built with -fmad=false (the written float order, as the oracle's).
 #include "internal.cuh"
@@ -105,16 +106,49 @@ __device__ __forceinline__ float sigma_at(const float *__restrict__ brick, int32
     return c0 * gz + c1 * t.f[2];
 }
 
-__device__ __forceinline__ void scatter_grad(float *grad, int32_t N, const Taps &t, float gs)
+// Per-ray gradient accumulator: consecutive samples of a ray (half a voxel
+// apart) mostly share their eight trilinear corners, so their weighted
+// gradients are summed in registers while the corners stay the same and
+// added to the grid (atomic adds) when they change or the ray leaves.
+struct GradAcc {
+    int32_t g0[3], g1[3];
+    float v[8];
+    bool any;
+};
+
+__device__ __forceinline__ void grad_flush(float *grad, int32_t N, GradAcc &A)
 {
+    if (!A.any) return;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int32_t ix = (c & 1) ? A.g1[0] : A.g0[0];
+        const int32_t iy = (c & 2) ? A.g1[1] : A.g0[1];
+        const int32_t iz = (c & 4) ? A.g1[2] : A.g0[2];
+        if (A.v[c] != 0.0f) atomicAdd(grad + ((size_t)iz * N + iy) * N + ix, A.v[c]);
+    }
+    A.any = false;
+}
+
+__device__ __forceinline__ void grad_add(float *grad, int32_t N, GradAcc &A, const Taps &t, float gs)
+{
+    const bool same = A.any && A.g0[0] == t.g0[0] && A.g0[1] == t.g0[1] && A.g0[2] == t.g0[2] &&
+                      A.g1[0] == t.g1[0] && A.g1[1] == t.g1[1] && A.g1[2] == t.g1[2];
+    if (!same) {
+        grad_flush(grad, N, A);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            A.g0[a] = t.g0[a];
+            A.g1[a] = t.g1[a];
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) A.v[c] = 0.0f;
+        A.any = true;
+    }
     const float gx = 1.0f - t.f[0], gy = 1.0f - t.f[1], gz = 1.0f - t.f[2];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const int32_t ix = (c & 1) ? t.g1[0] : t.g0[0];
-        const int32_t iy = (c & 2) ? t.g1[1] : t.g0[1];
-        const int32_t iz = (c & 4) ? t.g1[2] : t.g0[2];
         const float w = ((c & 1) ? t.f[0] : gx) * ((c & 2) ? t.f[1] : gy) * ((c & 4) ? t.f[2] : gz);
-        atomicAdd(grad + ((size_t)iz * N + iy) * N + ix, gs * w);
+        A.v[c] = A.v[c] + gs * w;
     }
 }
 
@@ -193,15 +227,19 @@ __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_que
         const float *brick = P.bricks + (size_t)rank * S * S * S;
         int32_t k = (int32_t)r.k;
         float T = r.T, acc = r.acc;
+        GradAcc ga;
+        ga.any = false;
         for (;;) {
             const float tk = r.t0 + ((float)k + 0.5f) * 0.5f;
             if (!(tk < r.t1)) {
                 if (!ADJ) P.rayC[r.id] = acc;
+                if (ADJ) grad_flush(P.grad, P.N, ga);
                 break;
             }
             const float px = r.ox + r.dx * tk, py = r.oy + r.dy * tk, pz = r.oz + r.dz * tk;
             const int32_t own = owner_of(px, py, pz, P.B, P.nb);
             if (own != rank) {
+                if (ADJ) grad_flush(P.grad, P.N, ga);
                 r.k = (float)k;
                 r.T = T;
                 r.acc = acc;
@@ -219,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_que
             if (ADJ) {
                 const float suffix = r.cfin - acc;  // sum over later samples
                 const float dC = T * ((0.5f * e) * cc + al * 20.0f) - 0.5f * suffix;
-                scatter_grad(P.grad, P.N, tp, r.g * dC);
+                grad_add(P.grad, P.N, ga, tp, r.g * dC);
             }
             T = T * e;
             ++k;
