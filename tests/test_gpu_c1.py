@@ -292,6 +292,32 @@ def test_graph_form(mode, deterministic):
                                               canonical_rows(want["dump_items"][off[r]:off[r + 1]]))
 
 
+@pytest.mark.parametrize("fuse", [True, False], ids=["step_on_arrival", "step_in_place"])
+@pytest.mark.parametrize("ranks,grid,n", [(1, (1, 1, 1), 5000), (1024, (8, 8, 16), 300007), (64, (4, 4, 4), 0),
+                                          (64, (4, 4, 4), 17)],
+                         ids=["one_rank", "max_ranks", "empty", "ragged"])
+def test_batched_rank_count_extremes_and_empty(fuse, ranks, grid, n):
+    # one rank (every item forwarded to itself), the maximum rank count (1025
+    # destination digits: the per-CTA counts no longer fit one staging pass),
+    # an empty run and a run smaller than one tile
+    seed = 14
+    items = inputs.c1_items(max(n, 1), seed=seed)[:n]
+    s = stream()
+    retired = torch.zeros((max(n, 1), 16), dtype=torch.int32, device=dev())
+    with rafi.Context(ranks, 64, max(n, 1)) as ctx:
+        for mode in MODES:
+            st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, to_dev(items) if n else retired, n, seed, mode,
+                                                          1.1, grid, retired, stream=s, step_on_arrival=fuse)
+            assert st == rafi.RF_OK and cnt == n
+            if n == 0:
+                assert rounds == 0 and fwd == 0 and rafi.rf_num_active(ctx.handle) == 0
+                continue
+            final, hops, _, _ = oracle.c1_walk(items, ranks, seed, mode, grid=grid)
+            assert rounds == int(hops.max()) + 1 and fwd == int(hops.sum())
+            got = retired[:cnt].cpu().numpy().view(np.uint32)
+            np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
+
+
 def test_batched_full_size_matches_plain():
     n, seed = 1 << 24, 1
     items = inputs.c1_items(n, seed=seed)
