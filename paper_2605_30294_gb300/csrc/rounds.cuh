@@ -203,6 +203,47 @@ __device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned 
     return *sFlag != 0;
 }
 
+// The flat barrier in two halves, so a CTA can do work that needs no other
+// CTA between arriving and waiting: grid_arrive (all threads; thread 0 adds
+// to the counter, its earlier writes released) returns whether this CTA
+// arrived last; grid_wait (all threads) waits for the rest, bounded, and
+// returns false when any CTA has given up.
+__device__ inline void grid_arrive(GridSync *gs, unsigned int seq, unsigned int *sLast)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *sLast = atom_add_release(&gs->count, 1u) + 1u == gridDim.x * (seq + 1u) ? 1u : 0u;
+}
+
+__device__ inline bool grid_wait(GridSync *gs, unsigned int *sFlag, unsigned int seq, const unsigned int *sLast)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int ok = 1;
+        const unsigned int target = gridDim.x * (seq + 1u);
+        if (!*sLast) {
+            const long long t0 = clock64();
+            for (unsigned int k = 0; ld_acquire(&gs->count) < target; ++k) {
+                if ((k & 15u) == 15u) {
+                    if (ld_acquire(&gs->abort)) {
+                        ok = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > kSpinLimitCycles) {
+                        atomicExch(&gs->abort, 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(20);
+            }
+        }
+        if (ld_acquire(&gs->abort)) ok = 0;
+        *sFlag = ok;
+    }
+    __syncthreads();
+    return *sFlag != 0;
+}
+
 // Exclusive block scan of v[0..n) in shared memory (n <= 8 * kRoundsBlock).
 __device__ inline uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
 {
@@ -516,10 +557,10 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     // dBase[d] = dStart[d] for ranks and the retired count so far for R.
     // Returns the number of valid items.  All threads; ends with a barrier.
     // carryPrev: first add the previous tile's counts (still in dCnt) to dBase.
-    auto rank_tile = [&](uint4 *sItems, int32_t *dts, uint32_t cnt, bool doFuse, uint32_t qs,
-                         bool ownBases, bool carryPrev) -> uint32_t {
-        int myD[kK];
-        uint32_t myR[kK];
+    // First half (needs no other CTA): per-warp ranks (myD, myR, wc) and the
+    // fused step; second half: per-tile counts, slots and positions.
+    auto rank_a = [&](uint4 *sItems, int32_t *dts, uint32_t cnt, bool doFuse, uint32_t qs, int (&myD)[kK],
+                      uint32_t (&myR)[kK]) {
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
             const uint32_t idx = (uint32_t)(warp * 32 * kK + k * 32 + lane);
@@ -554,6 +595,8 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         }
         if (doFuse) fence_proxy_async_smem();  // generic writes before the buffer's next bulk load
         __syncthreads();
+    };
+    auto rank_b = [&](bool ownBases, bool carryPrev, const int (&myD)[kK], const uint32_t (&myR)[kK]) -> uint32_t {
         for (int e = tid; e < D; e += kRoundsBlock) {
             uint32_t sum = 0;
 #pragma unroll
@@ -584,6 +627,13 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         }
         __syncthreads();
         return nValid;
+    };
+    auto rank_tile = [&](uint4 *sItems, int32_t *dts, uint32_t cnt, bool doFuse, uint32_t qs, bool ownBases,
+                         bool carryPrev) -> uint32_t {
+        int myD[kK];
+        uint32_t myR[kK];
+        rank_a(sItems, dts, cnt, doFuse, qs, myD, myR);
+        return rank_b(ownBases, carryPrev, myD, myR);
     };
 
     for (;; ++it) {
@@ -830,7 +880,29 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             }
         }
         fence_proxy_async_global();
-        if (failed || !round_barrier()) {
+        if (failed) break;
+        // With the first tile staged early, its per-warp ranks and fused step
+        // (the half that needs no other CTA) run between arriving at the
+        // first barrier and waiting for it.
+        int myD0[kK];
+        uint32_t myR0[kK];
+        bool earlyDone = false;
+        if (kFlatBarrier && !solo && prefetched) {
+            grid_arrive(a.sync, barrierSeq, sFlag + 1);
+            for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
+            __syncwarp();
+            if (!wait(0)) {
+                failed = true;
+            } else {
+                rank_a(sBuf, sDst, min(kTile, hi - lo), fuse, q, myD0, myR0);
+                earlyDone = true;
+            }
+            const bool ok = grid_wait(a.sync, sFlag, barrierSeq++, sFlag + 1);
+            if (failed || !ok) {
+                failed = true;
+                break;
+            }
+        } else if (!round_barrier()) {
             failed = true;
             break;
         }
@@ -910,14 +982,19 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             const uint32_t b = lo + t * kTile;
             const uint32_t cnt = min(kTile, hi - b);
             if (tid == 0 && t + 1 < nt) issue3(buf ^ 1, b + kTile);
-            for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
-            if (!wait(buf)) {
-                failed = true;
-                break;
-            }
             int32_t *dts = sDst + buf * (kTile + 4u);
             uint4 *sItems = sBuf + buf * kTileVecs;
-            const uint32_t nValid = rank_tile(sItems, dts, cnt, fuse, q, false, t > 0);
+            uint32_t nValid;
+            if (t == 0 && earlyDone) {
+                nValid = rank_b(false, false, myD0, myR0);
+            } else {
+                for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
+                if (!wait(buf)) {
+                    failed = true;
+                    break;
+                }
+                nValid = rank_tile(sItems, dts, cnt, fuse, q, false, t > 0);
+            }
             // consecutive threads write consecutive 16-byte vectors of the
             // destination-grouped tile (coalesced runs per destination)
             const uint32_t total = nValid * V;
