@@ -18,17 +18,20 @@ workload; particle-steps/s of the streamline workload (512^3 field, 16
 uneven seed sets in one launch, batched and plain forms); rays/s of the
 differentiable renderer (forward and adjoint) and paths/s of the delta-tracking
 transport (1024^3, 512 ranks, four views at 16 spp); the oracle timed
-on a bounded sample (cpu_baseline); SM clocks sampled during the timed
-region and the number of kernels launched.
+on the host (cpu_baseline, one GPU only): single-threaded on a bounded
+sample, on all host threads over the whole microbenchmark, and on subsets
+of the streamline and transport workloads; SM clocks sampled during the
+timed region and the number of kernels launched.
 
 ``--impl reference`` times the oracle (the CPU reference of this method) on a
-bounded sample of the same workload instead.
+bounded sample of the same workload instead, on all host threads.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -51,8 +54,10 @@ LAW_NAMES = {0: "uniform", 1: "zipf_1.1", 2: "torus_6"}
 WORKLOAD = ("forwarding microbenchmark: 2^24 x 64-byte items (Philox payloads), 64 logical ranks, "
             "destinations uniform / Zipf s=1.1 / 6-neighbour 4x4x4 torus, retire p=0.1, seed 1; "
             "one step = the three runs, each seeded and run to zero active items")
-SAMPLE_ITEMS = 1 << 18  # oracle sample per destination law, per reference-arm step
-BASELINE_ITEMS = 1 << 22  # oracle sample per destination law for cpu_baseline (about 10 s)
+SAMPLE_ITEMS = 1 << 21  # oracle sample per destination law, per reference-arm step (all host threads)
+BASELINE_ITEMS = 1 << 22  # single-thread oracle sample per destination law for cpu_baseline (about 5 s)
+C2_ORACLE_SEEDS = 1 << 14  # streamline seeds the oracle traces for cpu_baseline
+C4_ORACLE_CROP = 64  # 64 x 64 pixel crop of the first view the oracle renders for cpu_baseline
 
 
 def peaks():
@@ -133,26 +138,122 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_sample_step(sample_items):
+def host_threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            lines = f.read().splitlines()
+    except OSError:
+        lines = []
+    for key in ("model name", "CPU part"):
+        for ln in lines:
+            if ln.startswith(key) and ":" in ln:
+                v = ln.split(":", 1)[1].strip()
+                return v if key == "model name" else f"{platform.machine()}, CPU part {v}"
+    return platform.machine()
+
+
+def on_threads(fn, shards, threads):
+    """fn over independent shards on `threads` host threads (the oracle's C calls
+    release the GIL, so the shards run in parallel)."""
+    if threads <= 1 or len(shards) <= 1:
+        return [fn(x) for x in shards]
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(fn, shards))
+
+
+def oracle_sample_step(sample_items, threads=1):
+    """Forwarded items of the three runs over sample_items.  With threads > 1 the
+    items are split into contiguous shards of whole multiples of the rank count
+    (item i keeps its start rank i mod 64); every item's hops depend on its own
+    payload only, so the shards' forwarded counts add up to the whole sample's."""
     import oracle
 
-    fwd = 0
-    for mode in MODES:
-        res = oracle.c1_rounds(sample_items, RANKS, SEED, mode, grid=GRID)
-        fwd += int(res["active"][1:].sum())
-    return fwd
+    n = sample_items.shape[0]
+    per = -(-n // max(threads, 1))
+    per = max(RANKS, -(-per // RANKS) * RANKS)
+    shards = [sample_items[a:a + per] for a in range(0, n, per)]
+
+    def one(sh):
+        f = 0
+        for mode in MODES:
+            res = oracle.c1_rounds(sh, RANKS, SEED, mode, grid=GRID)
+            f += int(res["active"][1:].sum())
+        return f
+
+    return sum(on_threads(one, shards, threads))
 
 
-def oracle_baseline(steps=1):
+def oracle_baseline(n=N_ITEMS):
+    """The oracle on the host: single-threaded on 2^22 items per law (the parity
+    oracle as it is), and on all host threads over the bench's n items per law."""
     from paper_2605_30294_gb300 import inputs
 
-    items = inputs.c1_items(BASELINE_ITEMS, seed=SEED)
+    items = inputs.c1_items(n, seed=SEED)
     t0 = time.perf_counter()
-    fwd = 0
-    for _ in range(steps):
-        fwd += oracle_sample_step(items)
+    fwd1 = oracle_sample_step(items[:BASELINE_ITEMS])
+    dt1 = time.perf_counter() - t0
+    threads = host_threads()
+    t0 = time.perf_counter()
+    fwd = oracle_sample_step(items, threads)
     dt = time.perf_counter() - t0
-    return fwd / dt, fwd, dt
+    return {"value": fwd / dt, "unit": "items/s", "cores": threads, "kind": "oracle",
+            "sample": f"the bench's workload ({n} items per destination law) split into {threads} shards "
+                      f"run round by round through the oracle's queues, one host thread each, {dt:.1f} s",
+            "cpu": cpu_model(),
+            "single_thread": {"value": fwd1 / dt1, "unit": "items/s", "cores": 1,
+                              "sample": f"{BASELINE_ITEMS} items per destination law, {dt1:.1f} s"}}
+
+
+def repeat_for(fn, min_s=1.0):
+    """Runs fn until at least min_s seconds have passed; returns (fn's last result, runs, seconds)."""
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        r = fn()
+        runs += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_s:
+            return r, runs, dt
+
+
+def oracle_c2_subset(field, seeds, brick):
+    """Streamline oracle on every k-th seed (C2_ORACLE_SEEDS of them), all host threads."""
+    import oracle
+
+    stride = max(1, seeds.shape[0] // C2_ORACLE_SEEDS)
+    sub = np.ascontiguousarray(seeds[::stride][:C2_ORACLE_SEEDS])
+    threads = host_threads()
+    shards = np.array_split(sub, threads)
+    steps, runs, dt = repeat_for(lambda: sum(
+        int(r["steps"].astype(np.int64).sum())
+        for r in on_threads(lambda x: oracle.c2_trace(field, x, brick), shards, threads)))
+    return {"particle_steps_per_s": runs * steps / dt, "cores": threads, "kind": "oracle",
+            "sample": f"subset: {sub.shape[0]} of {seeds.shape[0]} seeds (every {stride}th), "
+                      f"{steps} particle-steps per run, {runs} runs in {dt:.1f} s"}
+
+
+def oracle_c4_subset(vol, smax, view, spp):
+    """Transport oracle on a centred crop of one view, all host threads (one band of rows each)."""
+    import oracle
+
+    cam, w, h, base = view
+    c = C4_ORACLE_CROP
+    x0, y0 = w // 2 - c // 2, h // 2 - c // 2
+    threads = host_threads()
+    bands = [(y0 + a[0], len(a)) for a in np.array_split(np.arange(c), threads) if len(a)]
+    _, runs, dt = repeat_for(lambda: on_threads(
+        lambda b: oracle.c4_render_crop(vol, smax, cam, w, base, x0, b[0], c, b[1], spp), bands, threads))
+    return {"paths_per_s": runs * c * c * spp / dt, "cores": threads, "kind": "oracle",
+            "sample": f"subset: the centred {c}x{c} crop of the {w}x{h} view at {spp} spp "
+                      f"({c * c * spp} paths per run), {runs} runs in {dt:.1f} s"}
 
 
 def reduce_over_ranks(dist, device, sec: float, units: int, e2e_s: float, e2e_units: int):
@@ -175,21 +276,23 @@ def run_reference(args):
     from paper_2605_30294_gb300 import inputs
 
     items = inputs.c1_items(SAMPLE_ITEMS, seed=SEED)
+    threads = host_threads()
     for _ in range(args.warmup):
-        oracle_sample_step(items)
+        oracle_sample_step(items, threads)
     t0 = time.perf_counter()
     fwd = 0
     for _ in range(args.steps):
-        fwd += oracle_sample_step(items)
+        fwd += oracle_sample_step(items, threads)
     dt = time.perf_counter() - t0
     v = fwd / dt
     sample = (f"{SAMPLE_ITEMS} of the 2^24 items per destination law (same seed, ranks and laws), "
-              f"run round by round through the oracle's queues")
+              f"run round by round through the oracle's queues in {threads} shards, one host thread each")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "items/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": "items/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "items/s", "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": v, "unit": "items/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -293,7 +396,7 @@ def phase_rates(log_rows, item_bytes, min_items=1 << 20):
     return out
 
 
-def c2_streamlines(torch, rafi, inputs, s, reps=3):
+def c2_streamlines(torch, rafi, inputs, s, reps=3, cpu=None):
     """Streamlines: 512^3 field over 4x4x4 ranks, the 16 uneven seed sets in one launch.
 
     Returns particle-steps/s and items forwarded/s of the batched (persistent)
@@ -344,6 +447,8 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3):
                     "items_forwarded_per_s": fwd / nrep / sec, "rounds": rounds, "particle_steps": steps}
             res[key]["batched_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["batched"]["ms_per_run"]
             res[key]["graph_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["graph"]["ms_per_run"]
+    if cpu is not None:  # the cpu_baseline leg: the oracle on a subset of the seeds
+        cpu["streamlines_subset"] = oracle_c2_subset(field, seeds, brick)
     return res
 
 
@@ -381,7 +486,7 @@ def c3_ea(torch, rafi, inputs, s, reps=5):
     return out
 
 
-def c4_transport(torch, rafi, inputs, s):
+def c4_transport(torch, rafi, inputs, s, cpu=None):
     """Delta tracking: 1024^3 noise (mean optical depth 8) over 8x8x8 ranks, 4 views at 16 spp."""
     n, brick, spp = 1024, 128, 16
     vol, smax = inputs.c4_volume(n)
@@ -389,7 +494,7 @@ def c4_transport(torch, rafi, inputs, s):
     bricks = torch.zeros(512 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
     dv = torch.from_numpy(vol.reshape(-1)).cuda()
     rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
-    del dv, vol
+    del dv
     torch.cuda.empty_cache()
     npix = sum(w * h for _, w, h, _ in views)
     paths = npix * spp
@@ -414,6 +519,8 @@ def c4_transport(torch, rafi, inputs, s):
                                                            "rays_forwarded_per_s": fwd / sec, "rounds": rounds}
     out["batched_over_plain"] = out["plain"]["ms"] / out["batched"]["ms"]
     out["graph_over_plain"] = out["plain"]["ms"] / out["graph"]["ms"]
+    if cpu is not None:  # the cpu_baseline leg: the oracle on a crop of the first view
+        cpu["transport_subset"] = oracle_c4_subset(vol, smax, views[0], spp)
     return out
 
 
@@ -578,11 +685,13 @@ def run_ours(args):
     ctx.close()
     del d_items, retired, h_items, h_ret
     torch.cuda.empty_cache()
-    streamlines = c2_streamlines(torch, rafi, inputs, s) if not args.skip_extra else None
+    # the oracle's timings (cpu_baseline) run at one GPU only
+    cpu_extra = {} if world == 1 else None
+    streamlines = c2_streamlines(torch, rafi, inputs, s, cpu=cpu_extra) if not args.skip_extra else None
     torch.cuda.empty_cache()
     ea = c3_ea(torch, rafi, inputs, s) if not args.skip_extra else None
     torch.cuda.empty_cache()
-    transport = c4_transport(torch, rafi, inputs, s) if not args.skip_extra else None
+    transport = c4_transport(torch, rafi, inputs, s, cpu=cpu_extra) if not args.skip_extra else None
     torch.cuda.empty_cache()
     mp = multi_phase(torch, rafi, inputs, s) if not args.skip_extra else None
 
@@ -609,7 +718,10 @@ def run_ours(args):
                if tp.scatterMsLarge > 0 else 0.0)
     u_ach = (2 * ITEM_BYTES * (tu.roundsLaunches * n + 2 * u_fwd) / (tu.roundsMs * 1e-3) / 1e9
              if tu.roundsMs > 0 else 0.0)
-    cpu_v, cpu_fwd, cpu_dt = oracle_baseline()
+    cpu_line = None
+    if cpu_extra is not None:
+        cpu_line = oracle_baseline(n)
+        cpu_line.update(cpu_extra)
     line = {
         "metric": METRIC, "value": total_fwd / sec, "unit": "items/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -655,9 +767,7 @@ def run_ours(args):
         "differentiable_ea": ea,
         "delta_tracking": transport,
         "multi_phase": mp,
-        "cpu_baseline": {"value": cpu_v, "unit": "items/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{BASELINE_ITEMS} items per destination law, round-by-round oracle, "
-                                   f"{cpu_dt:.1f} s"},
+        "cpu_baseline": cpu_line,
         "clocks": clocks,
         "gpu_launches": launches,
     }

@@ -63,3 +63,48 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_shards_add_up_to_the_whole_sample():
+    """The all-threads CPU baseline splits the items into shards of whole
+    multiples of the rank count: every item keeps its start rank and its hops
+    depend on its own payload only, so the shards' forwarded counts must add
+    up to the single-threaded count (ragged last shard included)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2605_30294_gb300 import inputs
+
+    items = inputs.c1_items(3 * 1024 + 64 * 5, seed=bench.SEED)
+    one = bench.oracle_sample_step(items, 1)
+    assert one > 0
+    for threads in (2, 3, 8):
+        assert bench.oracle_sample_step(items, threads) == one
+
+
+def test_reference_arm_uses_every_host_thread(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import json
+
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(bench, "SAMPLE_ITEMS", 4096)
+
+    class Args:
+        steps, warmup = 1, 0
+
+    assert bench.run_reference(Args()) == 0
+    line = json.loads(capsys.readouterr().out)
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == bench.host_threads()
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_repeat_for_runs_until_the_time_is_spent():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    calls = []
+    r, runs, dt = bench.repeat_for(lambda: calls.append(1) or len(calls), min_s=0.05)
+    assert runs == len(calls) == r and dt >= 0.05
