@@ -777,6 +777,88 @@ def run_ours(args):
     return 0
 
 
+def run_section(args):
+    """One workload kernel's host loop alone, at a size for a profiler capture (a few
+    GB on the device, each workload launched once, no warm-up), printing one JSON
+    line of its own (not the bench line):
+      c2: streamlines, 512^3 field in 4x4x4 bricks, 2^18 seeds, until brick exit;
+      c3: EA renderer at its configured size, one forward and one adjoint render;
+      c4: delta tracking, 512^3 noise in 4x4x4 bricks, one 512x512 view at 16 spp."""
+    import torch
+
+    from paper_2605_30294_gb300 import build, inputs, rafi
+
+    build.build()
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"section": args.section}
+    if args.section == "c2":
+        n, brick, count = 512, 128, 1 << 18
+        R = (n // brick) ** 3
+        field, _ = inputs.c2_field(n)
+        d_field = torch.from_numpy(field.reshape(-1)).cuda()
+        bricks = torch.zeros(R * (brick + 4) ** 3 * 4, dtype=torch.float32, device="cuda")
+        rafi.rf_c2_make_bricks(d_field, n, brick, bricks, s)
+        del d_field
+        d_seeds = torch.from_numpy(inputs.c2_seeds(count, n, seed=2)).cuda()
+        d_sets = torch.zeros(count, dtype=torch.int32, device="cuda")
+        res = torch.zeros((count, 8), dtype=torch.int32, device="cuda")
+        with rafi.Context(R, 32, count) as ctx:
+            e0.record(s)
+            _, rounds, fwd = rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, 0,
+                                            res, 0, stream=s)
+            e1.record(s)
+            torch.cuda.synchronize()
+        steps = int(res[:, 4].cpu().numpy().view(np.uint32).astype(np.int64).sum())
+        out.update(workload=f"512^3 curl-noise field, 4x4x4 ranks, {count} seeds, until brick exit, host loop",
+                   ms=e0.elapsed_time(e1), rounds=rounds, particle_steps=steps,
+                   particle_steps_per_s=steps / (e0.elapsed_time(e1) * 1e-3))
+    elif args.section == "c3":
+        n, brick, w, h, spp = 256, 128, 512, 512, 4
+        vol = inputs.c0_volume(n)
+        cam = inputs.c0_camera(n, w, h)
+        dv = torch.from_numpy(vol.reshape(-1)).cuda()
+        bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+        rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
+        nr = w * h * spp
+        rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
+        img = torch.zeros(w * h, dtype=torch.float32, device="cuda")
+        gimg = torch.ones(w * h, dtype=torch.float32, device="cuda")
+        grad = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+        out["workload"] = "256^3 blob density, 2x2x2 ranks, 512x512 at 4 spp"
+        with rafi.Context(8, 64, nr) as ctx:
+            for name, fn in (("forward", lambda: rafi.rf_c3_render(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
+                                                                    rayC, img, stream=s)),
+                             ("adjoint", lambda: rafi.rf_c3_adjoint(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
+                                                                     rayC, gimg, grad, stream=s))):
+                e0.record(s)
+                fn()
+                e1.record(s)
+                torch.cuda.synchronize()
+                out[name] = {"ms": e0.elapsed_time(e1), "rays_per_s": nr / (e0.elapsed_time(e1) * 1e-3)}
+    else:
+        n, brick, spp = 512, 128, 16
+        R = (n // brick) ** 3
+        vol, smax = inputs.c4_volume(n)
+        views = inputs.c4_views(n, sizes=((512, 512),))
+        bricks = torch.zeros(R * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+        dv = torch.from_numpy(vol.reshape(-1)).cuda()
+        rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
+        del dv
+        paths = 512 * 512 * spp
+        score = torch.zeros(512 * 512, dtype=torch.float32, device="cuda")
+        with rafi.Context(R, 64, paths) as ctx:
+            e0.record(s)
+            rounds, fwd = rafi.rf_c4_render(ctx.handle, bricks, n, brick, smax, views, spp, 4, score, 0, stream=s)
+            e1.record(s)
+            torch.cuda.synchronize()
+        out.update(workload="512^3 noise (mean optical depth 8), 4x4x4 ranks, one 512x512 view at 16 spp, host loop",
+                   ms=e0.elapsed_time(e1), rounds=rounds, paths_per_s=paths / (e0.elapsed_time(e1) * 1e-3))
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -786,9 +868,13 @@ def main():
     ap.add_argument("--items", type=int, default=N_ITEMS)
     ap.add_argument("--skip-extra", action="store_true",
                     help="leave out the streamline, differentiable and transport workloads")
+    ap.add_argument("--section", choices=["c2", "c3", "c4"], default=None,
+                    help="run one workload's host loop alone at a profiling size and print its own JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.section:
+        return run_section(args)
     return run_ours(args)
 
 
