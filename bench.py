@@ -410,7 +410,7 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3, cpu=None):
     seeds = inputs.c2_seeds(count, n, seed=2)
     set_ids = np.repeat(np.arange(len(sizes), dtype=np.uint32), sizes)
     d_field = torch.from_numpy(field.reshape(-1)).cuda()
-    bricks = torch.zeros(R * (brick + 4) ** 3 * 4, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(R * (brick + 4) ** 3 * 8, dtype=torch.float32, device="cuda")
     rafi.rf_c2_make_bricks(d_field, n, brick, bricks, s)
     del d_field
     d_seeds = torch.from_numpy(seeds).cuda()
@@ -798,7 +798,7 @@ def run_section(args):
         R = (n // brick) ** 3
         field, _ = inputs.c2_field(n)
         d_field = torch.from_numpy(field.reshape(-1)).cuda()
-        bricks = torch.zeros(R * (brick + 4) ** 3 * 4, dtype=torch.float32, device="cuda")
+        bricks = torch.zeros(R * (brick + 4) ** 3 * 8, dtype=torch.float32, device="cuda")
         rafi.rf_c2_make_bricks(d_field, n, brick, bricks, s)
         del d_field
         d_seeds = torch.from_numpy(inputs.c2_seeds(count, n, seed=2)).cuda()

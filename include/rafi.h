@@ -371,9 +371,13 @@ rf_status rf_c0_render_graph(rf_ctx *ctx, const float *bricks, const float *cam,
 #define RF_C2_MAXSTEPS 3
 
 /* Cut an N^3 x 3 float vector field (device, index ((z*N + y)*N + x)*3 + c)
- * into (N/B)^3 bricks of (B+4)^3 float4 {vx, vy, vz, 0} with a two-voxel
- * halo (clamp to edge at the grid border); brick of rank r = bx + nb*(by +
- * nb*bz) at bricks + r*(B+4)^3*4 floats. */
+ * into (N/B)^3 bricks of (B+4)^3 elements with a two-voxel halo.  Element
+ * (lx, ly, lz) holds 8 floats {vx, vy, vz, 0} of the voxel at the brick's
+ * halo origin + (lx, ly, lz) and the same for the voxel one step further
+ * along x, both clamped to the grid (so one 32-byte load gives both x corners
+ * of a trilinear sample).  Brick of rank r = bx + nb*(by + nb*bz) at
+ * bricks + r*(B+4)^3*8 floats; bricks (device, (N/B)^3*(B+4)^3*8 floats) must
+ * be 32-byte aligned, else RF_ERR_ARG. */
 rf_status rf_c2_make_bricks(const float *field, int32_t N, int32_t B, float *bricks, void *stream);
 
 /* Seed (Sec. 5.4 "particles are released at predefined seed points"):

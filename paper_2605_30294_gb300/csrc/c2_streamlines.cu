@@ -22,7 +22,7 @@ constexpr int kHalo = 2;
 enum : uint32_t { kExited = 1u, kStalled = 2u, kMaxSteps = 3u };
 
 struct C2Params {
-    const float4 *bricks;  // (N/B)^3 bricks of (B + 2*kHalo)^3 float4
+    const float *bricks;   // (N/B)^3 bricks of (B + 2*kHalo)^3 x-pairs of 8 floats (32-byte aligned)
     uint4 *out;            // final particle per id (2 x uint4)
     uint64_t outCap;
     int32_t N, B, nb;
@@ -41,9 +41,23 @@ __device__ __forceinline__ int32_t owner_of(float px, float py, float pz, int32_
     return bx + nb * (by + nb * bz);
 }
 
+// One brick element: the velocities {vx, vy, vz, 0} of voxel x and of voxel
+// x + 1, read by one 32-byte load through the read-only path.
+__device__ __forceinline__ void ld_pair(const float *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // Trilinear velocity at p from the brick whose halo origin is org (voxel
-// centres at v + 0.5, clamp to the grid edge, then to the halo).
-__device__ __forceinline__ void sample(const float4 *__restrict__ brick, int32_t N, int32_t S, const int32_t org[3],
+// centres at v + 0.5, clamp to the grid edge).  Along y and z the two corner
+// indices are clamped to the grid, then to the halo; along x the element at
+// lo - org holds both corners (make_bricks_kernel clamps them to the grid),
+// so the eight corners take four loads.  A stage point stays within a
+// quarter voxel of the brick (speed at most 1, h = 0.25), well inside the
+// halo, where this equals the unpartitioned trilinear sample.
+__device__ __forceinline__ void sample(const float *__restrict__ brick, int32_t N, int32_t S, const int32_t org[3],
                                        const float p[3], float v[3])
 {
     int32_t i0[3], i1[3];
@@ -54,17 +68,19 @@ __device__ __forceinline__ void sample(const float4 *__restrict__ brick, int32_t
         const float fl = floorf(u);
         f[a] = u - fl;
         const int32_t lo = (int32_t)fl;
-        i0[a] = clampi(clampi(lo, 0, N - 1) - org[a], 0, S - 1);
-        i1[a] = clampi(clampi(lo + 1, 0, N - 1) - org[a], 0, S - 1);
+        if (a == 0) {
+            i0[a] = clampi(lo - org[a], 0, S - 1);
+            i1[a] = i0[a];
+        } else {
+            i0[a] = clampi(clampi(lo, 0, N - 1) - org[a], 0, S - 1);
+            i1[a] = clampi(clampi(lo + 1, 0, N - 1) - org[a], 0, S - 1);
+        }
     }
-    const float4 t000 = __ldg(brick + (i0[2] * S + i0[1]) * S + i0[0]);
-    const float4 t100 = __ldg(brick + (i0[2] * S + i0[1]) * S + i1[0]);
-    const float4 t010 = __ldg(brick + (i0[2] * S + i1[1]) * S + i0[0]);
-    const float4 t110 = __ldg(brick + (i0[2] * S + i1[1]) * S + i1[0]);
-    const float4 t001 = __ldg(brick + (i1[2] * S + i0[1]) * S + i0[0]);
-    const float4 t101 = __ldg(brick + (i1[2] * S + i0[1]) * S + i1[0]);
-    const float4 t011 = __ldg(brick + (i1[2] * S + i1[1]) * S + i0[0]);
-    const float4 t111 = __ldg(brick + (i1[2] * S + i1[1]) * S + i1[0]);
+    float4 t000, t100, t010, t110, t001, t101, t011, t111;
+    ld_pair(brick + (size_t)8 * ((i0[2] * S + i0[1]) * S + i0[0]), t000, t100);
+    ld_pair(brick + (size_t)8 * ((i0[2] * S + i1[1]) * S + i0[0]), t010, t110);
+    ld_pair(brick + (size_t)8 * ((i1[2] * S + i0[1]) * S + i0[0]), t001, t101);
+    ld_pair(brick + (size_t)8 * ((i1[2] * S + i1[1]) * S + i0[0]), t011, t111);
     const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
 #define RF_TRI(c, k)                                       \
     {                                                      \
@@ -87,7 +103,7 @@ __device__ int32_t c2_advance(const C2Params &P, uint4 (&w)[2], int32_t rank)
     const int32_t S = P.B + 2 * kHalo;
     const int32_t bx = rank % P.nb, by = (rank / P.nb) % P.nb, bz = rank / (P.nb * P.nb);
     const int32_t org[3] = {bx * P.B - kHalo, by * P.B - kHalo, bz * P.B - kHalo};
-    const float4 *brick = P.bricks + (size_t)rank * S * S * S;
+    const float *brick = P.bricks + (size_t)rank * S * S * S * 8;
     float p[3] = {__uint_as_float(w[0].x), __uint_as_float(w[0].y), __uint_as_float(w[0].z)};
     uint32_t steps = w[1].x, hops = w[1].y, status = 0u, taken = 0u;
     int32_t dst = -1;
@@ -177,6 +193,8 @@ struct C2Work {
     __device__ void retire(const uint4 (&w)[2]) const { c2_write_out(P, w); }
 };
 
+// Element (lx, ly, lz) of brick r holds the grid voxels (gx, gy, gz) and
+// (gx + 1, gy, gz) of its halo origin + (lx, ly, lz), each clamped to the grid.
 __global__ void __launch_bounds__(kBlock) make_bricks_kernel(const float *__restrict__ field, int32_t N, int32_t B,
                                                              float4 *__restrict__ bricks)
 {
@@ -189,10 +207,13 @@ __global__ void __launch_bounds__(kBlock) make_bricks_kernel(const float *__rest
         const int32_t lx = l % S, ly = (l / S) % S, lz = l / (S * S);
         const int32_t bx = r % nb, by = (r / nb) % nb, bz = r / (nb * nb);
         const int32_t gx = clampi(bx * B - kHalo + lx, 0, N - 1);
+        const int32_t gx1 = clampi(bx * B - kHalo + lx + 1, 0, N - 1);
         const int32_t gy = clampi(by * B - kHalo + ly, 0, N - 1);
         const int32_t gz = clampi(bz * B - kHalo + lz, 0, N - 1);
-        const float *f = field + (((size_t)gz * N + gy) * N + gx) * 3u;
-        bricks[v] = make_float4(f[0], f[1], f[2], 0.0f);
+        const float *row = field + ((size_t)gz * N + gy) * N * 3u;
+        const float *f = row + (size_t)gx * 3u, *f1 = row + (size_t)gx1 * 3u;
+        bricks[2 * v] = make_float4(f[0], f[1], f[2], 0.0f);
+        bricks[2 * v + 1] = make_float4(f1[0], f1[1], f1[2], 0.0f);
     }
 }
 
@@ -259,7 +280,7 @@ C2Params make_params(const float *bricks, int32_t N, int32_t B, float h, uint32_
                      void *out, uint64_t outCap)
 {
     C2Params P;
-    P.bricks = reinterpret_cast<const float4 *>(bricks);
+    P.bricks = bricks;
     P.out = static_cast<uint4 *>(out);
     P.outCap = outCap;
     P.N = N;
@@ -287,8 +308,8 @@ extern "C" {
 
 rf_status rf_c2_make_bricks(const float *field, int32_t N, int32_t B, float *bricks, void *stream)
 {
-    if (!field || !bricks || N < 1 || B < 1 || N % B) {
-        set_error("rf_c2_make_bricks: bad arguments");
+    if (!field || !bricks || N < 1 || B < 1 || N % B || (reinterpret_cast<uintptr_t>(bricks) & 31u)) {
+        set_error("rf_c2_make_bricks: bad arguments (bricks must be 32-byte aligned)");
         return RF_ERR_ARG;
     }
     const int32_t nb = N / B, S = B + 2 * kHalo;
@@ -322,8 +343,8 @@ rf_status rf_c2_trace(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, fl
                       uint32_t stepsPerRound, void *out, uint64_t outCapacity, void *stream)
 {
     if (rf_status st = check_c2(ctx, N, B, "rf_c2_trace")) return st;
-    if (!bricks || !out || !(h > 0.0f)) {
-        set_error("rf_c2_trace: NULL bricks/out or step <= 0");
+    if (!bricks || !out || !(h > 0.0f) || (reinterpret_cast<uintptr_t>(bricks) & 31u)) {
+        set_error("rf_c2_trace: NULL or unaligned bricks, NULL out or step <= 0");
         return RF_ERR_ARG;
     }
     DeviceGuard g(ctx->device);
@@ -343,7 +364,8 @@ rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const 
                     int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded)
 {
     if (rf_status st = check_c2(ctx, N, B, "rf_c2_run")) return st;
-    if (!bricks || !out || (n && !seeds) || n > ctx->capacity || !(h > 0.0f)) {
+    if (!bricks || !out || (n && !seeds) || n > ctx->capacity || !(h > 0.0f) ||
+        (reinterpret_cast<uintptr_t>(bricks) & 31u)) {
         set_error("rf_c2_run: bad arguments");
         return RF_ERR_ARG;
     }
