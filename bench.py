@@ -330,7 +330,7 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
     vol = inputs.c0_volume(n)
     cam = inputs.c0_camera(n, w, h)
     dvol = torch.from_numpy(vol.reshape(-1)).cuda()
-    bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
     rafi.rf_c0_make_bricks(dvol, n, brick, bricks, s)
     image = torch.zeros(w * h, dtype=torch.float32, device="cuda")
     out = {}
@@ -460,7 +460,7 @@ def c3_ea(torch, rafi, inputs, s, reps=5):
     vol = inputs.c0_volume(n)
     cam = inputs.c0_camera(n, w, h)
     dv = torch.from_numpy(vol.reshape(-1)).cuda()
-    bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
     rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
     nr = w * h * spp
     rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
@@ -491,7 +491,7 @@ def c4_transport(torch, rafi, inputs, s, cpu=None):
     n, brick, spp = 1024, 128, 16
     vol, smax = inputs.c4_volume(n)
     views = inputs.c4_views(n)
-    bricks = torch.zeros(512 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(512 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
     dv = torch.from_numpy(vol.reshape(-1)).cuda()
     rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
     del dv
@@ -819,7 +819,7 @@ def run_section(args):
         vol = inputs.c0_volume(n)
         cam = inputs.c0_camera(n, w, h)
         dv = torch.from_numpy(vol.reshape(-1)).cuda()
-        bricks = torch.zeros(8 * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+        bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
         rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
         nr = w * h * spp
         rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
@@ -842,7 +842,7 @@ def run_section(args):
         R = (n // brick) ** 3
         vol, smax = inputs.c4_volume(n)
         views = inputs.c4_views(n, sizes=((512, 512),))
-        bricks = torch.zeros(R * (brick + 2) ** 3, dtype=torch.float32, device="cuda")
+        bricks = torch.zeros(R * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
         dv = torch.from_numpy(vol.reshape(-1)).cuda()
         rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
         del dv

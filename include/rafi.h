@@ -326,8 +326,13 @@ rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t
 /* --- absorption marching through bricks (48-byte rays) ------------------- */
 
 /* Cut an N^3 float volume (device, x fastest) into (N/B)^3 bricks of
- * (B+2)^3 floats with a one-voxel halo, clamp-to-edge at the volume border;
- * brick of rank r = bx + nb*(by + nb*bz) at bricks + r*(B+2)^3. */
+ * (B+2)^3 elements with a one-voxel halo.  Element (lx, ly, lz) is the x-y
+ * quad {v(x, y), v(x+1, y), v(x, y+1), v(x+1, y+1)} of plane z, where (x, y,
+ * z) = the brick's halo origin + (lx, ly, lz) and every index is clamped to
+ * the volume (so the eight corners of a trilinear sample take two 16-byte
+ * loads).  Brick of rank r = bx + nb*(by + nb*bz) at bricks + r*(B+2)^3*4
+ * floats; bricks (device, (N/B)^3*(B+2)^3*4 floats) must be 16-byte aligned,
+ * else RF_ERR_ARG, here and in the calls that read them. */
 rf_status rf_c0_make_bricks(const float *volume, int32_t N, int32_t B, float *bricks, void *stream);
 
 /* Raygen (Sec. 5.1 step 2): one primary ray per pixel of a W x H pinhole

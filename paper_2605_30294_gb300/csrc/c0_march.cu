@@ -49,38 +49,39 @@ __device__ __forceinline__ int32_t owner(float px, float py, float pz, int32_t B
     return brick_of(px, B, nb) + nb * (brick_of(py, B, nb) + nb * brick_of(pz, B, nb));
 }
 
-// Trilinear sigma at p from the brick (bx,by,bz) stored with halo: voxel
-// centres at v + 0.5, clamp to the volume edge, then to the brick's halo.
-__device__ __forceinline__ float sample(const float *__restrict__ brick, int32_t N, int32_t B, int32_t bx,
+// Trilinear sigma at p from the brick (bx,by,bz) stored with halo as x-y
+// quads: voxel centres at v + 0.5, clamp to the volume edge.  The quad at
+// (lo - origin) along x and y carries both corners, clamped to the volume;
+// along z the two planes are clamped to the volume, then to the halo.  A
+// sample the rank owns lies within its brick, so the indices stay inside
+// the halo, where this equals the unpartitioned trilinear sample.
+__device__ __forceinline__ float sample(const float4 *__restrict__ brick, int32_t N, int32_t B, int32_t bx,
                                         int32_t by, int32_t bz, float px, float py, float pz)
 {
     const int32_t S = B + 2;
     const float u[3] = {px - 0.5f, py - 0.5f, pz - 0.5f};
     const int32_t org[3] = {bx * B - 1, by * B - 1, bz * B - 1};
-    int32_t i0[3], i1[3];
+    int32_t j[3], z1 = 0;
     float f[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float fl = floorf(u[a]);
         f[a] = u[a] - fl;
         const int32_t lo = (int32_t)fl;
-        i0[a] = clampi(clampi(lo, 0, N - 1) - org[a], 0, S - 1);
-        i1[a] = clampi(clampi(lo + 1, 0, N - 1) - org[a], 0, S - 1);
+        if (a < 2) {
+            j[a] = clampi(lo - org[a], 0, S - 1);
+        } else {
+            j[a] = clampi(clampi(lo, 0, N - 1) - org[a], 0, S - 1);
+            z1 = clampi(clampi(lo + 1, 0, N - 1) - org[a], 0, S - 1);
+        }
     }
-#define VX(x, y, z) __ldg(brick + ((z) * S + (y)) * S + (x))
-    const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
-    const float c00 = VX(i0[0], i0[1], i0[2]) * gx + VX(i1[0], i0[1], i0[2]) * f[0];
-    const float c10 = VX(i0[0], i1[1], i0[2]) * gx + VX(i1[0], i1[1], i0[2]) * f[0];
-    const float c01 = VX(i0[0], i0[1], i1[2]) * gx + VX(i1[0], i0[1], i1[2]) * f[0];
-    const float c11 = VX(i0[0], i1[1], i1[2]) * gx + VX(i1[0], i1[1], i1[2]) * f[0];
-#undef VX
-    const float c0 = c00 * gy + c10 * f[1];
-    const float c1 = c01 * gy + c11 * f[1];
-    return c0 * gz + c1 * f[2];
+    return quad_trilinear(brick, S, j[0], j[1], j[2], z1, f);
 }
 
+// Element (lx, ly, lz) of brick r: the x-y quad of the volume voxels at the
+// brick's halo origin + (lx, ly, lz), each index clamped to the volume.
 __global__ void __launch_bounds__(kBlock) make_bricks_kernel(const float *__restrict__ vol, int32_t N, int32_t B,
-                                                             float *__restrict__ bricks)
+                                                             float4 *__restrict__ bricks)
 {
     const int32_t nb = N / B, S = B + 2;
     const uint64_t per = (uint64_t)S * S * S;
@@ -90,10 +91,12 @@ __global__ void __launch_bounds__(kBlock) make_bricks_kernel(const float *__rest
         const int32_t l = (int32_t)(v % per);
         const int32_t lx = l % S, ly = (l / S) % S, lz = l / (S * S);
         const int32_t bx = r % nb, by = (r / nb) % nb, bz = r / (nb * nb);
-        const int32_t gx = clampi(bx * B - 1 + lx, 0, N - 1);
-        const int32_t gy = clampi(by * B - 1 + ly, 0, N - 1);
+        const int32_t gx = clampi(bx * B - 1 + lx, 0, N - 1), gx1 = clampi(bx * B + lx, 0, N - 1);
+        const int32_t gy = clampi(by * B - 1 + ly, 0, N - 1), gy1 = clampi(by * B + ly, 0, N - 1);
         const int32_t gz = clampi(bz * B - 1 + lz, 0, N - 1);
-        bricks[v] = vol[((size_t)gz * N + gy) * N + gx];
+        const float *pl = vol + (size_t)gz * N * N;
+        bricks[v] = make_float4(pl[(size_t)gy * N + gx], pl[(size_t)gy * N + gx1], pl[(size_t)gy1 * N + gx],
+                                pl[(size_t)gy1 * N + gx1]);
     }
 }
 
@@ -162,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(const float *__restrict__
             hopCount[r.pixel] = c + 1;
         }
         const int32_t bx = rank % nb, by = (rank / nb) % nb, bz = rank / (nb * nb);
-        const float *brick = bricks + (size_t)rank * S * S * S;
+        const float4 *brick = reinterpret_cast<const float4 *>(bricks) + (size_t)rank * S * S * S;
         int32_t k = (int32_t)r.k;
         float tau = r.tau;
         for (;;) {
@@ -219,15 +222,16 @@ extern "C" {
 
 rf_status rf_c0_make_bricks(const float *volume, int32_t N, int32_t B, float *bricks, void *stream)
 {
-    if (!volume || !bricks || N < 1 || B < 1 || N % B) {
-        set_error("rf_c0_make_bricks: bad arguments");
+    if (!volume || !bricks || N < 1 || B < 1 || N % B || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
+        set_error("rf_c0_make_bricks: bad arguments (bricks must be 16-byte aligned)");
         return RF_ERR_ARG;
     }
     const int32_t nb = N / B, S = B + 2;
     const uint64_t total = (uint64_t)S * S * S * nb * nb * nb;
     uint64_t blocks = (total + kBlock - 1) / kBlock;
     if (blocks > 65535u * 16u) blocks = 65535u * 16u;
-    make_bricks_kernel<<<(unsigned)blocks, kBlock, 0, static_cast<cudaStream_t>(stream)>>>(volume, N, B, bricks);
+    make_bricks_kernel<<<(unsigned)blocks, kBlock, 0, static_cast<cudaStream_t>(stream)>>>(
+        volume, N, B, reinterpret_cast<float4 *>(bricks));
     RF_LAUNCHED("make_bricks_kernel");
     return RF_OK;
 }
@@ -260,8 +264,8 @@ rf_status rf_c0_march(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, fl
                       int32_t maxHops, int32_t *hopCount, void *stream)
 {
     if (rf_status st = check_c0(ctx, N, B, "rf_c0_march")) return st;
-    if (!bricks || !image || (hopLog && (!hopCount || maxHops < 1))) {
-        set_error("rf_c0_march: NULL bricks/image, or hopLog without hopCount");
+    if (!bricks || !image || (hopLog && (!hopCount || maxHops < 1)) || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
+        set_error("rf_c0_march: NULL or unaligned bricks, NULL image, or hopLog without hopCount");
         return RF_ERR_ARG;
     }
     DeviceGuard g(ctx->device);

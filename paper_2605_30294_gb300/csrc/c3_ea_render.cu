@@ -62,9 +62,11 @@ __device__ __forceinline__ int32_t owner_of(float px, float py, float pz, int32_
     return bx + nb * (by + nb * bz);
 }
 
-// Trilinear taps at p: global clamped indices gi0/gi1 and fractions f.
+// Trilinear taps at p: global clamped indices g0/g1, the unclamped lower
+// corner along x and y (lo), and fractions f.
 struct Taps {
     int32_t g0[3], g1[3];
+    int32_t lo[2];
     float f[3];
 };
 
@@ -79,31 +81,20 @@ __device__ __forceinline__ Taps taps_at(float px, float py, float pz, int32_t N)
         const int32_t lo = (int32_t)fl;
         t.g0[a] = clampi(lo, 0, N - 1);
         t.g1[a] = clampi(lo + 1, 0, N - 1);
+        if (a < 2) t.lo[a] = lo;
     }
     return t;
 }
 
-// sigma from the brick with halo 1 whose halo origin is org (same taps and
-// operation order as the unpartitioned grid)
-__device__ __forceinline__ float sigma_at(const float *__restrict__ brick, int32_t S, const int32_t org[3],
+// sigma from the brick of x-y quads with halo 1 whose halo origin is org
+// (same corners and operation order as the unpartitioned grid: a sample the
+// rank owns lies within its brick, so the indices stay inside the halo)
+__device__ __forceinline__ float sigma_at(const float4 *__restrict__ brick, int32_t S, const int32_t org[3],
                                           const Taps &t)
 {
-    int32_t i0[3], i1[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        i0[a] = clampi(t.g0[a] - org[a], 0, S - 1);
-        i1[a] = clampi(t.g1[a] - org[a], 0, S - 1);
-    }
-#define VX(x, y, z) __ldg(brick + ((z) * S + (y)) * S + (x))
-    const float gx = 1.0f - t.f[0], gy = 1.0f - t.f[1], gz = 1.0f - t.f[2];
-    const float c00 = VX(i0[0], i0[1], i0[2]) * gx + VX(i1[0], i0[1], i0[2]) * t.f[0];
-    const float c10 = VX(i0[0], i1[1], i0[2]) * gx + VX(i1[0], i1[1], i0[2]) * t.f[0];
-    const float c01 = VX(i0[0], i0[1], i1[2]) * gx + VX(i1[0], i0[1], i1[2]) * t.f[0];
-    const float c11 = VX(i0[0], i1[1], i1[2]) * gx + VX(i1[0], i1[1], i1[2]) * t.f[0];
-#undef VX
-    const float c0 = c00 * gy + c10 * t.f[1];
-    const float c1 = c01 * gy + c11 * t.f[1];
-    return c0 * gz + c1 * t.f[2];
+    const int32_t jx = clampi(t.lo[0] - org[0], 0, S - 1), jy = clampi(t.lo[1] - org[1], 0, S - 1);
+    const int32_t z0 = clampi(t.g0[2] - org[2], 0, S - 1), z1 = clampi(t.g1[2] - org[2], 0, S - 1);
+    return quad_trilinear(brick, S, jx, jy, z0, z1, t.f);
 }
 
 // Per-ray gradient accumulator: consecutive samples of a ray (half a voxel
@@ -224,7 +215,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_que
         EARay r = rf::getIncoming<EARay>(q, i);
         const int32_t bx = rank % P.nb, by = (rank / P.nb) % P.nb, bz = rank / (P.nb * P.nb);
         const int32_t org[3] = {bx * P.B - 1, by * P.B - 1, bz * P.B - 1};
-        const float *brick = P.bricks + (size_t)rank * S * S * S;
+        const float4 *brick = reinterpret_cast<const float4 *>(P.bricks) + (size_t)rank * S * S * S;
         int32_t k = (int32_t)r.k;
         float T = r.T, acc = r.acc;
         GradAcc ga;
@@ -371,7 +362,7 @@ rf_status rf_c3_render(rf_ctx *ctx, const float *bricks, const float *cam, int32
                        uint64_t *rounds)
 {
     if (rf_status st = check_c3(ctx, N, B, W, H, spp, "rf_c3_render")) return st;
-    if (!bricks || !cam || !rayC || !image) {
+    if (!bricks || !cam || !rayC || !image || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
         set_error("rf_c3_render: NULL buffer");
         return RF_ERR_ARG;
     }
@@ -390,7 +381,7 @@ rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int3
                         float *gradVolume, uint32_t maxRounds, void *stream, uint64_t *rounds)
 {
     if (rf_status st = check_c3(ctx, N, B, W, H, spp, "rf_c3_adjoint")) return st;
-    if (!bricks || !cam || !rayC || !gradImage || !gradVolume) {
+    if (!bricks || !cam || !rayC || !gradImage || !gradVolume || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
         set_error("rf_c3_adjoint: NULL buffer");
         return RF_ERR_ARG;
     }

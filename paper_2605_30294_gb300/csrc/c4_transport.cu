@@ -32,7 +32,7 @@ struct __align__(16) TRay {
 static_assert(sizeof(TRay) == 64, "64-byte ray");
 
 struct TParams {
-    const float *bricks;  // halo 1
+    const float *bricks;  // halo 1, x-y quads (4 floats per element, 16-byte aligned)
     int32_t N, B, nb;
     float sigmaMax;
     uint32_t seed;
@@ -54,30 +54,30 @@ __device__ __forceinline__ int32_t owner_of(float px, float py, float pz, int32_
     return bx + nb * (by + nb * bz);
 }
 
-__device__ __forceinline__ float sigma_at(const float *__restrict__ brick, int32_t N, int32_t S, const int32_t org[3],
+// Trilinear sigma at p from the rank's brick of x-y quads (halo 1, origin
+// org): the quad at (lo - org) along x and y holds both corners, clamped to
+// the volume; the two z planes are clamped to the volume, then to the halo.
+// Every evaluated point is owned by the rank, so the indices stay inside the
+// halo, where this equals the unpartitioned trilinear sample.
+__device__ __forceinline__ float sigma_at(const float4 *__restrict__ brick, int32_t N, int32_t S, const int32_t org[3],
                                           float px, float py, float pz)
 {
     const float u[3] = {px - 0.5f, py - 0.5f, pz - 0.5f};
-    int32_t i0[3], i1[3];
+    int32_t j[3], z1 = 0;
     float f[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float fl = floorf(u[a]);
         f[a] = u[a] - fl;
         const int32_t lo = (int32_t)fl;
-        i0[a] = clampi(clampi(lo, 0, N - 1) - org[a], 0, S - 1);
-        i1[a] = clampi(clampi(lo + 1, 0, N - 1) - org[a], 0, S - 1);
+        if (a < 2) {
+            j[a] = clampi(lo - org[a], 0, S - 1);
+        } else {
+            j[a] = clampi(clampi(lo, 0, N - 1) - org[a], 0, S - 1);
+            z1 = clampi(clampi(lo + 1, 0, N - 1) - org[a], 0, S - 1);
+        }
     }
-#define VX(x, y, z) __ldg(brick + ((z) * S + (y)) * S + (x))
-    const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
-    const float c00 = VX(i0[0], i0[1], i0[2]) * gx + VX(i1[0], i0[1], i0[2]) * f[0];
-    const float c10 = VX(i0[0], i1[1], i0[2]) * gx + VX(i1[0], i1[1], i0[2]) * f[0];
-    const float c01 = VX(i0[0], i0[1], i1[2]) * gx + VX(i1[0], i0[1], i1[2]) * f[0];
-    const float c11 = VX(i0[0], i1[1], i1[2]) * gx + VX(i1[0], i1[1], i1[2]) * f[0];
-#undef VX
-    const float c0 = c00 * gy + c10 * f[1];
-    const float c1 = c01 * gy + c11 * f[1];
-    return c0 * gz + c1 * f[2];
+    return quad_trilinear(brick, S, j[0], j[1], j[2], z1, f);
 }
 
 // Henyey-Greenstein (g = 0.3) scattering of direction d by (xi, xphi).
@@ -119,7 +119,7 @@ __device__ int32_t track(const TParams &P, uint4 (&w)[4], int32_t rank)
     const int32_t S = P.B + 2;
     const int32_t bx = rank % P.nb, by = (rank / P.nb) % P.nb, bz = rank / (P.nb * P.nb);
     const int32_t org[3] = {bx * P.B - 1, by * P.B - 1, bz * P.B - 1};
-    const float *brick = P.bricks + (size_t)rank * S * S * S;
+    const float4 *brick = reinterpret_cast<const float4 *>(P.bricks) + (size_t)rank * S * S * S;
     const float fN = (float)P.N;
     float p[3] = {r.px, r.py, r.pz}, d[3] = {r.dx, r.dy, r.dz};
     int32_t dst = -1;
@@ -305,7 +305,7 @@ extern "C" rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, i
         return RF_ERR_ARG;
     }
     if (!bricks || !cams || !sizes || !score || numViews < 1 || spp < 1 || !(sigmaMax > 0.0f) || N < 1 || B < 1 ||
-        N % B || (int64_t)(N / B) * (N / B) * (N / B) != ctx->numRanks) {
+        N % B || (int64_t)(N / B) * (N / B) * (N / B) != ctx->numRanks || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
         set_error("rf_c4_render: bad arguments");
         return RF_ERR_ARG;
     }

@@ -224,6 +224,27 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// Scalar bricks with a one-voxel halo (rf_c0_make_bricks) hold x-y quads:
+// element (x, y, z) is the float4 {v(x, y), v(x+1, y), v(x, y+1), v(x+1, y+1)}
+// of plane z, every index clamped to the volume, so the eight corners of a
+// trilinear sample take two 16-byte loads.  jx, jy: brick-local indices of the
+// lower x and y corner; z0, z1: the two planes; f: the fractions.  The blend
+// runs in x, then y, then z.
+__device__ __forceinline__ float quad_trilinear(const float4 *__restrict__ brick, int32_t S, int32_t jx, int32_t jy,
+                                                int32_t z0, int32_t z1, const float f[3])
+{
+    const float4 q0 = __ldg(brick + ((size_t)z0 * S + jy) * S + jx);
+    const float4 q1 = __ldg(brick + ((size_t)z1 * S + jy) * S + jx);
+    const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
+    const float c00 = q0.x * gx + q0.y * f[0];
+    const float c10 = q0.z * gx + q0.w * f[0];
+    const float c01 = q1.x * gx + q1.y * f[0];
+    const float c11 = q1.z * gx + q1.w * f[0];
+    const float c0 = c00 * gy + c10 * f[1];
+    const float c1 = c01 * gy + c11 * f[1];
+    return c0 * gz + c1 * f[2];
+}
+
 __device__ __forceinline__ uint32_t lanemask_lt()
 {
     uint32_t m;
