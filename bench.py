@@ -330,7 +330,7 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
     vol = inputs.c0_volume(n)
     cam = inputs.c0_camera(n, w, h)
     dvol = torch.from_numpy(vol.reshape(-1)).cuda()
-    bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
     rafi.rf_c0_make_bricks(dvol, n, brick, bricks, s)
     image = torch.zeros(w * h, dtype=torch.float32, device="cuda")
     out = {}
@@ -410,7 +410,7 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3, cpu=None):
     seeds = inputs.c2_seeds(count, n, seed=2)
     set_ids = np.repeat(np.arange(len(sizes), dtype=np.uint32), sizes)
     d_field = torch.from_numpy(field.reshape(-1)).cuda()
-    bricks = torch.zeros(R * (brick + 4) ** 3 * 8, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(rafi.c2_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
     rafi.rf_c2_make_bricks(d_field, n, brick, bricks, s)
     del d_field
     d_seeds = torch.from_numpy(seeds).cuda()
@@ -460,7 +460,7 @@ def c3_ea(torch, rafi, inputs, s, reps=5):
     vol = inputs.c0_volume(n)
     cam = inputs.c0_camera(n, w, h)
     dv = torch.from_numpy(vol.reshape(-1)).cuda()
-    bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
     rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
     nr = w * h * spp
     rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
@@ -491,7 +491,7 @@ def c4_transport(torch, rafi, inputs, s, cpu=None):
     n, brick, spp = 1024, 128, 16
     vol, smax = inputs.c4_volume(n)
     views = inputs.c4_views(n)
-    bricks = torch.zeros(512 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
     dv = torch.from_numpy(vol.reshape(-1)).cuda()
     rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
     del dv
@@ -798,7 +798,7 @@ def run_section(args):
         R = (n // brick) ** 3
         field, _ = inputs.c2_field(n)
         d_field = torch.from_numpy(field.reshape(-1)).cuda()
-        bricks = torch.zeros(R * (brick + 4) ** 3 * 8, dtype=torch.float32, device="cuda")
+        bricks = torch.zeros(rafi.c2_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
         rafi.rf_c2_make_bricks(d_field, n, brick, bricks, s)
         del d_field
         d_seeds = torch.from_numpy(inputs.c2_seeds(count, n, seed=2)).cuda()
@@ -819,7 +819,7 @@ def run_section(args):
         vol = inputs.c0_volume(n)
         cam = inputs.c0_camera(n, w, h)
         dv = torch.from_numpy(vol.reshape(-1)).cuda()
-        bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
+        bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
         rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
         nr = w * h * spp
         rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
@@ -842,7 +842,7 @@ def run_section(args):
         R = (n // brick) ** 3
         vol, smax = inputs.c4_volume(n)
         views = inputs.c4_views(n, sizes=((512, 512),))
-        bricks = torch.zeros(R * (brick + 2) ** 3 * 4, dtype=torch.float32, device="cuda")
+        bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
         dv = torch.from_numpy(vol.reshape(-1)).cuda()
         rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
         del dv

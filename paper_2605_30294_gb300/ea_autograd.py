@@ -18,7 +18,7 @@ class PartitionedEARender(torch.autograd.Function):
         ranks = (n // brick) ** 3
         vol = volume.detach().contiguous()
         s = torch.cuda.current_stream(vol.device)
-        bricks = torch.empty(ranks * (brick + 2) ** 3 * 4, dtype=torch.float32, device=vol.device)
+        bricks = torch.empty(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device=vol.device)
         rafi.rf_c0_make_bricks(vol, n, brick, bricks, s)
         nrays = width * height * spp
         ray_c = torch.empty(nrays, dtype=torch.float32, device=vol.device)

@@ -290,7 +290,42 @@ def rf_c1_run_batched(ctx: int, items, n: int, seed: int, mode: int, zipf_s: flo
     return st, cnt.value, rounds.value, fwd.value
 
 
+def c0_bricks_floats(n: int, brick: int) -> int:
+    """Floats of the bricks rf_c0_make_bricks writes: (n/brick)^3 bricks of
+    (brick+2)^3 x-y quads of 4 floats."""
+    return (n // brick) ** 3 * (brick + 2) ** 3 * 4
+
+
+def c2_bricks_floats(n: int, brick: int) -> int:
+    """Floats of the bricks rf_c2_make_bricks writes: (n/brick)^3 bricks of
+    (brick+4)^3 x-pairs of 8 floats."""
+    return (n // brick) ** 3 * (brick + 4) ** 3 * 8
+
+
+def _need(buf, nbytes: int, fn: str, what: str) -> None:
+    """Raises RF_ERR_ARG before the call when a sized buffer (torch tensor or
+    numpy array) holds fewer bytes than the call reads or writes.  Plain
+    pointers (ints) cannot be checked and pass."""
+    if buf is None or isinstance(buf, int):
+        return
+    if hasattr(buf, "numel") and hasattr(buf, "element_size"):
+        have = buf.numel() * buf.element_size()
+    elif hasattr(buf, "nbytes"):
+        have = int(buf.nbytes)
+    else:
+        return
+    if have < nbytes:
+        raise RafiError(RF_ERR_ARG, fn, f"{what} holds {have} bytes, the call needs {nbytes}")
+
+
+def _need_bricks(bricks, n: int, brick: int, fn: str, c2: bool = False) -> None:
+    if brick > 0 and n > 0 and n % brick == 0:  # other shapes are refused by the library
+        _need(bricks, 4 * (c2_bricks_floats(n, brick) if c2 else c0_bricks_floats(n, brick)), fn, "bricks")
+
+
 def rf_c0_make_bricks(volume, n: int, brick: int, bricks, stream=None) -> None:
+    _need(volume, 4 * max(n, 0) ** 3, "rf_c0_make_bricks", "volume")
+    _need_bricks(bricks, n, brick, "rf_c0_make_bricks")
     _check("rf_c0_make_bricks", lib().rf_c0_make_bricks(ptr(volume), n, brick, ptr(bricks), stream_handle(stream)))
 
 
@@ -307,12 +342,14 @@ def rf_c0_raygen(ctx: int, cam, n: int, brick: int, width: int, height: int, ima
 
 def rf_c0_march(ctx: int, bricks, n: int, brick: int, image, hop_log=None, max_hops: int = 0,
                 hop_count=None, stream=None) -> None:
+    _need_bricks(bricks, n, brick, "rf_c0_march")
     _check("rf_c0_march", lib().rf_c0_march(ctx, ptr(bricks), n, brick, ptr(image), ptr(hop_log), max_hops,
                                             ptr(hop_count), stream_handle(stream)))
 
 
 def rf_c0_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, image, hop_log=None,
                  max_hops: int = 0, hop_count=None, max_rounds: int = 64, stream=None) -> int:
+    _need_bricks(bricks, n, brick, "rf_c0_render")
     c = _cam(cam)
     rounds = ctypes.c_uint64()
     _check("rf_c0_render", lib().rf_c0_render(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height,
@@ -324,6 +361,7 @@ def rf_c0_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: 
 def rf_c0_render_graph(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, image, hop_log=None,
                        max_hops: int = 0, hop_count=None, max_rounds: int = 64, stream=None) -> int:
     """rf_c0_render with the rounds in a kept CUDA graph (conditional while node)."""
+    _need_bricks(bricks, n, brick, "rf_c0_render_graph")
     c = _cam(cam)
     rounds = ctypes.c_uint64()
     _check("rf_c0_render_graph", lib().rf_c0_render_graph(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width,
@@ -337,6 +375,8 @@ RF_C2_EXITED, RF_C2_STALLED, RF_C2_MAXSTEPS = 1, 2, 3
 
 
 def rf_c2_make_bricks(field, n: int, brick: int, bricks, stream=None) -> None:
+    _need(field, 12 * max(n, 0) ** 3, "rf_c2_make_bricks", "field")
+    _need_bricks(bricks, n, brick, "rf_c2_make_bricks", c2=True)
     _check("rf_c2_make_bricks", lib().rf_c2_make_bricks(ptr(field), n, brick, ptr(bricks), stream_handle(stream)))
 
 
@@ -346,6 +386,7 @@ def rf_c2_seed(ctx: int, seeds, set_ids, count: int, n: int, brick: int, stream=
 
 def rf_c2_trace(ctx: int, bricks, n: int, brick: int, h: float, max_steps: int, steps_per_round: int, out,
                 out_capacity: int, stream=None) -> None:
+    _need_bricks(bricks, n, brick, "rf_c2_trace", c2=True)
     _check("rf_c2_trace", lib().rf_c2_trace(ctx, ptr(bricks), n, brick, h, max_steps, steps_per_round, ptr(out),
                                             out_capacity, stream_handle(stream)))
 
@@ -353,6 +394,7 @@ def rf_c2_trace(ctx: int, bricks, n: int, brick: int, h: float, max_steps: int, 
 def rf_c2_run(ctx: int, bricks, seeds, set_ids, count: int, n: int, brick: int, h: float, max_steps: int,
               steps_per_round: int, out, batched: bool, max_rounds: int = 1 << 20, stream=None, allow=()):
     """Whole streamline run; returns (status, rounds, forwarded)."""
+    _need_bricks(bricks, n, brick, "rf_c2_run", c2=True)
     rounds, fwd = ctypes.c_uint64(), ctypes.c_uint64()
     st = lib().rf_c2_run(ctx, ptr(bricks), ptr(seeds), ptr(set_ids), count, n, brick, h, max_steps,
                          steps_per_round, ptr(out), int(batched), max_rounds, stream_handle(stream),
@@ -363,6 +405,7 @@ def rf_c2_run(ctx: int, bricks, seeds, set_ids, count: int, n: int, brick: int, 
 
 def rf_c3_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, spp: int, seed: int, ray_c,
                  image, max_rounds: int = 64, stream=None) -> int:
+    _need_bricks(bricks, n, brick, "rf_c3_render")
     c = _cam(cam)
     rounds = ctypes.c_uint64()
     _check("rf_c3_render", lib().rf_c3_render(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height, spp,
@@ -373,6 +416,7 @@ def rf_c3_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: 
 
 def rf_c3_adjoint(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, spp: int, seed: int, ray_c,
                   grad_image, grad_volume, max_rounds: int = 64, stream=None) -> int:
+    _need_bricks(bricks, n, brick, "rf_c3_adjoint")
     c = _cam(cam)
     rounds = ctypes.c_uint64()
     _check("rf_c3_adjoint", lib().rf_c3_adjoint(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height, spp,
@@ -384,6 +428,7 @@ def rf_c3_adjoint(ctx: int, bricks, cam, n: int, brick: int, width: int, height:
 def rf_c4_render(ctx: int, bricks, n: int, brick: int, sigma_max: float, views, spp: int, seed: int, score,
                  batched: bool = True, max_rounds: int = 1 << 20, stream=None):
     """views: sequence of (cam[12], width, height, ...); returns (rounds, forwarded)."""
+    _need_bricks(bricks, n, brick, "rf_c4_render")
     nv = len(views)
     cams = (ctypes.c_float * (12 * nv))(*[float(x) for v in views for x in v[0]])
     sizes = (ctypes.c_int32 * (2 * nv))(*[int(x) for v in views for x in (v[1], v[2])])

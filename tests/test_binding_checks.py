@@ -1,0 +1,51 @@
+"""Host-side argument checks of the Python binding (CPU, no GPU needed): a
+sized buffer that is smaller than what a call would read or write raises
+RF_ERR_ARG before the library is called, so a wrong allocation can never
+reach a kernel."""
+import numpy as np
+import pytest
+
+from paper_2605_30294_gb300 import rafi
+
+
+def test_brick_sizes():
+    # scalar bricks: (n/b)^3 bricks of (b+2)^3 x-y quads of 4 floats
+    assert rafi.c0_bricks_floats(64, 32) == 8 * 34 ** 3 * 4
+    assert rafi.c0_bricks_floats(1024, 128) == 512 * 130 ** 3 * 4
+    # streamline bricks: (n/b)^3 bricks of (b+4)^3 x-pairs of 8 floats
+    assert rafi.c2_bricks_floats(512, 128) == 64 * 132 ** 3 * 8
+
+
+@pytest.mark.parametrize("short", ["volume", "bricks"])
+def test_c0_make_bricks_refuses_short_buffers(short):
+    n, b = 16, 8
+    vol = np.zeros(n ** 3 - (1 if short == "volume" else 0), np.float32)
+    bricks = np.zeros(rafi.c0_bricks_floats(n, b) - (1 if short == "bricks" else 0), np.float32)
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_c0_make_bricks(vol, n, b, bricks)
+    assert e.value.status == rafi.RF_ERR_ARG and short in str(e.value)
+
+
+def test_c2_make_bricks_refuses_the_scalar_brick_size():
+    n, b = 16, 8
+    field = np.zeros(n ** 3 * 3, np.float32)
+    bricks = np.zeros(rafi.c0_bricks_floats(n, b), np.float32)  # a quarter of what the field needs
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_c2_make_bricks(field, n, b, bricks)
+    assert e.value.status == rafi.RF_ERR_ARG
+
+
+@pytest.mark.parametrize("call", ["rf_c0_march", "rf_c2_trace", "rf_c3_render", "rf_c4_render"])
+def test_readers_refuse_short_bricks(call):
+    n, b = 16, 8
+    short = np.zeros(16, np.float32)
+    with pytest.raises(rafi.RafiError) as e:
+        if call == "rf_c0_march":
+            rafi.rf_c0_march(0, short, n, b, short)
+        elif call == "rf_c2_trace":
+            rafi.rf_c2_trace(0, short, n, b, 0.25, 10, 0, short, 1)
+        elif call == "rf_c3_render":
+            rafi.rf_c3_render(0, short, [0.0] * 12, n, b, 4, 4, 1, 3, short, short)
+        else:
+            rafi.rf_c4_render(0, short, n, b, 1.0, [([0.0] * 12, 4, 4)], 1, 4, short)
+    assert e.value.status == rafi.RF_ERR_ARG

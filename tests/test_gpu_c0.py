@@ -25,7 +25,7 @@ def render(vol, cam, n, brick, w, h, max_hops=16):
     R = nb ** 3
     s = stream()
     dvol = to_dev(vol.reshape(-1))
-    bricks = torch.zeros(R * (brick + 2) ** 3 * 4, dtype=torch.float32, device=dev())
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     rafi.rf_c0_make_bricks(dvol, n, brick, bricks, s)
     image = torch.full((w * h,), -1.0, dtype=torch.float32, device=dev())
     hop_log = torch.full((w * h, max_hops), -1, dtype=torch.int32, device=dev())
@@ -97,7 +97,7 @@ def test_raygen_then_manual_rounds():
     cam = inputs.c0_camera(n, w, h)
     ref = render(vol, cam, n, brick, w, h)
     s = stream()
-    bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device=dev())
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     rafi.rf_c0_make_bricks(to_dev(vol.reshape(-1)), n, brick, bricks, s)
     image = torch.zeros(w * h, dtype=torch.float32, device=dev())
     with rafi.Context(8, RAY_BYTES, w * h) as ctx:
@@ -122,7 +122,7 @@ def test_graph_form_matches_host_loop_and_is_relaunched():
     cam = inputs.c0_camera(n, w, h)
     want = render(vol, cam, n, brick, w, h)
     s = stream()
-    bricks = torch.zeros(8 * (brick + 2) ** 3 * 4, dtype=torch.float32, device=dev())
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     rafi.rf_c0_make_bricks(to_dev(vol.reshape(-1)), n, brick, bricks, s)
     image = torch.zeros(w * h, dtype=torch.float32, device=dev())
     hop_log = torch.full((w * h, 16), -1, dtype=torch.int32, device=dev())

@@ -29,7 +29,7 @@ def field(n):
 def run_gpu(f, n, brick, seeds, set_ids=None, h=0.25, max_steps=2000, spr=0, batched=False):
     R = (n // brick) ** 3
     s = stream()
-    bricks = torch.zeros(R * (brick + 4) ** 3 * 8, dtype=torch.float32, device=dev())
+    bricks = torch.zeros(rafi.c2_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     rafi.rf_c2_make_bricks(to_dev(f.reshape(-1)), n, brick, bricks, s)
     cnt = len(seeds)
     out = torch.zeros((cnt, 8), dtype=torch.int32, device=dev())

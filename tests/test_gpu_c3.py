@@ -23,7 +23,7 @@ def gpu_render(vol, cam, brick, w, h, spp, seed=3):
     n = vol.shape[0]
     R = (n // brick) ** 3
     s = stream()
-    bricks = torch.zeros(R * (brick + 2) ** 3 * 4, dtype=torch.float32, device=dev())
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     rafi.rf_c0_make_bricks(to_dev(vol.reshape(-1)), n, brick, bricks, s)
     rayC = torch.zeros(w * h * spp, dtype=torch.float32, device=dev())
     img = torch.zeros(w * h, dtype=torch.float32, device=dev())

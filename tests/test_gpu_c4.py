@@ -24,7 +24,7 @@ def gpu_render(vol, smax, views, brick, spp, batched=True, seed=4):
     n = vol.shape[0]
     R = (n // brick) ** 3
     s = stream()
-    bricks = torch.zeros(R * (brick + 2) ** 3 * 4, dtype=torch.float32, device=dev())
+    bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     dv = to_dev(vol.reshape(-1))
     rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
     del dv
