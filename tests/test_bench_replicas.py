@@ -108,3 +108,27 @@ def test_repeat_for_runs_until_the_time_is_spent():
     calls = []
     r, runs, dt = bench.repeat_for(lambda: calls.append(1) or len(calls), min_s=0.05)
     assert runs == len(calls) == r and dt >= 0.05
+
+
+def test_subset_oracle_legs_on_small_inputs(monkeypatch):
+    """The cpu_baseline leg's streamline and transport subsets: the threaded
+    shards trace exactly the particles and paths of the single-threaded call."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import oracle
+    from paper_2605_30294_gb300 import inputs
+
+    monkeypatch.setattr(bench, "C2_ORACLE_SEEDS", 64)
+    monkeypatch.setattr(bench, "C4_ORACLE_CROP", 8)
+    field, _ = inputs.c2_field(32)
+    seeds = inputs.c2_seeds(640, 32, seed=2)
+    r = bench.oracle_c2_subset(field, seeds, 8)
+    want = int(oracle.c2_trace(field, seeds[::10][:64], 8)["steps"].astype(np.int64).sum())
+    assert r["cores"] == bench.host_threads() and f"{want} particle-steps per run" in r["sample"]
+    assert r["particle_steps_per_s"] > 0
+    vol, smax = inputs.c4_volume(32)
+    view = inputs.c4_views(32, sizes=((16, 16),))[0]
+    t = bench.oracle_c4_subset(vol, smax, view, 2)
+    assert t["paths_per_s"] > 0 and "(128 paths per run)" in t["sample"]
