@@ -382,7 +382,7 @@ rf_status rf_c0_render_graph(rf_ctx *ctx, const float *bricks, const float *cam,
  * along x, both clamped to the grid (so one 32-byte load gives both x corners
  * of a trilinear sample).  Brick of rank r = bx + nb*(by + nb*bz) at
  * bricks + r*(B+4)^3*8 floats; bricks (device, (N/B)^3*(B+4)^3*8 floats) must
- * be 32-byte aligned, else RF_ERR_ARG. */
+ * be 32-byte aligned, else RF_ERR_ARG, here and in the calls that read them. */
 rf_status rf_c2_make_bricks(const float *field, int32_t N, int32_t B, float *bricks, void *stream);
 
 /* Seed (Sec. 5.4 "particles are released at predefined seed points"):

@@ -1105,7 +1105,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     int perSM = 0;
     RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
     if (perSM < W::kMinBlocksPerSM) {
-        // the hint did not leave room for the intended occupancy: let the driver choose
+        // the hint did not leave room for the intended occupancy: leave the carve-out to CUDA
         RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, -1));
         RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
     }
