@@ -381,6 +381,12 @@ def phase_rates(log_rows, item_bytes, min_items=1 << 20):
         out["scatter_gbs_ge_2^20_min_round"] = float(per_round.min())
         round_s = (lg[big, 4] - lg[big, 0]).sum() * 1e-9
         out["round_gbs_ge_2^20"] = float((work_b[big].sum() + scat_b[big].sum()) / round_s / 1e9)
+        # forwarding rate in algorithmic bytes: 2 x itemBytes per item the round
+        # forwards (its n_next), over the whole round, start to second barrier
+        fwd_b = lg[:, 6] * 2 * item_bytes
+        out["fwd_gbs_ge_2^20"] = float(fwd_b[big].sum() / round_s / 1e9)
+        per_fwd = fwd_b[big] / ((lg[big, 4] - lg[big, 0]) * 1e-9) / 1e9
+        out["fwd_gbs_ge_2^20_min_round"] = float(per_fwd.min())
     small = ~big
     if small.any():
         out["us_per_round_lt_2^20"] = float((lg[small, 4] - lg[small, 0]).mean() * 1e-3)
@@ -681,6 +687,35 @@ def run_ours(args):
     barrier()
     e2e_s = time.perf_counter() - t0
 
+    # where the end-to-end time goes: one more step with the persistent kernel
+    # timed on the device (it writes the retired items straight into the pinned
+    # host buffer), and the host-to-device copy of one run's items timed alone
+    rafi.rf_set_timing(ctx.handle, True)
+    rafi.rf_get_timing(ctx.handle, reset=True)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_step()
+    barrier()
+    one_step_s = time.perf_counter() - t0
+    te = rafi.rf_get_timing(ctx.handle, reset=True)
+    rafi.rf_set_timing(ctx.handle, False)
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record(s)
+    retired.copy_(h_items.view(n, 16), non_blocking=True)
+    ev[1].record(s)
+    torch.cuda.synchronize()
+    h2d_ms = ev[0].elapsed_time(ev[1])
+    run_ms = one_step_s * 1e3 / len(MODES)
+    kern_ms = te.roundsMs / max(te.roundsLaunches, 1)
+    e2e_split = {"ms_per_run": run_ms, "h2d_items_ms": h2d_ms,
+                 "h2d_gbs": n * ITEM_BYTES / (h2d_ms * 1e-3) / 1e9,
+                 "rounds_kernel_ms": kern_ms,
+                 "rounds_kernel_ms_device_buffers": tb.roundsMs / max(tb.roundsLaunches, 1),
+                 "rest_ms": run_ms - h2d_ms - kern_ms,
+                 "what": "one run = copy of the items in, seed kernel, persistent kernel writing retired items "
+                         "into the pinned host buffer, read-back of the counts; rest = launches, host calls "
+                         "and synchronisation"}
+
     rays_s, c0_ms, rays_g, c0_ms_g = c0_rays_per_s(torch, rafi, inputs, s)
     ctx.close()
     del d_items, retired, h_items, h_ret
@@ -705,13 +740,17 @@ def run_ours(args):
         return 0
 
     peak, peak_kind = peaks()
-    # persistent kernel: round 0 reads and writes every seeded item (its step);
-    # every round's scatter reads each queued item and writes it once (to its
-    # destination, stepped on arrival, or to the retirement sink).  The queued
-    # items of all rounds of a run are its n seeded items plus its deliveries.
+    # persistent kernel, algorithmic bytes as the forwarding layer counts them:
+    # 2 x itemBytes per forwarded item (an item delivered by a work round's
+    # exchange), so `fwd` items move 128 * fwd bytes over all timed launches.
+    # Also reported: the bytes the kernel actually has to move, the queued
+    # items of every round (each read once and written once, to its next
+    # segment or to the retirement sink) plus the seed exchange's n items.
     runs = tb.roundsLaunches
-    alg_bytes = 2 * ITEM_BYTES * (2 * runs * n + fwd)
+    alg_bytes = 2 * ITEM_BYTES * fwd
     achieved = alg_bytes / (tb.roundsMs * 1e-3) / 1e9 if tb.roundsMs > 0 else 0.0
+    moved_bytes = 2 * ITEM_BYTES * (2 * runs * n + fwd)
+    moved = moved_bytes / (tb.roundsMs * 1e-3) / 1e9 if tb.roundsMs > 0 else 0.0
     p_bytes = tp.scatterItems * 2 * ITEM_BYTES
     p_ach = p_bytes / (tp.scatterMs * 1e-3) / 1e9 if tp.scatterMs > 0 else 0.0
     p_ach_l = (tp.scatterItemsLarge * 2 * ITEM_BYTES / (tp.scatterMsLarge * 1e-3) / 1e9
@@ -733,11 +772,17 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "rounds_kernel<C1Work>", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": rounds_kernel_traffic(),
                      "peak_kind": peak_kind,
+                     "alg_bytes": "2 x 64 B per forwarded item (deliveries of work rounds)",
                      "alg_bytes_per_launch": alg_bytes / max(runs, 1), "launches": runs,
-                     "ms_total": tb.roundsMs},
+                     "ms_total": tb.roundsMs, "ms_per_launch": tb.roundsMs / max(runs, 1),
+                     "frac_rounds_ge_2^20": rates.get("fwd_gbs_ge_2^20", 0.0) / peak,
+                     "moved": {"bytes_per_launch": moved_bytes / max(runs, 1), "achieved": moved,
+                               "frac": moved / peak,
+                               "what": "2 x 64 B per queued item of every round plus the seed exchange"}},
         "phases_from_round_log": {**rates,
                                   "scatter_frac_ge_2^20": rates.get("scatter_gbs_ge_2^20", 0.0) / peak,
-                                  "round_frac_ge_2^20": rates.get("round_gbs_ge_2^20", 0.0) / peak},
+                                  "round_frac_ge_2^20": rates.get("round_gbs_ge_2^20", 0.0) / peak,
+                                  "fwd_frac_ge_2^20": rates.get("fwd_gbs_ge_2^20", 0.0) / peak},
         "per_law": laws_batched,
         "batched_step_in_place": {
             "value": u_fwd / (u_ms / 1e3), "ms_per_step": u_ms / p_steps, "steps": p_steps, "per_law": laws_in_place,
@@ -758,7 +803,7 @@ def run_ours(args):
                   "gpu_launches": p_launches, "clocks": p_clocks},
         "e2e": {"value": e2e_fwd / e2e_s, "unit": "items/s",
                 "h2d_bytes_per_step": len(MODES) * n * ITEM_BYTES,
-                "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8)},
+                "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8), "split": e2e_split},
         "rays_per_s": {"value": rays_s, "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
                        "ms_per_frame": c0_ms, "form": "host loop (rf_c0_render)",
                        "graph": {"value": rays_g, "ms_per_frame": c0_ms_g,
@@ -778,9 +823,10 @@ def run_ours(args):
 
 
 def run_section(args):
-    """One workload kernel's host loop alone, at a size for a profiler capture (a few
-    GB on the device, each workload launched once, no warm-up), printing one JSON
-    line of its own (not the bench line):
+    """One workload alone, at a size for a profiler capture (a few GB on the
+    device, each workload launched once, no warm-up), printing one JSON line of
+    its own (not the bench line):
+      c1: the microbenchmark, one rf_c1_run_batched call (one persistent launch);
       c2: streamlines, 512^3 field in 4x4x4 bricks, 2^18 seeds, until brick exit;
       c3: EA renderer at its configured size, one forward and one adjoint render;
       c4: delta tracking, 512^3 noise in 4x4x4 bricks, one 512x512 view at 16 spp."""
@@ -793,7 +839,30 @@ def run_section(args):
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {"section": args.section}
-    if args.section == "c2":
+    if args.section == "c1":
+        # one persistent-kernel launch of the microbenchmark (steps on arrival),
+        # one destination law, no warm-up: the launch a profiler captures
+        n = args.items
+        items = inputs.c1_items(n, seed=SEED)
+        d_items = torch.from_numpy(items.view(np.int32)).cuda()
+        retired = torch.zeros((n, 16), dtype=torch.int32, device="cuda")
+        log = torch.zeros(7 * LOG_CAP, dtype=torch.int64, device="cuda")
+        with rafi.Context(RANKS, ITEM_BYTES, n) as ctx:
+            e0.record(s)
+            st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, d_items, n, SEED, args.law, 1.1, GRID, retired,
+                                                          stream=s, round_log=log, round_log_cap=LOG_CAP)
+            e1.record(s)
+            torch.cuda.synchronize()
+        lg = log.cpu().numpy().reshape(-1, 7)
+        rows = [r for r in lg if r[0] > 0]
+        out.update(workload=f"microbenchmark, {n} x 64 B items, 64 ranks, law {LAW_NAMES[args.law]}, one "
+                            f"rf_c1_run_batched call", items=n, ms=e0.elapsed_time(e1), rounds=rounds, forwarded=fwd,
+                   retired=cnt, phases=phase_rates(rows, ITEM_BYTES))
+        if args.round_log:
+            with open(args.round_log, "w") as f:
+                json.dump({"columns": ["t_start", "t_count_end", "t_barrier1", "t_scatter_end", "t_barrier2",
+                                       "n_in", "n_next"], "rows": [[int(x) for x in r] for r in rows]}, f)
+    elif args.section == "c2":
         n, brick, count = 512, 128, 1 << 18
         R = (n // brick) ** 3
         field, _ = inputs.c2_field(n)
@@ -868,8 +937,11 @@ def main():
     ap.add_argument("--items", type=int, default=N_ITEMS)
     ap.add_argument("--skip-extra", action="store_true",
                     help="leave out the streamline, differentiable and transport workloads")
-    ap.add_argument("--section", choices=["c2", "c3", "c4"], default=None,
-                    help="run one workload's host loop alone at a profiling size and print its own JSON line")
+    ap.add_argument("--section", choices=["c1", "c2", "c3", "c4"], default=None,
+                    help="run one workload alone at a profiling size and print its own JSON line (c1: one "
+                         "persistent-kernel launch of the microbenchmark at --items; c2-c4: a host loop)")
+    ap.add_argument("--law", type=int, default=0, choices=list(MODES), help="destination law of --section c1")
+    ap.add_argument("--round-log", default=None, help="--section c1: write the kernel's round log to this JSON file")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

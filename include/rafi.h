@@ -195,6 +195,19 @@ rf_status rf_restore(rf_ctx *ctx, const void *items, const uint32_t *offsets, ui
 rf_status rf_set_timing(rf_ctx *ctx, int32_t enable);
 rf_status rf_get_timing(rf_ctx *ctx, rf_phase_times *out, int32_t reset);
 
+/* Bounds of the persistent round kernels' grid-barrier waits on this context
+ * (the batched form, rf_c1_run_batched and the batched streamline and
+ * transport runs).  Every such wait gives up after spinCycles SM clock cycles
+ * (0 restores the default of 10^9, about half a second), raises an abort flag
+ * that every other CTA sees at its next wait, and the call returns
+ * RF_ERR_TIMEOUT with the context still usable: the next call reseeds it.
+ * missingArrivals (normally 0) makes each grid barrier wait for that many CTAs
+ * beyond the grid, which never arrive, so that every wait runs out: a way to
+ * drive the timeout path on a real GPU without any fault.  The paper has no
+ * counterpart (its only failure mode is the dropped emit of Sec. 3.3).
+ * RF_ERR_ARG for spinCycles above 2^40 or missingArrivals above 1024. */
+rf_status rf_set_wait_limits(rf_ctx *ctx, uint64_t spinCycles, uint32_t missingArrivals);
+
 /* Kernels this library launched in this process so far (all contexts). */
 uint64_t rf_launch_count(void);
 
@@ -206,10 +219,9 @@ const char *rf_last_error(void);
 /* Stable partition of n items by destination into caller buffers, without
  * allocating anything.  The paper has no counterpart to this entry point.
  *
- * It exists for callers that must not allocate device memory once they are
- * running: code that issues work while a CUDA graph is being captured (an
- * allocation there is an error), latency-critical loops whose memory budget
- * is fixed at start-up (an allocation can stall the whole device), and hosts
+ * It exists for callers that must not call cudaMalloc once they are
+ * running: latency-critical loops whose memory budget is fixed at start-up
+ * (an allocation can synchronise and stall the whole device), and hosts
  * whose own caching allocator already owns almost all device memory (a fresh
  * allocation can fail while the host's pool still has room).
  *
@@ -219,7 +231,10 @@ const char *rf_last_error(void);
  * receives the segment offsets.  dest == -1 marks an empty slot (skipped);
  * other destinations outside [0, numRanks) are dropped.  statsOut (device,
  * 4 words, may be NULL) receives {delivered, empty slots, dropped, status}.
- * items (n x itemBytes) and dest (n int32) are device memory.
+ * items (n x itemBytes) and dest (n int32) are device memory.  items and
+ * itemsOut must be 16-byte aligned and must not overlap (no in-place call);
+ * dest and offsetsOut must be 4-byte aligned, statsOut 8-byte aligned.  A
+ * call that breaks one of these rules returns RF_ERR_ARG before any launch.
  *
  * Scratch: one file-scope device array of 8 MiB, which every device that
  * loads the library holds until the process exits.  numRanks x ceil(n /

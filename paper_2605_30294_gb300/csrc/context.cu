@@ -489,6 +489,18 @@ rf_status rf_get_timing(rf_ctx *ctx, rf_phase_times *out, int32_t reset)
     return st;
 }
 
+rf_status rf_set_wait_limits(rf_ctx *ctx, uint64_t spinCycles, uint32_t missingArrivals)
+{
+    if (rf_status st = check_ctx(ctx, "rf_set_wait_limits")) return st;
+    if (spinCycles > (1ull << 40) || missingArrivals > 1024u) {
+        set_error("rf_set_wait_limits: spinCycles above 2^40 or missingArrivals above 1024");
+        return RF_ERR_ARG;
+    }
+    ctx->waitLimitCycles = spinCycles;
+    ctx->missingArrivals = missingArrivals;
+    return RF_OK;
+}
+
 uint64_t rf_launch_count(void) { return g_launches.load(); }
 
 const char *rf_last_error(void) { return g_err; }

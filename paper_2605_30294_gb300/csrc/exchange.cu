@@ -800,6 +800,21 @@ extern "C" rf_status rf_partition_static(const void *items, const int32_t *dest,
                   "n below 2^31, non-NULL buffers)", RF_MAX_RANKS, RF_MAX_ITEM_BYTES);
         return RF_ERR_ARG;
     }
+    // The scatter stages input tiles with bulk copies and stores 16-byte
+    // vectors: both item buffers must be 16-byte aligned, and they must not
+    // overlap (other CTAs write output while a tile is still being read).
+    const uintptr_t pi = reinterpret_cast<uintptr_t>(items), po = reinterpret_cast<uintptr_t>(itemsOut);
+    const uint64_t span = n * (uint64_t)itemBytes;
+    if (n && (((pi | po) & 15u) || (reinterpret_cast<uintptr_t>(dest) & 3u) ||
+              (reinterpret_cast<uintptr_t>(statsOut) & 7u) || (pi < po + span && po < pi + span))) {
+        set_error("rf_partition_static: items and itemsOut must be 16-byte aligned and must not overlap, dest "
+                  "4-byte and statsOut 8-byte aligned");
+        return RF_ERR_ARG;
+    }
+    if (reinterpret_cast<uintptr_t>(offsetsOut) & 3u) {
+        set_error("rf_partition_static: offsetsOut must be 4-byte aligned");
+        return RF_ERR_ARG;
+    }
     const ScatterChoice c = pick_scatter(itemBytes);
     const uint32_t tileItems = 256u * c.k;
     const uint64_t tiles = (n + tileItems - 1) / tileItems;

@@ -79,6 +79,9 @@ struct rf_ctx {
     uint32_t *zipfThr = nullptr;  // numRanks words: Zipf table of the microbenchmark
     double zipfS = -1.0;           // exponent the table was built for
 
+    unsigned long long waitLimitCycles = 0;  // bound of the persistent kernel's barrier waits (0: kSpinLimitCycles)
+    uint32_t missingArrivals = 0;            // > 0 only to exercise the timeout path
+
     bool timing = false;
     unsigned pendingSlots = 0;  // timing slots recorded since the last read-back
     cudaEvent_t ev[10] = {};

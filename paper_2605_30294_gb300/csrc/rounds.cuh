@@ -39,15 +39,13 @@
 
 namespace rfi {
 
-constexpr int kSyncGroups = 16;  // first level of the grid barrier
+constexpr int kSyncGroups = 16;  // runs of consecutive CTAs whose destination counts are summed per round
 
 struct GridSync {
-    unsigned int count;  // groups complete at the current barrier
-    unsigned int gen;    // barrier generation
-    unsigned int abort;  // set by a CTA whose wait gave up
+    unsigned int count;    // arrivals at grid barriers so far
+    unsigned int abort;    // set by a CTA whose wait gave up
     unsigned int work[2];  // work-phase chunk counters (round parity), dynamic policies
-    unsigned int pad[27];
-    unsigned int group[kSyncGroups][32];  // CTAs arrived per group, one 128-byte line each
+    unsigned int pad[28];
 };
 
 struct RoundsArgs {
@@ -67,6 +65,8 @@ struct RoundsArgs {
     unsigned long long *retiredCountOut;
     unsigned long long *seedCount;  // nullable: start from a seeded out-queue of this many items (kFuseStep)
     const uint4 *seedItems;         // nullable: the seeded items, read in place instead of from the out-queue
+    long long spinLimit;       // bound of every grid-barrier wait, in SM clock cycles
+    uint32_t missingArrivals;  // CTAs a grid barrier waits for beyond the grid (0; > 0 only to test timeouts)
     uint32_t maxRounds;
     uint32_t roundLogCap;
     uint32_t fuseStep;  // apply steps on arrival (policies with kFuseStep)
@@ -144,58 +144,40 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsign
 }
 
 // Bounded grid barrier for a cooperative launch (all CTAs resident).
-// Counters only grow (the launch zeroes them): barrier number `seq` (0, 1,
-// ...) is complete once the counter reaches G * (seq + 1), so nothing is
-// ever reset.  kFlatBarrier: every CTA adds to one counter and waits for it
-// to reach the target (one atomic and one load on the critical path).
-// Otherwise, in two levels: CTAs arrive on one of kSyncGroups group
-// counters (separate cache lines), the last of a group on the top counter,
-// and the last group publishes the sequence number.  Arrivals are release
+// The counter only grows (the launch zeroes it): barrier number `seq` (0, 1,
+// ...) is complete once it reaches (G + missing) * (seq + 1), so nothing is
+// ever reset.  Every CTA adds to the one counter and waits for the target
+// (one atomic and one load on the critical path).  Arrivals are release
 // operations and the waits acquire loads, which orders every CTA's writes
-// before the barrier with every read after it.
+// before the barrier with every read after it.  `missing` is 0 in normal
+// runs; a positive value names CTAs that never arrive, so every wait runs
+// out after `limit` cycles (the timeout path, exercised without a fault).
+// A wait that runs out raises the abort flag; every CTA that sees it gives up.
 // Returns false when any CTA has given up; the caller must then return.
-constexpr bool kFlatBarrier = true;
+__device__ inline bool barrier_wait_bounded(GridSync *gs, unsigned int target, long long limit)
+{
+    const long long t0 = clock64();
+    for (unsigned int k = 0; ld_acquire(&gs->count) < target; ++k) {
+        if ((k & 15u) == 15u) {
+            if (ld_acquire(&gs->abort)) return false;
+            if (clock64() - t0 > limit) {
+                atomicExch(&gs->abort, 1u);
+                return false;
+            }
+        }
+        __nanosleep(20);
+    }
+    return true;
+}
 
-__device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned int seq)
+__device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned int seq, long long limit,
+                                    unsigned int missing)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned int ok = 1;
-        const unsigned int G = gridDim.x;
-        unsigned int *watch;
-        unsigned int target;
-        bool last = false;
-        if (kFlatBarrier) {
-            watch = &gs->count;
-            target = G * (seq + 1u);
-            last = atom_add_release(watch, 1u) + 1u == target;
-        } else {
-            const unsigned int groups = G < (unsigned)kSyncGroups ? G : (unsigned)kSyncGroups;
-            const unsigned int grp = blockIdx.x % groups;
-            const unsigned int members = G / groups + (grp < G % groups ? 1u : 0u);
-            watch = &gs->gen;
-            target = seq + 1u;
-            if (atom_add_release(&gs->group[grp][0], 1u) + 1u == members * (seq + 1u))
-                last = atom_add_acq_rel(&gs->count, 1u) + 1u == groups * (seq + 1u);
-            if (last) st_release(&gs->gen, seq + 1u);
-        }
-        if (!last) {
-            const long long t0 = clock64();
-            for (unsigned int k = 0; ld_acquire(watch) < target; ++k) {
-                if ((k & 15u) == 15u) {
-                    if (ld_acquire(&gs->abort)) {
-                        ok = 0;
-                        break;
-                    }
-                    if (clock64() - t0 > kSpinLimitCycles) {
-                        atomicExch(&gs->abort, 1u);
-                        ok = 0;
-                        break;
-                    }
-                }
-                __nanosleep(20);
-            }
-        }
+        const unsigned int target = (gridDim.x + missing) * (seq + 1u);
+        const bool last = atom_add_release(&gs->count, 1u) + 1u == target;
+        unsigned int ok = last ? 1u : (barrier_wait_bounded(gs, target, limit) ? 1u : 0u);
         if (ld_acquire(&gs->abort)) ok = 0;
         *sFlag = ok;
     }
@@ -208,35 +190,20 @@ __device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned 
 // to the counter, its earlier writes released) returns whether this CTA
 // arrived last; grid_wait (all threads) waits for the rest, bounded, and
 // returns false when any CTA has given up.
-__device__ inline void grid_arrive(GridSync *gs, unsigned int seq, unsigned int *sLast)
+__device__ inline void grid_arrive(GridSync *gs, unsigned int seq, unsigned int *sLast, unsigned int missing)
 {
     __syncthreads();
-    if (threadIdx.x == 0) *sLast = atom_add_release(&gs->count, 1u) + 1u == gridDim.x * (seq + 1u) ? 1u : 0u;
+    if (threadIdx.x == 0)
+        *sLast = atom_add_release(&gs->count, 1u) + 1u == (gridDim.x + missing) * (seq + 1u) ? 1u : 0u;
 }
 
-__device__ inline bool grid_wait(GridSync *gs, unsigned int *sFlag, unsigned int seq, const unsigned int *sLast)
+__device__ inline bool grid_wait(GridSync *gs, unsigned int *sFlag, unsigned int seq, const unsigned int *sLast,
+                                 long long limit, unsigned int missing)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int ok = 1;
-        const unsigned int target = gridDim.x * (seq + 1u);
-        if (!*sLast) {
-            const long long t0 = clock64();
-            for (unsigned int k = 0; ld_acquire(&gs->count) < target; ++k) {
-                if ((k & 15u) == 15u) {
-                    if (ld_acquire(&gs->abort)) {
-                        ok = 0;
-                        break;
-                    }
-                    if (clock64() - t0 > kSpinLimitCycles) {
-                        atomicExch(&gs->abort, 1u);
-                        ok = 0;
-                        break;
-                    }
-                }
-                __nanosleep(20);
-            }
-        }
+        if (!*sLast) ok = barrier_wait_bounded(gs, (gridDim.x + missing) * (seq + 1u), limit) ? 1u : 0u;
         if (ld_acquire(&gs->abort)) ok = 0;
         *sFlag = ok;
     }
@@ -521,7 +488,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     bool solo = false;
     unsigned int barrierSeq = 0;  // grid barriers passed (every CTA passes the same ones)
     auto round_barrier = [&]() -> bool {
-        if (!solo) return grid_barrier(a.sync, sFlag, barrierSeq++);
+        if (!solo) return grid_barrier(a.sync, sFlag, barrierSeq++, a.spinLimit, a.missingArrivals);
         __threadfence();
         __syncthreads();
         return true;
@@ -887,8 +854,8 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         int myD0[kK];
         uint32_t myR0[kK];
         bool earlyDone = false;
-        if (kFlatBarrier && !solo && prefetched) {
-            grid_arrive(a.sync, barrierSeq, sFlag + 1);
+        if (!solo && prefetched) {
+            grid_arrive(a.sync, barrierSeq, sFlag + 1, a.missingArrivals);
             for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
             __syncwarp();
             if (!wait(0)) {
@@ -897,7 +864,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 rank_a(sBuf, sDst, min(kTile, hi - lo), fuse, q, myD0, myR0);
                 earlyDone = true;
             }
-            const bool ok = grid_wait(a.sync, sFlag, barrierSeq++, sFlag + 1);
+            const bool ok = grid_wait(a.sync, sFlag, barrierSeq++, sFlag + 1, a.spinLimit, a.missingArrivals);
             if (failed || !ok) {
                 failed = true;
                 break;
@@ -1140,6 +1107,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.seedCount = seeded ? &ctx->dev->outCount : nullptr;
     a.seedItems = seeded ? static_cast<const uint4 *>(seedItems) : nullptr;
     a.fuseStep = stepOnArrival ? 1u : 0u;
+    a.spinLimit = ctx->waitLimitCycles ? (long long)ctx->waitLimitCycles : kSpinLimitCycles;
+    a.missingArrivals = ctx->missingArrivals;
     a.maxRounds = maxRounds;
     a.numRanks = R;
     RF_CUDA(cudaMemsetAsync(base + totBytes, 0, tailBytes, s));

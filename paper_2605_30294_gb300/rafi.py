@@ -74,6 +74,7 @@ _SIGS = {
     "rf_restore": [_P, _P, _P, _u64, _P],
     "rf_set_timing": [_P, _i32],
     "rf_get_timing": [_P, ctypes.POINTER(rf_phase_times), _i32],
+    "rf_set_wait_limits": [_P, _u64, _u32],
     "rf_launch_count": [],
     "rf_last_error": [],
     "rf_partition_static": [_P, _P, _u64, _u32, _i32, _P, _P, _P, _P],
@@ -165,6 +166,10 @@ def rf_last_error() -> str:
     return lib().rf_last_error().decode()
 
 
+def rf_set_wait_limits(ctx: int, spin_cycles: int = 0, missing_arrivals: int = 0) -> None:
+    _check("rf_set_wait_limits", lib().rf_set_wait_limits(ctx, spin_cycles, missing_arrivals))
+
+
 def rf_launch_count() -> int:
     return int(lib().rf_launch_count())
 
@@ -240,6 +245,12 @@ def rf_get_timing(ctx: int, reset: bool = False, allow=()) -> rf_phase_times:
 def rf_partition_static(items, dest, n: int, item_bytes: int, num_ranks: int, items_out, offsets_out,
                         stats_out=None, stream=None) -> None:
     """Allocation-free stable partition into caller buffers (see rafi.h)."""
+    fn = "rf_partition_static"
+    _need(items, n * item_bytes, fn, "items")
+    _need(items_out, n * item_bytes, fn, "items_out")
+    _need(dest, n * 4, fn, "dest")
+    _need(offsets_out, (max(num_ranks, 0) + 1) * 4, fn, "offsets_out")
+    _need(stats_out, 32, fn, "stats_out")
     _check("rf_partition_static", lib().rf_partition_static(ptr(items), ptr(dest), n, item_bytes, num_ranks,
                                                             ptr(items_out), ptr(offsets_out), ptr(stats_out),
                                                             stream_handle(stream)))

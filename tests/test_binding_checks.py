@@ -49,3 +49,48 @@ def test_readers_refuse_short_bricks(call):
         else:
             rafi.rf_c4_render(0, short, n, b, 1.0, [([0.0] * 12, 4, 4)], 1, 4, short)
     assert e.value.status == rafi.RF_ERR_ARG
+
+
+@pytest.mark.parametrize("short", ["items", "items_out", "dest", "offsets_out", "stats_out"])
+def test_static_partition_refuses_short_buffers(short):
+    n, ib, R = 100, 48, 7
+    bufs = dict(items=np.zeros(n * ib, np.uint8), items_out=np.zeros(n * ib, np.uint8),
+                dest=np.zeros(n, np.int32), offsets_out=np.zeros(R + 1, np.int32), stats_out=np.zeros(4, np.int64))
+    bufs[short] = bufs[short][:-1]
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_partition_static(bufs["items"], bufs["dest"], n, ib, R, bufs["items_out"], bufs["offsets_out"],
+                                 bufs["stats_out"])
+    assert e.value.status == rafi.RF_ERR_ARG and short in str(e.value)
+
+
+@pytest.mark.parametrize("case", ["items_unaligned", "out_unaligned", "overlap", "in_place", "dest_unaligned",
+                                  "offsets_unaligned", "stats_unaligned"])
+def test_static_partition_refuses_misaligned_or_overlapping_pointers(case):
+    # plain integers stand for device addresses: the library rejects them by
+    # arithmetic alone and returns before any CUDA call, so no GPU is needed
+    n, ib, R = 4, 16, 2
+    items, out, dest, off, stats = 0x100000, 0x200000, 0x300000, 0x400000, 0x500000
+    if case == "items_unaligned":
+        items += 8
+    elif case == "out_unaligned":
+        out += 4
+    elif case == "overlap":
+        out = items + 16
+    elif case == "in_place":
+        out = items
+    elif case == "dest_unaligned":
+        dest += 2
+    elif case == "offsets_unaligned":
+        off += 1
+    else:
+        stats += 4
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_partition_static(items, dest, n, ib, R, out, off, stats)
+    assert e.value.status == rafi.RF_ERR_ARG
+    assert "aligned" in rafi.rf_last_error()
+
+
+def test_wait_limits_refuse_a_null_context_and_wild_values():
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_set_wait_limits(0, 1000, 0)
+    assert e.value.status == rafi.RF_ERR_ARG

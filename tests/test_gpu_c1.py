@@ -106,7 +106,7 @@ def test_round_queues_match_oracle(mode, deterministic):
 def test_full_size_sampled_parity():
     # the bench workload: 2^24 items x 64 B, 64 ranks, each destination law
     n, seed = 1 << 24, 1
-    items = inputs.c1_items(n, seed=seed)
+    items = _full_items()
     d_items = to_dev(items)
     s = stream()
     rng = np.random.default_rng(0)
@@ -318,23 +318,97 @@ def test_batched_rank_count_extremes_and_empty(fuse, ranks, grid, n):
             np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
 
 
-def test_batched_full_size_matches_plain():
+_FULL = {}
+
+
+def _full_items():
+    """The bench's 2^24 seeded items (generated once per test session)."""
+    if "items" not in _FULL:
+        _FULL["items"] = inputs.c1_items(1 << 24, seed=1)
+    return _FULL["items"]
+
+
+def _by_key(a: np.ndarray) -> np.ndarray:
+    """Rows ordered by (w0, w1), which identifies an item (checked by the caller)."""
+    key = (a[:, 0].astype(np.uint64) << np.uint64(32)) | a[:, 1].astype(np.uint64)
+    return a[np.argsort(key, kind="stable")]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_full_size_every_word_matches_oracle(mode):
+    # The benched configuration, checked word for word: 2^24 x 64 B items over
+    # 64 ranks.  The batched forms retire items in the serial round-by-round
+    # order (round by round, queue order within a round), so their retirement
+    # buffers must equal the oracle's queue simulation row for row, all 16
+    # words; the plain host loop appends in scheduling order and is compared
+    # as a multiset.  4096 sampled items are also walked one by one.
     n, seed = 1 << 24, 1
-    items = inputs.c1_items(n, seed=seed)
+    items = _full_items()
+    want = oracle.c1_rounds(items, R, seed, mode, grid=GRID)
+    want_rounds, want_fwd = int(want["rounds"]), int(want["active"][1:].sum())
+    want_items = want["retired_items"]
     d_items = to_dev(items)
     s = stream()
     with rafi.Context(R, 64, n) as ctx:
-        ra = torch.zeros((n, 16), dtype=torch.int32, device=dev())
-        rb = torch.zeros((n, 16), dtype=torch.int32, device=dev())
-        rc = torch.zeros((n, 16), dtype=torch.int32, device=dev())
-        for mode in MODES:
-            st, ca, roa, fa = rafi.rf_c1_run(ctx.handle, d_items, n, seed, mode, 1.1, GRID, ra, stream=s)
-            st, cb, rob, fb = rafi.rf_c1_run_batched(ctx.handle, d_items, n, seed, mode, 1.1, GRID, rb, stream=s)
-            st, cc, roc, fc = rafi.rf_c1_run_batched(ctx.handle, d_items, n, seed, mode, 1.1, GRID, rc, stream=s,
-                                                     step_on_arrival=False)
-            assert (ca, roa, fa) == (cb, rob, fb) == (cc, roc, fc) and ca == n
-            # both batched forms retire in the same deterministic order
-            assert torch.equal(rb, rc)
-            ka = canonical_rows(ra.cpu().numpy().view(np.uint32)[:, [0, 1, 13, 14, 15]])
-            kb = canonical_rows(rb.cpu().numpy().view(np.uint32)[:, [0, 1, 13, 14, 15]])
-            np.testing.assert_array_equal(ka, kb)
+        ret = torch.zeros((n, 16), dtype=torch.int32, device=dev())
+        for fuse in (True, False):
+            ret.fill_(-1)
+            st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, d_items, n, seed, mode, 1.1, GRID, ret,
+                                                          stream=s, step_on_arrival=fuse)
+            assert st == rafi.RF_OK and cnt == n
+            assert (rounds, fwd) == (want_rounds, want_fwd)
+            got = ret.cpu().numpy().view(np.uint32)
+            bad = np.flatnonzero(np.any(got != want_items, axis=1))
+            assert bad.size == 0, f"step_on_arrival={fuse}: {bad.size} rows differ, first at {bad[:4]}"
+        ret.zero_()
+        st, cnt, rounds, fwd = rafi.rf_c1_run(ctx.handle, d_items, n, seed, mode, 1.1, GRID, ret, stream=s)
+        assert st == rafi.RF_OK and cnt == n and (rounds, fwd) == (want_rounds, want_fwd)
+        plain = ret.cpu().numpy().view(np.uint32)
+    wk = _by_key(want_items)
+    key = (wk[:, 0].astype(np.uint64) << np.uint64(32)) | wk[:, 1].astype(np.uint64)
+    assert np.all(np.diff(key) > 0)  # (w0, w1) identifies an item
+    np.testing.assert_array_equal(_by_key(plain), wk)
+    # sampled items walked one by one through the unpartitioned definition
+    sample = np.random.default_rng(mode).choice(n, size=4096, replace=False)
+    final, _, unfinished, _ = oracle.c1_walk(items[sample], R, seed, mode, grid=GRID,
+                                             start_ranks=(sample % R).astype(np.int32))
+    assert unfinished == 0
+    skey = (final[:, 0].astype(np.uint64) << np.uint64(32)) | final[:, 1].astype(np.uint64)
+    np.testing.assert_array_equal(wk[np.searchsorted(key, skey)], final)
+
+
+@pytest.mark.parametrize("fuse", [True, False], ids=["step_on_arrival", "step_in_place"])
+@pytest.mark.parametrize("mode", MODES)
+def test_batched_2m_items_ordered_retirements(mode, fuse):
+    # 2^21 items: rounds above 2^20 items and tens of tiles per CTA; the whole
+    # retirement buffer equals the oracle's round-by-round order, every word
+    n, seed = 1 << 21, 21
+    items = inputs.c1_items(n, seed=seed)
+    want = oracle.c1_rounds(items, R, seed, mode, grid=GRID)
+    got, rounds, fwd, st = _run_batched(items, seed, mode, fuse=fuse)
+    assert st == rafi.RF_OK and len(got) == n
+    assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
+    np.testing.assert_array_equal(got, want["retired_items"])
+
+
+@pytest.mark.parametrize("fuse", [True, False], ids=["step_on_arrival", "step_in_place"])
+def test_batched_barrier_timeout_is_reported_and_the_context_recovers(fuse):
+    # Each grid barrier waits for one CTA that does not exist, with a bound of
+    # 2 * 10^4 cycles: every wait runs out, the abort flag stops every CTA and
+    # the call returns RF_ERR_TIMEOUT (no fault, nothing left running).  The
+    # same context then runs normally and matches the oracle.
+    n, seed = 300007, 31
+    items = inputs.c1_items(n, seed=seed)
+    final, hops, _, _ = oracle.c1_walk(items, R, seed, rafi.RF_C1_NBR6, grid=GRID)
+    with rafi.Context(R, 64, n) as ctx:
+        rafi.rf_set_wait_limits(ctx.handle, 20000, 1)
+        for _ in range(2):
+            got, rounds, fwd, st = _run_batched(items, seed, rafi.RF_C1_NBR6, ctx=ctx, fuse=fuse,
+                                                allow=(rafi.RF_ERR_TIMEOUT,))
+            assert st == rafi.RF_ERR_TIMEOUT
+            assert "gave up" in rafi.rf_last_error()
+        rafi.rf_set_wait_limits(ctx.handle, 0, 0)
+        got, rounds, fwd, st = _run_batched(items, seed, rafi.RF_C1_NBR6, ctx=ctx, fuse=fuse)
+        assert st == rafi.RF_OK and len(got) == n
+        assert rounds == int(hops.max()) + 1 and fwd == int(hops.sum())
+        np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
