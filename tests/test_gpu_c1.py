@@ -412,3 +412,17 @@ def test_batched_barrier_timeout_is_reported_and_the_context_recovers(fuse):
         assert st == rafi.RF_OK and len(got) == n
         assert rounds == int(hops.max()) + 1 and fwd == int(hops.sum())
         np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n", [20011, 300007, 1 << 20])
+def test_batched_retirements_in_the_oracle_order(mode, n):
+    # the persistent kernel retires items in the serial round-by-round order:
+    # its retirement buffer equals the oracle's queue simulation, every word
+    seed = 41
+    items = inputs.c1_items(n, seed=seed)
+    want = oracle.c1_rounds(items, R, seed, mode, grid=GRID)
+    got, rounds, fwd, st = _run_batched(items, seed, mode)
+    assert st == rafi.RF_OK and len(got) == n
+    assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
+    np.testing.assert_array_equal(got, want["retired_items"])

@@ -81,6 +81,8 @@ def test_static_partition_matches_exchange_on_two_calls_in_a_row():
 def test_static_partition_rejects_requests_beyond_its_scratch():
     n, R = 1 << 30, 1024
     with pytest.raises(rafi.RafiError) as e:
-        rafi.rf_partition_static(1, 1, n, 16, R, 1, 1, None, 0)
+        # aligned, non-overlapping stand-in addresses: only the size is wrong, and the
+        # library refuses it before touching any of them
+        rafi.rf_partition_static(1 << 40, 1 << 39, n, 16, R, 1 << 41, 1 << 38, None, 0)
     assert e.value.status == rafi.RF_ERR_ARG
     assert "static scratch" in rafi.rf_last_error()
