@@ -426,13 +426,34 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3, cpu=None):
                        f"{len(sizes)} uneven seed sets ({sizes[0]}..{sizes[-1]}, {count} particles) in one launch, "
                        f"RK4 h=0.25, <= 2000 steps",
            "particles": count}
+    from paper_2605_30294_gb300 import autotune
+
+    # the autotuner's sample: every 4th particle of the 16 seed sets
+    d_seeds_s = d_seeds[::4].contiguous()
+    d_sets_s = d_sets[::4].contiguous()
+    ns = int(d_seeds_s.shape[0])
     with rafi.Context(R, 32, count) as ctx:
         # steps per round: 0 = until a particle leaves its brick; 1 = the paper's
         # pattern (one RK step per round, every particle forwarded every round)
         for spr, nrep in ((0, reps), (1, 1)):
             key = "brick_exit" if spr == 0 else "one_step_per_round"
             res[key] = {}
-            for batched in (1, 0, 2):
+
+            def sample(form, spr=spr):
+                rafi.rf_c2_run(ctx.handle, bricks, d_seeds_s, d_sets_s, ns, n, brick, 0.25, 2000, spr, out,
+                               rafi.RF_FORM_TUNED, stream=s)
+
+            res[key]["autotune"] = autotune.tune(
+                ctx.handle, rafi.RF_POLICY_STREAMLINES, sample, item_bytes=32, ranks=R, n=ns,
+                tag=f"steps_per_round={spr}", forms=(rafi.RF_FORM_HOST_LOOP, rafi.RF_FORM_PERSISTENT,
+                                                      rafi.RF_FORM_GRAPH), reps=1, stream=s)
+            res[key]["autotune"]["sample"] = f"every 4th particle ({ns} of {count})"
+            for batched in (rafi.RF_FORM_PERSISTENT, rafi.RF_FORM_HOST_LOOP, rafi.RF_FORM_GRAPH, rafi.RF_FORM_TUNED):
+                if batched == rafi.RF_FORM_PERSISTENT:
+                    rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_STREAMLINES, rafi.RF_FORM_PERSISTENT, 0)
+                elif batched == rafi.RF_FORM_TUNED:
+                    t = res[key]["autotune"]
+                    rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_STREAMLINES, t["form"], t["shape"])
                 for _ in range(2 if spr == 0 else 1):
                     rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, spr, out,
                                    batched, stream=s)
@@ -448,11 +469,12 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3, cpu=None):
                 torch.cuda.synchronize()
                 sec = e0.elapsed_time(e1) / 1e3 / nrep
                 steps = int(out[:, 4].cpu().numpy().view(np.uint32).astype(np.int64).sum())
-                res[key][("plain", "batched", "graph")[batched]] = {
+                res[key][("plain", "batched", "graph", "tuned")[batched]] = {
                     "ms_per_run": sec * 1e3, "particle_steps_per_s": steps / sec,
                     "items_forwarded_per_s": fwd / nrep / sec, "rounds": rounds, "particle_steps": steps}
             res[key]["batched_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["batched"]["ms_per_run"]
             res[key]["graph_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["graph"]["ms_per_run"]
+            res[key]["tuned_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["tuned"]["ms_per_run"]
     if cpu is not None:  # the cpu_baseline leg: the oracle on a subset of the seeds
         cpu["streamlines_subset"] = oracle_c2_subset(field, seeds, brick)
     return res
@@ -470,15 +492,17 @@ def c3_ea(torch, rafi, inputs, s, reps=5):
     rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
     nr = w * h * spp
     rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
+    rayClo = torch.zeros(nr, dtype=torch.float32, device="cuda")
     img = torch.zeros(w * h, dtype=torch.float32, device="cuda")
     gimg = torch.ones(w * h, dtype=torch.float32, device="cuda")
     grad = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
-    out = {"workload": "256^3 blob density, 2x2x2 ranks of 128^3, 512x512 at 4 spp (1,048,576 rays)"}
+    out = {"workload": "256^3 blob density, 2x2x2 ranks of 128^3, 512x512 at 4 spp (1,048,576 rays); forward "
+                       "and adjoint as the autograd wrapper runs them (compensated colour sums)"}
     with rafi.Context(8, 64, nr) as ctx:
         for name, fn in (("forward", lambda: rafi.rf_c3_render(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
-                                                                rayC, img, stream=s)),
+                                                                rayC, img, stream=s, ray_c_lo=rayClo)),
                          ("adjoint", lambda: rafi.rf_c3_adjoint(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
-                                                                 rayC, gimg, grad, stream=s))):
+                                                                 rayC, gimg, grad, stream=s, ray_c_lo=rayClo))):
             fn()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -508,8 +532,24 @@ def c4_transport(torch, rafi, inputs, s, cpu=None):
     out = {"workload": "1024^3 fractal gradient noise (6 octaves), mean optical depth 8, 8x8x8 ranks of 128^3, "
                        "views 2048^2, 1024x768, 512^2, 3840x2160 at 16 spp, albedo 0.8, HG g=0.3, <= 64 bounces",
            "paths": paths}
+    from paper_2605_30294_gb300 import autotune
+
     with rafi.Context(512, 64, paths) as ctx:
-        for batched in (1, 0, 2):
+        # the autotuner's sample: the four views at 4 of the 16 paths per pixel
+        def sample(form):
+            rafi.rf_c4_render(ctx.handle, bricks, n, brick, smax, views, 4, 4, score, rafi.RF_FORM_TUNED, stream=s)
+
+        out["autotune"] = autotune.tune(ctx.handle, rafi.RF_POLICY_TRANSPORT, sample, item_bytes=64, ranks=512,
+                                        n=npix * 4, tag="four views", forms=(rafi.RF_FORM_HOST_LOOP,
+                                                                              rafi.RF_FORM_PERSISTENT,
+                                                                              rafi.RF_FORM_GRAPH), reps=1, stream=s)
+        out["autotune"]["sample"] = f"the four views at 4 spp ({npix * 4} paths)"
+        for batched in (rafi.RF_FORM_PERSISTENT, rafi.RF_FORM_HOST_LOOP, rafi.RF_FORM_GRAPH, rafi.RF_FORM_TUNED):
+            if batched == rafi.RF_FORM_PERSISTENT:
+                rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_TRANSPORT, rafi.RF_FORM_PERSISTENT, 0)
+            elif batched == rafi.RF_FORM_TUNED:
+                rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_TRANSPORT, out["autotune"]["form"],
+                                           out["autotune"]["shape"])
             score.zero_()
             rafi.rf_c4_render(ctx.handle, bricks, n, brick, smax, views, spp, 4, score, batched, stream=s)
             score.zero_()
@@ -521,10 +561,12 @@ def c4_transport(torch, rafi, inputs, s, cpu=None):
             e1.record(s)
             torch.cuda.synchronize()
             sec = e0.elapsed_time(e1) / 1e3
-            out[("plain", "batched", "graph")[batched]] = {"ms": sec * 1e3, "paths_per_s": paths / sec,
-                                                           "rays_forwarded_per_s": fwd / sec, "rounds": rounds}
+            out[("plain", "batched", "graph", "tuned")[batched]] = {"ms": sec * 1e3, "paths_per_s": paths / sec,
+                                                                     "rays_forwarded_per_s": fwd / sec,
+                                                                     "rounds": rounds}
     out["batched_over_plain"] = out["plain"]["ms"] / out["batched"]["ms"]
     out["graph_over_plain"] = out["plain"]["ms"] / out["graph"]["ms"]
+    out["tuned_over_plain"] = out["plain"]["ms"] / out["tuned"]["ms"]
     if cpu is not None:  # the cpu_baseline leg: the oracle on a crop of the first view
         cpu["transport_subset"] = oracle_c4_subset(vol, smax, views[0], spp)
     return out
@@ -637,6 +679,12 @@ def run_ours(args):
         timed.laws = laws
         return fwd, e0.elapsed_time(e1), t, launches, clocks.summary()
 
+    # the autotuner picks the persistent kernel's shape on one step of the workload itself
+    from paper_2605_30294_gb300 import autotune
+
+    tuned_c1 = autotune.tune(ctx.handle, rafi.RF_POLICY_MICROBENCH, lambda form: step(True), item_bytes=ITEM_BYTES,
+                             ranks=RANKS, n=n, tag="steps on arrival, three laws", reps=1, stream=s)
+
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
     uuid = getattr(props, "uuid", None)
@@ -700,11 +748,13 @@ def run_ours(args):
     te = rafi.rf_get_timing(ctx.handle, reset=True)
     rafi.rf_set_timing(ctx.handle, False)
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    retired.copy_(h_items.view(n, 16), non_blocking=True)  # first copy: untimed
     ev[0].record(s)
-    retired.copy_(h_items.view(n, 16), non_blocking=True)
+    for _ in range(3):
+        retired.copy_(h_items.view(n, 16), non_blocking=True)
     ev[1].record(s)
     torch.cuda.synchronize()
-    h2d_ms = ev[0].elapsed_time(ev[1])
+    h2d_ms = ev[0].elapsed_time(ev[1]) / 3
     run_ms = one_step_s * 1e3 / len(MODES)
     kern_ms = te.roundsMs / max(te.roundsLaunches, 1)
     e2e_split = {"ms_per_run": run_ms, "h2d_items_ms": h2d_ms,
@@ -767,6 +817,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "items": n, "item_bytes": ITEM_BYTES, "ranks": RANKS,
                    "form": "batched: all rounds in one persistent cooperative kernel per run, each step applied on arrival",
+                   "shape": {"threads": tuned_c1["threads"], "items_per_thread": tuned_c1["items_per_thread"],
+                             "ctas_per_sm": tuned_c1["ctas_per_sm"], "chosen_by": "autotune"},
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "no flush: the 1 GiB item queues exceed the 129 MB L2"},
         "roofline": {"bound": "hbm", "kernel": "rounds_kernel<C1Work>", "achieved": achieved, "peak": peak,
@@ -784,6 +836,7 @@ def run_ours(args):
                                   "round_frac_ge_2^20": rates.get("round_gbs_ge_2^20", 0.0) / peak,
                                   "fwd_frac_ge_2^20": rates.get("fwd_gbs_ge_2^20", 0.0) / peak},
         "per_law": laws_batched,
+        "autotune": tuned_c1,
         "batched_step_in_place": {
             "value": u_fwd / (u_ms / 1e3), "ms_per_step": u_ms / p_steps, "steps": p_steps, "per_law": laws_in_place,
             "form": "persistent kernel; each round steps every item in its queue slot, then scatters",
@@ -892,15 +945,16 @@ def run_section(args):
         rafi.rf_c0_make_bricks(dv, n, brick, bricks, s)
         nr = w * h * spp
         rayC = torch.zeros(nr, dtype=torch.float32, device="cuda")
+        rayClo = torch.zeros(nr, dtype=torch.float32, device="cuda")
         img = torch.zeros(w * h, dtype=torch.float32, device="cuda")
         gimg = torch.ones(w * h, dtype=torch.float32, device="cuda")
         grad = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
-        out["workload"] = "256^3 blob density, 2x2x2 ranks, 512x512 at 4 spp"
+        out["workload"] = "256^3 blob density, 2x2x2 ranks, 512x512 at 4 spp (compensated colour sums)"
         with rafi.Context(8, 64, nr) as ctx:
             for name, fn in (("forward", lambda: rafi.rf_c3_render(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
-                                                                    rayC, img, stream=s)),
+                                                                    rayC, img, stream=s, ray_c_lo=rayClo)),
                              ("adjoint", lambda: rafi.rf_c3_adjoint(ctx.handle, bricks, cam, n, brick, w, h, spp, 3,
-                                                                     rayC, gimg, grad, stream=s))):
+                                                                     rayC, gimg, grad, stream=s, ray_c_lo=rayClo))):
                 e0.record(s)
                 fn()
                 e1.record(s)

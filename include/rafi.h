@@ -208,6 +208,38 @@ rf_status rf_get_timing(rf_ctx *ctx, rf_phase_times *out, int32_t reset);
  * RF_ERR_ARG for spinCycles above 2^40 or missingArrivals above 1024. */
 rf_status rf_set_wait_limits(rf_ctx *ctx, uint64_t spinCycles, uint32_t missingArrivals);
 
+/* --- batched form: forms, shapes and the autotuner's settings ------------ */
+
+/* Workloads that run the persistent round kernel (policies). */
+#define RF_POLICY_MICROBENCH 0 /* rf_c1_run_batched */
+#define RF_POLICY_STREAMLINES 1 /* rf_c2_run */
+#define RF_POLICY_TRANSPORT 2 /* rf_c4_render */
+
+/* Forms of a run: the per-round host loop, all rounds in one persistent
+ * cooperative kernel, the round's kernels in a CUDA graph whose conditional
+ * while node repeats them; RF_FORM_TUNED (rf_c2_run / rf_c4_render's batched
+ * argument) takes the form and shape set for the policy on the context. */
+#define RF_FORM_HOST_LOOP 0
+#define RF_FORM_PERSISTENT 1
+#define RF_FORM_GRAPH 2
+#define RF_FORM_TUNED 3
+
+/* The persistent kernel's compiled shapes for a policy: *count receives how
+ * many there are; shapes (host, 3 x cap int32, may be NULL) receives
+ * {threads per CTA, items per thread per tile, resident CTAs per SM} for the
+ * first min(count, cap).  Every shape computes the same rounds, bit for bit;
+ * only the time differs.  RF_ERR_ARG for an unknown policy. */
+rf_status rf_rounds_shapes(int32_t policy, int32_t *count, int32_t *shapes, int32_t cap);
+
+/* The form and shape a context uses for a policy: form for RF_FORM_TUNED runs
+ * (RF_FORM_HOST_LOOP, _PERSISTENT or _GRAPH; the microbenchmark's batched call
+ * is always persistent), shape for every persistent run of the policy.
+ * Defaults: persistent, shape 0.  The autotuner (autotune.py in the package)
+ * times the candidates on a sample of the caller's run and sets the fastest.
+ * RF_ERR_ARG for an unknown policy, form or shape. */
+rf_status rf_set_batched_config(rf_ctx *ctx, int32_t policy, int32_t form, int32_t shape);
+rf_status rf_get_batched_config(rf_ctx *ctx, int32_t policy, int32_t *form, int32_t *shape);
+
 /* Kernels this library launched in this process so far (all contexts). */
 uint64_t rf_launch_count(void);
 
@@ -324,9 +356,11 @@ rf_status rf_c1_run_graph(rf_ctx *ctx, const void *items, uint64_t n, uint32_t s
  * one of rf_c1_run with deterministic != 0.  With hostMemory != 0 and a
  * page-locked (device-mapped) retired buffer the kernel writes the retired
  * items straight into it during the run; other host buffers are filled from
- * a device staging buffer after it.  Rounds of at most 2048 items
+ * a device staging buffer after it.  The kernel runs in the shape set for
+ * RF_POLICY_MICROBENCH on the context (rf_set_batched_config; shape 0 by
+ * default: tiles of 512 items, 3 CTAs per SM).  Rounds of at most four tiles
  * run on one CTA (the others return); with steps on arrival, rounds of at
- * most 512 items keep the whole queue in that CTA's shared memory.  roundLog (device, 7 x roundLogCap
+ * most one tile keep the whole queue in that CTA's shared memory.  roundLog (device, 7 x roundLogCap
  * words, nullable) receives per round, as seen by CTA 0, the %globaltimer ns
  * at round start, end of its work step (or count), after the first barrier,
  * end of its scatter and after the second barrier, then the incoming and the
@@ -424,8 +458,11 @@ rf_status rf_c2_trace(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, fl
  * round); batched == 1: all rounds in one persistent cooperative kernel (the
  * batched form of rf_c1_run_batched); batched == 2: the trace kernel and the
  * exchange kernels captured once into a CUDA graph whose conditional while
- * node repeats them on the device while particles are active.  out (device) receives every particle
- * by id; *rounds = trace rounds, *forwarded = particles delivered by them. */
+ * node repeats them on the device while particles are active; batched == 3
+ * (RF_FORM_TUNED): the form set for RF_POLICY_STREAMLINES on the context
+ * (rf_set_batched_config).  Persistent runs use the context's shape for the
+ * policy.  out (device) receives every particle by id; *rounds = trace
+ * rounds, *forwarded = particles delivered by them. */
 rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const uint32_t *setIds, uint64_t n,
                     int32_t N, int32_t B, float h, uint32_t maxSteps, uint32_t stepsPerRound, void *out,
                     int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded);
@@ -439,22 +476,29 @@ rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const 
  * Samples at t0 + (k + 0.5) * 0.5; per sample e = expf(-sigma/2), alpha =
  * 1 - e, c = 20 sigma, C += (T alpha) c, T *= e (the Lander renderer's
  * emission-absorption model, Sec. 5.2, each ray carrying C and T across
- * bricks).  rayC (device, W*H*spp) receives every sample's C, image (device,
- * W*H) the mean over a pixel's samples. */
+ * bricks).  rayC (device, W*H*spp) receives every sample's C (the plain float
+ * sum), image (device, W*H) the mean over a pixel's samples.  rayCLo (device,
+ * W*H*spp, or NULL) receives the rounding error of each C, kept with Knuth's
+ * error-free TwoSum, so that C + Clo is the exact sum of the float terms to
+ * about 2^-48 relative; rf_c3_adjoint uses it to take exact suffixes. */
 rf_status rf_c3_render(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W, int32_t H,
-                       int32_t spp, uint32_t seed, float *rayC, float *image, uint32_t maxRounds, void *stream,
-                       uint64_t *rounds);
+                       int32_t spp, uint32_t seed, float *rayC, float *rayCLo, float *image, uint32_t maxRounds,
+                       void *stream, uint64_t *rounds);
 
-/* Adjoint of rf_c3_render: given rayC from the forward call and gradImage =
- * dL/dimage (device, W*H), adds dL/dsigma to gradVolume (device, N^3, x
- * fastest; the caller zeroes it).  Adjoint rays carry their forward C and
- * dL/dC (= gradImage / spp) through the same bricks, recompute T and the
- * running sum per brick, and scatter dC/dsigma_k = T_k (0.5 e_k c_k + 20
- * alpha_k) - 0.5 (C - sum_{j<=k} T_j alpha_j c_j) with the trilinear weights
- * (atomic adds: the summation order, not the value, depends on scheduling). */
+/* Adjoint of rf_c3_render: given rayC (and rayCLo, or NULL) from the forward
+ * call and gradImage = dL/dimage (device, W*H), adds dL/dsigma to gradVolume
+ * (device, N^3, x fastest; the caller zeroes it).  Adjoint rays carry their
+ * forward C and dL/dC (= gradImage / spp) through the same bricks, recompute
+ * T per brick and scatter dC/dsigma_k = T_k (0.5 e_k c_k + 20 alpha_k) - 0.5
+ * S_{>k} with the trilinear weights, where the suffix S_{>k} = C - sum_{j<=k}
+ * T_j alpha_j c_j is kept as a TwoSum pair starting from (C, Clo): exact up to
+ * the rounding of the terms when rayCLo is given, else off by the rounding of
+ * C itself.  Atomic adds: the summation order, not the value, depends on
+ * scheduling. */
 rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W,
-                        int32_t H, int32_t spp, uint32_t seed, const float *rayC, const float *gradImage,
-                        float *gradVolume, uint32_t maxRounds, void *stream, uint64_t *rounds);
+                        int32_t H, int32_t spp, uint32_t seed, const float *rayC, const float *rayCLo,
+                        const float *gradImage, float *gradVolume, uint32_t maxRounds, void *stream,
+                        uint64_t *rounds);
 
 /* --- stochastic transport by delta tracking (64-byte paths) -------------- */
 
@@ -472,8 +516,9 @@ rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int3
  * forwarded to the rank owning their next tentative collision point (VoPaT,
  * Sec. 5.1, Fig. 1).  score (device, total pixels; the caller zeroes it)
  * receives the number of escaped paths per pixel.  batched: 0 host loop, 1
- * persistent kernel, 2 CUDA graph loop, as rf_c2_run.  *rounds, *forwarded
- * as rf_c2_run. */
+ * persistent kernel, 2 CUDA graph loop, 3 the form set for
+ * RF_POLICY_TRANSPORT on the context, as rf_c2_run.  *rounds, *forwarded as
+ * rf_c2_run. */
 rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, float sigmaMax, int32_t numViews,
                        const float *cams, const int32_t *sizes, int32_t spp, uint32_t seed, float *score,
                        int32_t batched, uint32_t maxRounds, void *stream, uint64_t *rounds, uint64_t *forwarded);

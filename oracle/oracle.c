@@ -600,9 +600,12 @@ void or_c3_render(const float *vol, int32_t N, const float *cam, int32_t W, int3
  * then k from last to first with the suffix S = sum_{j>k} T_j alpha_j c_j:
  *   dC/dsigma_k = T_k (0.5 e_k c_k + alpha_k * 20) - 0.5 S,
  * scattered to the 8 voxels with the trilinear weights (clamped taps add).
+ * gabs (may be NULL) receives, per voxel, the sum of the absolute values of
+ * the same contributions: the scale against which a float sum of them can
+ * be judged (it is not part of the gradient).
  * Returns the loss-independent sum of dLdC * C (a consistency value). */
 double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t W, int32_t H, int32_t spp,
-                         uint32_t seed, const double *dLdC, double *grad)
+                         uint32_t seed, const double *dLdC, double *grad, double *gabs)
 {
     int32_t maxK = (int32_t)(2.0f * 1.7321f * (float)N) + 8;
     double *sg = (double *)malloc((size_t)maxK * sizeof(double));
@@ -667,6 +670,7 @@ double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t 
                         double wt = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
                                     ((c & 4) ? w[2] : 1.0 - w[2]);
                         grad[((size_t)iz * N + iy) * N + ix] += gs * wt;
+                        if (gabs) gabs[((size_t)iz * N + iy) * N + ix] += fabs(gs * wt);
                     }
                 }
             }

@@ -155,6 +155,7 @@ struct C1Work {
     static constexpr bool kFuseStep = true;
     static constexpr int kMinBlocksPerSM = 3;
     static constexpr int kItemsPerThread = 2;
+    static constexpr int kBlock = kRoundsBlock;
     static constexpr unsigned kStepReadMask = 0x9u;   // the step reads words 0-1 and 12-15
     static constexpr unsigned kStepWriteMask = 0x8u;  // and writes words 13-15
     const uint32_t *zipfThr;
@@ -194,6 +195,13 @@ struct C1Work {
     }
     __device__ void retire(const uint4 (&)[4]) const {}
 };
+
+// Shapes of the persistent kernel for the microbenchmark (the autotuner's
+// candidates): {items per thread, CTAs per SM, threads}; tiles of 512, 768
+// and 1024 items (the larger the tile, the longer each destination's run of
+// stores), one shape per SM-occupancy that fits the tile's shared memory.
+using C1Shapes = ShapeList<C1Work, Shape<C1Work, 2, 3, 256>, Shape<C1Work, 3, 2, 256>, Shape<C1Work, 4, 1, 256>,
+                           Shape<C1Work, 2, 1, 512>>;
 
 // Seed: emit item i to rank i mod R at out slot base + i, where base was
 // reserved on the append counter by reserve_kernel.
@@ -465,6 +473,20 @@ rf_status rf_c1_run_graph(rf_ctx *ctx, const void *items, uint64_t n, uint32_t s
 
 }  // extern "C"
 
+namespace rfi {
+int c1_shapes(int32_t *out, int32_t cap)
+{
+    ShapeInfo v[C1Shapes::kCount];
+    C1Shapes::infos(v);
+    for (int i = 0; i < C1Shapes::kCount && i < cap; ++i) {
+        out[3 * i] = v[i].block;
+        out[3 * i + 1] = v[i].itemsPerThread;
+        out[3 * i + 2] = v[i].ctasPerSM;
+    }
+    return C1Shapes::kCount;
+}
+}  // namespace rfi
+
 extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t seed, int32_t mode,
                                        double zipfS, int32_t gx, int32_t gy, int32_t gz, void *retired,
                                        uint64_t *retiredCountOut, int32_t hostMemory, int32_t stepOnArrival,
@@ -537,7 +559,8 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
     w.gz = gz;
     w.R = ctx->numRanks;
     unsigned long long res[4];
-    rf_status st = launch_rounds(ctx, w, maxRounds, s, roundLog, roundLogCap, static_cast<uint4 *>(devRetired), n,
+    rf_status st = C1Shapes::launch(ctx->batchedShape[RF_POLICY_MICROBENCH], ctx, w, maxRounds, s, roundLog,
+                                    roundLogCap, static_cast<uint4 *>(devRetired), n,
                                  ctx->stagingCount, res, stepOnArrival != 0, stepOnArrival != 0,
                                  inPlace ? items : nullptr);
     if (st != RF_OK) return st;

@@ -183,6 +183,7 @@ struct C2Work {
     static constexpr unsigned kStepWriteMask = 0x3u;
     static constexpr int kMinBlocksPerSM = 3;
     static constexpr int kItemsPerThread = 1;
+    static constexpr int kBlock = kRoundsBlock;
     C2Params P;
     __host__ __device__ uint32_t smemBytes() const { return 0u; }
     __device__ void load_smem(void *) const {}
@@ -192,6 +193,13 @@ struct C2Work {
     }
     __device__ void retire(const uint4 (&w)[2]) const { c2_write_out(P, w); }
 };
+
+// Shapes of the persistent kernel for this policy (the autotuner's
+// candidates): {items per thread, CTAs per SM, threads}.  The work phase's
+// occupancy is what matters here; the tile only sizes the scatter.
+using C2Shapes = ShapeList<C2Work, Shape<C2Work, 1, 3, 256>, Shape<C2Work, 1, 2, 256>, Shape<C2Work, 1, 6, 128>,
+                           Shape<C2Work, 2, 3, 256>>;
+
 
 // Element (lx, ly, lz) of brick r holds the grid voxels (gx, gy, gz) and
 // (gx + 1, gy, gz) of its halo origin + (lx, ly, lz), each clamped to the grid.
@@ -304,6 +312,20 @@ int grid_for(rf_ctx *ctx, uint64_t work)
 
 using namespace rfi;
 
+namespace rfi {
+int c2_shapes(int32_t *out, int32_t cap)
+{
+    ShapeInfo v[C2Shapes::kCount];
+    C2Shapes::infos(v);
+    for (int i = 0; i < C2Shapes::kCount && i < cap; ++i) {
+        out[3 * i] = v[i].block;
+        out[3 * i + 1] = v[i].itemsPerThread;
+        out[3 * i + 2] = v[i].ctasPerSM;
+    }
+    return C2Shapes::kCount;
+}
+}  // namespace rfi
+
 extern "C" {
 
 rf_status rf_c2_make_bricks(const float *field, int32_t N, int32_t B, float *bricks, void *stream)
@@ -365,7 +387,7 @@ rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const 
 {
     if (rf_status st = check_c2(ctx, N, B, "rf_c2_run")) return st;
     if (!bricks || !out || (n && !seeds) || n > ctx->capacity || !(h > 0.0f) ||
-        (reinterpret_cast<uintptr_t>(bricks) & 31u)) {
+        (reinterpret_cast<uintptr_t>(bricks) & 31u) || batched < RF_FORM_HOST_LOOP || batched > RF_FORM_TUNED) {
         set_error("rf_c2_run: bad arguments");
         return RF_ERR_ARG;
     }
@@ -373,8 +395,10 @@ rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (rf_status st = rf_c2_seed(ctx, seeds, setIds, n, N, B, stream)) return st;
     const C2Params P = make_params(bricks, N, B, h, maxSteps, stepsPerRound, out, n);
+    // RF_FORM_TUNED: the form the context holds for this policy (set by the autotuner)
+    const int32_t form = batched == RF_FORM_TUNED ? ctx->batchedForm[RF_POLICY_STREAMLINES] : batched;
     uint64_t active = 0, fwd = 0, r = 0;
-    if (batched == 2) {
+    if (form == RF_FORM_GRAPH) {
         // graph form: the trace kernel and the exchange repeated by a while node
         if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
         rf_status st = run_graph_loop(ctx, s, maxRounds, [&](cudaStream_t cs) -> rf_status {
@@ -386,12 +410,13 @@ rf_status rf_c2_run(rf_ctx *ctx, const float *bricks, const float *seeds, const 
         }, &r, &fwd);
         if (st != RF_OK) return st;
         active = ctx->host->numActive;
-    } else if (batched) {
+    } else if (form == RF_FORM_PERSISTENT) {
         if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
         C2Work w;
         w.P = P;
         unsigned long long res[4];
-        rf_status st = launch_rounds(ctx, w, maxRounds, s, nullptr, 0u, nullptr, 0ull, nullptr, res);
+        rf_status st = C2Shapes::launch(ctx->batchedShape[RF_POLICY_STREAMLINES], ctx, w, maxRounds, s, nullptr,
+                                        0u, nullptr, 0ull, nullptr, res);
         if (st != RF_OK) return st;
         r = res[0];
         fwd = res[1];

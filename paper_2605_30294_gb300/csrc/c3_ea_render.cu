@@ -10,10 +10,18 @@
 // Adjoint: dC/dsigma_k = T_k (0.5 e_k c_k + 20 alpha_k) - 0.5 S_{>k} with
 // S_{>k} = sum_{j>k} T_j alpha_j c_j = C - sum_{j<=k} T_j alpha_j c_j.  An
 // adjoint ray carries the final C of its forward ray and dL/dC; walking the
-// same bricks it recomputes T_k and the running sum segment by segment (no
+// same bricks it recomputes T_k and the running suffix segment by segment (no
 // stored history, no division by 1 - alpha) and scatters dL/dC * dC/dsigma_k
 // with the trilinear weights into the gradient grid (atomic adds, summed per
 // ray over consecutive samples that share their eight corners).
+//
+// Late samples of an opaque ray have a suffix far below C, so C minus a float
+// prefix loses most of its digits.  Both passes therefore keep their sums as
+// unevaluated pairs (hi + lo, Knuth's error-free TwoSum): the forward adds
+// each T alpha c to (C, Clo) and may return Clo beside C (C itself is the
+// plain float sum, bit for bit); the adjoint starts from (C, Clo) and takes
+// each T alpha c off again, so the suffix it uses is exact up to the rounding
+// of the individual terms.
 //
 // Built with -fmad=false (the written float order, as the oracle's).
 #include "internal.cuh"
@@ -25,8 +33,9 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// 64-byte ray.  Forward: acc = C so far.  Adjoint: acc = running sum of
-// T alpha c, cfin = C of the forward ray, g = dL/dC.
+// 64-byte ray.  Forward: (acc, lo) = C so far as a hi + lo pair.  Adjoint:
+// (acc, lo) = the suffix still to come (C minus the terms walked so far),
+// cfin = C of the forward ray, g = dL/dC.
 struct __align__(16) EARay {
     float ox, oy, oz, dx;
     float dy, dz, k, T;
@@ -34,7 +43,7 @@ struct __align__(16) EARay {
     uint32_t id;
     float cfin, g;
     int32_t rank;
-    uint32_t pad;
+    uint32_t lo;  // float bits of the low part of acc
 };
 static_assert(sizeof(EARay) == 64, "64-byte ray");
 
@@ -48,9 +57,21 @@ struct EAParams {
     int32_t W, H, spp;
     uint32_t seed;
     float *rayC;        // W*H*spp
+    float *rayCLo;      // W*H*spp low parts of rayC (nullable)
     float *grad;        // N^3 (adjoint)
     const float *gimg;  // W*H dL/dpixel (adjoint)
 };
+
+// a + b = s + err exactly (Knuth's TwoSum; the file is built without FMA
+// contraction, so every operation rounds once)
+__device__ __forceinline__ float two_sum(float a, float b, float &err)
+{
+    const float s = a + b;
+    const float bp = s - a;
+    const float ap = s - bp;
+    err = (a - ap) + (b - bp);
+    return s;
+}
 
 __device__ __forceinline__ int32_t clampi(int32_t v, int32_t lo, int32_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -177,7 +198,7 @@ __device__ __forceinline__ bool make_ray(const Cam &cam, const EAParams &P, int3
     r.id = (uint32_t)(pix * P.spp + s);
     r.cfin = 0.0f;
     r.g = 0.0f;
-    r.pad = 0u;
+    r.lo = 0u;
     const float tk = r.t0 + 0.5f * 0.5f;
     r.rank = owner_of(r.ox + r.dx * tk, r.oy + r.dy * tk, r.oz + r.dz * tk, P.B, P.nb);
     return tk < r.t1;
@@ -195,13 +216,16 @@ __global__ void __launch_bounds__(kBlock) raygen_kernel(Cam cam, EAParams P, rf_
         if (!hit) continue;
         if (ADJ) {
             r.cfin = P.rayC[i];
+            r.acc = r.cfin;  // the whole suffix before the first sample
+            r.lo = __float_as_uint(P.rayCLo ? P.rayCLo[i] : 0.0f);
             r.g = P.gimg[pix] / (float)P.spp;
         }
         rf::forward(q, r, r.rank);
     }
 }
 
-template <bool ADJ>
+// ADJ: adjoint rays.  COMP (forward): keep the low part of C and return it in rayCLo.
+template <bool ADJ, bool COMP>
 __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_queues q)
 {
     __shared__ uint32_t sOff[RF_MAX_RANKS + 1];
@@ -217,13 +241,14 @@ __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_que
         const int32_t org[3] = {bx * P.B - 1, by * P.B - 1, bz * P.B - 1};
         const float4 *brick = reinterpret_cast<const float4 *>(P.bricks) + (size_t)rank * S * S * S;
         int32_t k = (int32_t)r.k;
-        float T = r.T, acc = r.acc;
+        float T = r.T, acc = r.acc, lo = __uint_as_float(r.lo);
         GradAcc ga;
         ga.any = false;
         for (;;) {
             const float tk = r.t0 + ((float)k + 0.5f) * 0.5f;
             if (!(tk < r.t1)) {
                 if (!ADJ) P.rayC[r.id] = acc;
+                if (!ADJ && COMP) P.rayCLo[r.id] = lo;
                 if (ADJ) grad_flush(P.grad, P.N, ga);
                 break;
             }
@@ -234,6 +259,7 @@ __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_que
                 r.k = (float)k;
                 r.T = T;
                 r.acc = acc;
+                r.lo = __float_as_uint(lo);
                 r.rank = own;
                 rf::forward(q, r, own);
                 break;
@@ -244,11 +270,20 @@ __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_que
             const float al = 1.0f - e;
             const float cc = sg * 20.0f;
             const float contrib = (T * al) * cc;
-            acc = acc + contrib;
             if (ADJ) {
-                const float suffix = r.cfin - acc;  // sum over later samples
+                // suffix over the later samples: (acc, lo) minus this term
+                float err;
+                acc = two_sum(acc, -contrib, err);
+                lo = lo + err;
+                const float suffix = acc + lo;
                 const float dC = T * ((0.5f * e) * cc + al * 20.0f) - 0.5f * suffix;
                 grad_add(P.grad, P.N, ga, tp, r.g * dC);
+            } else if (COMP) {
+                float err;
+                acc = two_sum(acc, contrib, err);
+                lo = lo + err;
+            } else {
+                acc = acc + contrib;
             }
             T = T * e;
             ++k;
@@ -308,8 +343,8 @@ int grid_for(rf_ctx *ctx, uint64_t work)
 
 template <bool ADJ>
 rf_status run_ea(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W, int32_t H,
-                 int32_t spp, uint32_t seed, float *rayC, const float *gimg, float *grad, uint32_t maxRounds,
-                 void *stream, uint64_t *rounds)
+                 int32_t spp, uint32_t seed, float *rayC, float *rayCLo, const float *gimg, float *grad,
+                 uint32_t maxRounds, void *stream, uint64_t *rounds)
 {
     DeviceGuard g(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -323,6 +358,7 @@ rf_status run_ea(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, 
     P.spp = spp;
     P.seed = seed;
     P.rayC = rayC;
+    P.rayCLo = rayCLo;
     P.grad = grad;
     P.gimg = gimg;
     rf_device_queues q;
@@ -340,7 +376,8 @@ rf_status run_ea(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, 
             return RF_ERR_MAX_ROUNDS;
         }
         time_begin(ctx, kTimeWork, s);
-        march_kernel<ADJ><<<grid_for(ctx, ctx->capacity), kBlock, 0, s>>>(P, q);
+        if (ADJ || !P.rayCLo) march_kernel<ADJ, false><<<grid_for(ctx, ctx->capacity), kBlock, 0, s>>>(P, q);
+        else march_kernel<false, true><<<grid_for(ctx, ctx->capacity), kBlock, 0, s>>>(P, q);
         RF_LAUNCHED("c3 march_kernel");
         time_end(ctx, kTimeWork, s);
         if ((st = rf_exchange(ctx, stream, &active))) return st;
@@ -358,16 +395,16 @@ using namespace rfi;
 extern "C" {
 
 rf_status rf_c3_render(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W, int32_t H,
-                       int32_t spp, uint32_t seed, float *rayC, float *image, uint32_t maxRounds, void *stream,
-                       uint64_t *rounds)
+                       int32_t spp, uint32_t seed, float *rayC, float *rayCLo, float *image, uint32_t maxRounds,
+                       void *stream, uint64_t *rounds)
 {
     if (rf_status st = check_c3(ctx, N, B, W, H, spp, "rf_c3_render")) return st;
     if (!bricks || !cam || !rayC || !image || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
         set_error("rf_c3_render: NULL buffer");
         return RF_ERR_ARG;
     }
-    rf_status st = run_ea<false>(ctx, bricks, cam, N, B, W, H, spp, seed, rayC, nullptr, nullptr, maxRounds, stream,
-                                 rounds);
+    rf_status st = run_ea<false>(ctx, bricks, cam, N, B, W, H, spp, seed, rayC, rayCLo, nullptr, nullptr, maxRounds,
+                                 stream, rounds);
     if (st != RF_OK) return st;
     DeviceGuard g(ctx->device);
     image_kernel<<<grid_for(ctx, (uint64_t)W * H), kBlock, 0, static_cast<cudaStream_t>(stream)>>>(rayC, W * H, spp,
@@ -377,16 +414,17 @@ rf_status rf_c3_render(rf_ctx *ctx, const float *bricks, const float *cam, int32
 }
 
 rf_status rf_c3_adjoint(rf_ctx *ctx, const float *bricks, const float *cam, int32_t N, int32_t B, int32_t W,
-                        int32_t H, int32_t spp, uint32_t seed, const float *rayC, const float *gradImage,
-                        float *gradVolume, uint32_t maxRounds, void *stream, uint64_t *rounds)
+                        int32_t H, int32_t spp, uint32_t seed, const float *rayC, const float *rayCLo,
+                        const float *gradImage, float *gradVolume, uint32_t maxRounds, void *stream,
+                        uint64_t *rounds)
 {
     if (rf_status st = check_c3(ctx, N, B, W, H, spp, "rf_c3_adjoint")) return st;
     if (!bricks || !cam || !rayC || !gradImage || !gradVolume || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
         set_error("rf_c3_adjoint: NULL buffer");
         return RF_ERR_ARG;
     }
-    return run_ea<true>(ctx, bricks, cam, N, B, W, H, spp, seed, const_cast<float *>(rayC), gradImage, gradVolume,
-                        maxRounds, stream, rounds);
+    return run_ea<true>(ctx, bricks, cam, N, B, W, H, spp, seed, const_cast<float *>(rayC),
+                        const_cast<float *>(rayCLo), gradImage, gradVolume, maxRounds, stream, rounds);
 }
 
 }  // extern "C"

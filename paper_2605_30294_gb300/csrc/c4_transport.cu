@@ -189,12 +189,20 @@ struct C4Work {
     static constexpr unsigned kStepWriteMask = 0xfu;
     static constexpr int kMinBlocksPerSM = 4;
     static constexpr int kItemsPerThread = 1;
+    static constexpr int kBlock = kRoundsBlock;
     TParams P;
     __host__ __device__ uint32_t smemBytes() const { return 0u; }
     __device__ void load_smem(void *) const {}
     __device__ int32_t step(uint4 (&w)[4], int32_t rank, uint32_t, const void *) const { return track(P, w, rank); }
     __device__ void retire(const uint4 (&)[4]) const {}
 };
+
+// Shapes of the persistent kernel for this policy (the autotuner's
+// candidates): {items per thread, CTAs per SM, threads}.  The work phase's
+// occupancy is what matters here; the tile only sizes the scatter.
+using C4Shapes = ShapeList<C4Work, Shape<C4Work, 1, 4, 256>, Shape<C4Work, 1, 3, 256>, Shape<C4Work, 1, 8, 128>,
+                           Shape<C4Work, 2, 4, 256>>;
+
 
 // Primary paths of one view: path (pixel, s) starts where its jittered ray
 // enters the grid and is emitted, in out slot base + i, to that brick's rank
@@ -295,6 +303,20 @@ int grid_for(rf_ctx *ctx, uint64_t work)
 
 using namespace rfi;
 
+namespace rfi {
+int c4_shapes(int32_t *out, int32_t cap)
+{
+    ShapeInfo v[C4Shapes::kCount];
+    C4Shapes::infos(v);
+    for (int i = 0; i < C4Shapes::kCount && i < cap; ++i) {
+        out[3 * i] = v[i].block;
+        out[3 * i + 1] = v[i].itemsPerThread;
+        out[3 * i + 2] = v[i].ctasPerSM;
+    }
+    return C4Shapes::kCount;
+}
+}  // namespace rfi
+
 extern "C" rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, int32_t B, float sigmaMax,
                                   int32_t numViews, const float *cams, const int32_t *sizes, int32_t spp,
                                   uint32_t seed, float *score, int32_t batched, uint32_t maxRounds, void *stream,
@@ -305,7 +327,8 @@ extern "C" rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, i
         return RF_ERR_ARG;
     }
     if (!bricks || !cams || !sizes || !score || numViews < 1 || spp < 1 || !(sigmaMax > 0.0f) || N < 1 || B < 1 ||
-        N % B || (int64_t)(N / B) * (N / B) * (N / B) != ctx->numRanks || (reinterpret_cast<uintptr_t>(bricks) & 15u)) {
+        N % B || (int64_t)(N / B) * (N / B) * (N / B) != ctx->numRanks || (reinterpret_cast<uintptr_t>(bricks) & 15u) ||
+        batched < RF_FORM_HOST_LOOP || batched > RF_FORM_TUNED) {
         set_error("rf_c4_render: bad arguments");
         return RF_ERR_ARG;
     }
@@ -348,8 +371,10 @@ extern "C" rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, i
     }
     set_count_kernel<<<1, 32, 0, s>>>(q.outCount, total);
     RF_LAUNCHED("c4 set_count_kernel");
+    // RF_FORM_TUNED: the form the context holds for this policy (set by the autotuner)
+    const int32_t form = batched == RF_FORM_TUNED ? ctx->batchedForm[RF_POLICY_TRANSPORT] : batched;
     uint64_t active = 0, fwd = 0, r = 0;
-    if (batched == 2) {
+    if (form == RF_FORM_GRAPH) {
         // graph form: the tracking kernel and the exchange repeated by a while node
         if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
         rf_status st = run_graph_loop(ctx, s, maxRounds, [&](cudaStream_t cs) -> rf_status {
@@ -359,12 +384,13 @@ extern "C" rf_status rf_c4_render(rf_ctx *ctx, const float *bricks, int32_t N, i
         }, &r, &fwd);
         if (st != RF_OK) return st;
         active = ctx->host->numActive;
-    } else if (batched) {
+    } else if (form == RF_FORM_PERSISTENT) {
         if (rf_status st = rf_exchange(ctx, stream, nullptr)) return st;
         C4Work w;
         w.P = P;
         unsigned long long res[4];
-        rf_status st = launch_rounds(ctx, w, maxRounds, s, nullptr, 0u, nullptr, 0ull, nullptr, res);
+        rf_status st = C4Shapes::launch(ctx->batchedShape[RF_POLICY_TRANSPORT], ctx, w, maxRounds, s, nullptr, 0u,
+                                        nullptr, 0ull, nullptr, res);
         if (st != RF_OK) return st;
         r = res[0];
         fwd = res[1];

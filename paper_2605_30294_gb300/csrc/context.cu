@@ -501,6 +501,50 @@ rf_status rf_set_wait_limits(rf_ctx *ctx, uint64_t spinCycles, uint32_t missingA
     return RF_OK;
 }
 
+rf_status rf_rounds_shapes(int32_t policy, int32_t *count, int32_t *shapes, int32_t cap)
+{
+    if (!count || cap < 0 || (cap > 0 && !shapes)) {
+        set_error("rf_rounds_shapes: NULL count or shapes");
+        return RF_ERR_ARG;
+    }
+    int n = -1;
+    if (policy == RF_POLICY_MICROBENCH) n = c1_shapes(shapes, cap);
+    else if (policy == RF_POLICY_STREAMLINES) n = c2_shapes(shapes, cap);
+    else if (policy == RF_POLICY_TRANSPORT) n = c4_shapes(shapes, cap);
+    if (n < 0) {
+        set_error("rf_rounds_shapes: unknown policy %d", policy);
+        return RF_ERR_ARG;
+    }
+    *count = n;
+    return RF_OK;
+}
+
+rf_status rf_set_batched_config(rf_ctx *ctx, int32_t policy, int32_t form, int32_t shape)
+{
+    if (rf_status st = check_ctx(ctx, "rf_set_batched_config")) return st;
+    int32_t n = 0;
+    if (rf_rounds_shapes(policy, &n, nullptr, 0) != RF_OK) return RF_ERR_ARG;
+    if (form < RF_FORM_HOST_LOOP || form > RF_FORM_GRAPH || shape < 0 || shape >= n) {
+        set_error("rf_set_batched_config: form %d or shape %d (of %d) out of range", form, shape, n);
+        return RF_ERR_ARG;
+    }
+    ctx->batchedForm[policy] = form;
+    ctx->batchedShape[policy] = shape;
+    return RF_OK;
+}
+
+rf_status rf_get_batched_config(rf_ctx *ctx, int32_t policy, int32_t *form, int32_t *shape)
+{
+    if (rf_status st = check_ctx(ctx, "rf_get_batched_config")) return st;
+    if (policy < RF_POLICY_MICROBENCH || policy > RF_POLICY_TRANSPORT) {
+        set_error("rf_get_batched_config: unknown policy %d", policy);
+        return RF_ERR_ARG;
+    }
+    if (form) *form = ctx->batchedForm[policy];
+    if (shape) *shape = ctx->batchedShape[policy];
+    return RF_OK;
+}
+
 uint64_t rf_launch_count(void) { return g_launches.load(); }
 
 const char *rf_last_error(void) { return g_err; }

@@ -79,6 +79,9 @@ struct rf_ctx {
     uint32_t *zipfThr = nullptr;  // numRanks words: Zipf table of the microbenchmark
     double zipfS = -1.0;           // exponent the table was built for
 
+    // per policy (RF_POLICY_*): the form a tuned run uses and the persistent kernel's shape
+    int32_t batchedForm[3] = {RF_FORM_PERSISTENT, RF_FORM_PERSISTENT, RF_FORM_PERSISTENT};
+    int32_t batchedShape[3] = {0, 0, 0};
     unsigned long long waitLimitCycles = 0;  // bound of the persistent kernel's barrier waits (0: kSpinLimitCycles)
     uint32_t missingArrivals = 0;            // > 0 only to exercise the timeout path
 
@@ -152,6 +155,12 @@ rf_status run_graph_loop(rf_ctx *ctx, cudaStream_t s, uint32_t maxRounds,
                          size_t keyBytes = 0);
 // Release a kept graph loop (before the context's buffers change or go).
 void drop_graph_loop(rf_ctx *ctx);
+
+// The persistent kernel's shapes of each policy (defined beside the policy):
+// write at most cap {block, itemsPerThread, ctasPerSM} triples, return the count.
+int c1_shapes(int32_t *out, int32_t cap);
+int c2_shapes(int32_t *out, int32_t cap);
+int c4_shapes(int32_t *out, int32_t cap);
 
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);

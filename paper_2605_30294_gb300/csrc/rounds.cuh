@@ -34,6 +34,8 @@
 // CTAs check at the next barrier, and the kernel returns with a timeout status.
 #pragma once
 
+#include <utility>
+
 #include "internal.cuh"
 #include "rafi_device.cuh"
 
@@ -73,10 +75,25 @@ struct RoundsArgs {
     int32_t numRanks;
 };
 
-constexpr int kRoundsBlock = 256;
-constexpr int kRoundsWarps = kRoundsBlock / 32;
-constexpr int kRoundsK = 2;  // items per thread per tile
-constexpr uint32_t kRoundsTile = kRoundsBlock * kRoundsK;
+constexpr int kRoundsBlock = 256;  // threads per CTA of a policy's default shape
+
+// A workload policy W (described at rounds_kernel) launched in another shape:
+// K items per thread per tile, CTAS resident CTAs per SM to compile for,
+// BLOCK threads per CTA.  Every shape computes the same rounds; the batched
+// form's autotuner chooses among the shapes each policy compiles.
+template <class W, int K, int CTAS, int BLOCK>
+struct Shape : W {
+    static constexpr int kItemsPerThread = K;
+    static constexpr int kMinBlocksPerSM = CTAS;
+    static constexpr int kBlock = BLOCK;
+    Shape() = default;
+    __host__ __device__ explicit Shape(const W &w) : W(w) {}
+};
+
+// What the host knows of a compiled shape.
+struct ShapeInfo {
+    int32_t block, itemsPerThread, ctasPerSM;
+};
 
 // Row stride (words) of the per-CTA count table: rows start 16-byte aligned
 // so a run of rows can be staged with one bulk copy.
@@ -211,9 +228,11 @@ __device__ inline bool grid_wait(GridSync *gs, unsigned int *sFlag, unsigned int
     return *sFlag != 0;
 }
 
-// Exclusive block scan of v[0..n) in shared memory (n <= 8 * kRoundsBlock).
+// Exclusive scan of v[0..n) in shared memory by a block of kB threads (n <= 8 kB).
+template <int kB>
 __device__ inline uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
 {
+    constexpr int kWarps = kB / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __syncthreads();
     uint32_t x[8], sum = 0;
@@ -233,15 +252,15 @@ __device__ inline uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
     if (lane == 31) tmp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const uint32_t w = lane < kRoundsWarps ? tmp[lane] : 0u;
+        const uint32_t w = lane < kWarps ? tmp[lane] : 0u;
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
             if (lane >= o) wi += t;
         }
-        if (lane < kRoundsWarps) tmp[lane] = wi - w;
-        if (lane == 31) tmp[kRoundsWarps] = wi;
+        if (lane < kWarps) tmp[lane] = wi - w;
+        if (lane == 31) tmp[kWarps] = wi;
     }
     __syncthreads();
     const uint32_t base = tmp[warp] + incl - sum;
@@ -250,7 +269,7 @@ __device__ inline uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
         const int i = tid * 8 + j;
         if (i < n) v[i] = base + x[j];
     }
-    const uint32_t total = tmp[kRoundsWarps];
+    const uint32_t total = tmp[kWarps];
     __syncthreads();
     return total;
 }
@@ -351,14 +370,14 @@ inline size_t rounds_align_sz(size_t x, size_t a) { return (x + a - 1) / a * a; 
 // per-CTA count rows in phase 2.  dests: the tiles' destinations.  D =
 // destination digits (ranks, plus one retirement digit when the policy
 // appends retired items).
-__host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D, uint32_t workBytes,
-                                                  uint32_t tile = kRoundsTile)
+__host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D, uint32_t workBytes, uint32_t tile,
+                                                  uint32_t warps)
 {
     RoundsLayout L;
     uint32_t o = 0;
     L.items = o;   o = rounds_align(o + 2u * tile * itemBytes, 128);
     L.dests = o;   o = rounds_align(o + 2u * (tile + 4u) * 4u, 16);
-    L.wc = o;      o = rounds_align(o + kRoundsWarps * D * 4u, 16);
+    L.wc = o;      o = rounds_align(o + warps * D * 4u, 16);
     L.cnt = o;     o = rounds_align(o + D * 4u, 16);
     L.start = o;   o = rounds_align(o + D * 4u, 16);
     L.base = o;    o = rounds_align(o + D * 4u, 16);
@@ -366,7 +385,7 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
     L.off = o;     o = rounds_align(o + (D + 1) * 4u, 16);
     L.slotSrc = o; o = rounds_align(o + tile * 2u, 16);
     L.slotDst = o; o = rounds_align(o + tile * 4u, 16);
-    L.tmp = o;     o = rounds_align(o + (kRoundsWarps + 1) * 4u, 16);
+    L.tmp = o;     o = rounds_align(o + (warps + 1) * 4u, 16);
     L.flag = o;    o = rounds_align(o + 4u, 16);
     L.bar = o;     o = rounds_align(o + 16u, 16);
     L.work = o;    o = rounds_align(o + workBytes, 16);
@@ -383,7 +402,8 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
 //   static constexpr bool kGridStride;    (kDynamicWork) items by grid stride rather
 //                                         than dynamically handed-out chunks
 //   static constexpr int kMinBlocksPerSM; resident CTAs per SM to compile for
-//   static constexpr int kItemsPerThread; tile = 256 x this many items
+//   static constexpr int kItemsPerThread; tile = kBlock x this many items
+//   static constexpr int kBlock;          threads per CTA (multiple of 32)
 //   static constexpr bool kFuseStep;      short, even per-item work: the scatter
 //                                         applies the next round's step on arrival
 //   uint32_t smemBytes() const;           its own shared memory
@@ -392,12 +412,14 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
 //       advances one item: returns the destination rank (w updated) or -1 to retire
 //   void retire(const uint4 (&w)[V]) const;  (used when !kAppendRetired)
 template <class W>
-__global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kernel(RoundsArgs a, W work)
+__global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(RoundsArgs a, W work)
 {
     constexpr int V = W::V;
+    constexpr int kB = W::kBlock;  // threads per CTA
+    constexpr int kWarps = kB / 32;
     constexpr uint32_t kItemBytes = 16u * V;
     constexpr int kK = W::kItemsPerThread;  // items per thread per tile
-    constexpr uint32_t kTile = kRoundsBlock * kK;
+    constexpr uint32_t kTile = kB * kK;
     constexpr uint32_t kTileVecs = kTile * V;
     constexpr uint32_t kRetFlag = 0x80000000u;
     constexpr bool kFuse = W::kFuseStep && !W::kDynamicWork;
@@ -406,7 +428,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
     const int R = a.numRanks;
     const int D = R + (W::kAppendRetired ? 1 : 0);  // digits: ranks (+ retirement)
     const int Dp = rounds_row_stride(D);
-    const RoundsLayout L = rounds_layout(kItemBytes, D, work.smemBytes(), kTile);
+    const RoundsLayout L = rounds_layout(kItemBytes, D, work.smemBytes(), kTile, kWarps);
     uint4 *sBuf = reinterpret_cast<uint4 *>(smem + L.items);  // two tiles of kTileVecs
     uint32_t *sRows = reinterpret_cast<uint32_t *>(smem + L.items) + kTileVecs * 4u;  // tile buffer 1
     int32_t *sDst = reinterpret_cast<int32_t *>(smem + L.dests);  // two tiles of kTile + 4
@@ -564,10 +586,10 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         __syncthreads();
     };
     auto rank_b = [&](bool ownBases, bool carryPrev, const int (&myD)[kK], const uint32_t (&myR)[kK]) -> uint32_t {
-        for (int e = tid; e < D; e += kRoundsBlock) {
+        for (int e = tid; e < D; e += kB) {
             uint32_t sum = 0;
 #pragma unroll
-            for (int ww = 0; ww < kRoundsWarps; ++ww) {
+            for (int ww = 0; ww < kWarps; ++ww) {
                 const uint32_t v = wc[ww * D + e];
                 wc[ww * D + e] = sum;
                 sum += v;
@@ -576,9 +598,9 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             dCnt[e] = sum;
             dStart[e] = sum;
         }
-        const uint32_t nValid = rounds_block_scan(dStart, D, tmp);
+        const uint32_t nValid = rounds_block_scan<kB>(dStart, D, tmp);
         if (ownBases) {
-            for (int e = tid; e < D; e += kRoundsBlock)
+            for (int e = tid; e < D; e += kB)
                 dBase[e] = (W::kAppendRetired && e == R) ? (uint32_t)retiredSoFar : dStart[e];
             __syncthreads();
         }
@@ -633,7 +655,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 const uint32_t nNext = W::kAppendRetired ? dStart[R] : nValid;
                 const uint32_t retiredNow = W::kAppendRetired ? dCnt[R] : 0u;
                 if (lr) a.roundLog[7 * round + 1] = a.roundLog[7 * round + 2] = globaltimer();
-                for (uint32_t slot = tid; slot < nValid; slot += kRoundsBlock) {
+                for (uint32_t slot = tid; slot < nValid; slot += kB) {
                     const uint32_t dst = slotDst[slot];
                     const uint32_t src = slotSrc[slot];
                     const uint32_t rot = tile_rot<V>(src);
@@ -665,12 +687,12 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 // hand the stepped queue back in P0 and clear the round counters
                 uint4 *iA = sBuf + A * kTileVecs;
                 const int32_t *dA = sDst + A * (kTile + 4u);
-                for (uint32_t v = tid; v < n * V; v += kRoundsBlock) a.out[v] = iA[v];
-                for (uint32_t i = tid; i < n; i += kRoundsBlock) a.dest[i] = dA[i];
-                for (int e = tid; e < 2 * kSyncGroups * Dp; e += kRoundsBlock) a.grpTot[e] = 0u;
+                for (uint32_t v = tid; v < n * V; v += kB) a.out[v] = iA[v];
+                for (uint32_t i = tid; i < n; i += kB) a.dest[i] = dA[i];
+                for (int e = tid; e < 2 * kSyncGroups * Dp; e += kB) a.grpTot[e] = 0u;
                 xsel = 0u;
             } else {
-                for (int e = tid; e <= R; e += kRoundsBlock) a.inOffset[e] = 0u;
+                for (int e = tid; e <= R; e += kB) a.inOffset[e] = 0u;
             }
             fence_proxy_async_global();
             __threadfence();
@@ -680,8 +702,8 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         const int g = solo ? 1 : G;
         const bool logRound = !pre && a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
         if (logRound) a.roundLog[7 * round + 0] = globaltimer();
-        for (int e = tid; e <= R; e += kRoundsBlock) sOff[e] = a.inOffset[e];
-        for (int e = tid; e < D; e += kRoundsBlock) sTot[e] = 0u;
+        for (int e = tid; e <= R; e += kB) sOff[e] = a.inOffset[e];
+        for (int e = tid; e < D; e += kB) sTot[e] = 0u;
         __syncthreads();
         const uint32_t lo = bound(n, c, g);
         const uint32_t hi = bound(n, c + 1, g);
@@ -717,12 +739,12 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             // (no atomics; for steps of similar cost).  Otherwise each warp
             // takes 32-item chunks from the round's counter.
             unsigned int *ticket = &a.sync->work[it & 1u];
-            uint32_t strided = (uint32_t)c * kRoundsBlock + (uint32_t)warp * 32u;
+            uint32_t strided = (uint32_t)c * kB + (uint32_t)warp * 32u;
             for (;;) {
                 uint32_t base = 0;
                 if (W::kGridStride) {
                     base = strided;
-                    strided += (uint32_t)G * kRoundsBlock;
+                    strided += (uint32_t)G * kB;
                 } else {
                     if (lane == 0) base = atomicAdd(ticket, 32u);
                     base = __shfl_sync(0xFFFFFFFFu, base, 0);
@@ -770,7 +792,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             uint4 *sItems = sBuf + buf * kTileVecs;
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
-                const uint32_t j = (uint32_t)(k * kRoundsBlock + tid);
+                const uint32_t j = (uint32_t)(k * kB + tid);
                 const bool valid = j < cnt;
                 int32_t d = -1;
                 if (valid) {
@@ -813,16 +835,16 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             __syncwarp();
             const int4 *dv = reinterpret_cast<const int4 *>(curDest + lo);
             const uint32_t nv = (hi - lo + 3u) / 4u;
-            for (uint32_t v0 = 0; v0 < nv; v0 += 4u * kRoundsBlock) {
+            for (uint32_t v0 = 0; v0 < nv; v0 += 4u * kB) {
                 int4 x[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const uint32_t v = v0 + (uint32_t)u * kRoundsBlock + tid;
+                    const uint32_t v = v0 + (uint32_t)u * kB + tid;
                     x[u] = v < nv ? __ldcg(dv + v) : make_int4(-1, -1, -1, -1);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const uint32_t i = lo + 4u * (v0 + (uint32_t)u * kRoundsBlock + tid);
+                    const uint32_t i = lo + 4u * (v0 + (uint32_t)u * kB + tid);
                     const int32_t e4[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
 #pragma unroll
                     for (int m = 0; m < 4; ++m)
@@ -830,17 +852,17 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                 }
             }
             __syncthreads();
-            for (int e = tid; e < D; e += kRoundsBlock) {
+            for (int e = tid; e < D; e += kB) {
                 uint32_t sum = 0;
 #pragma unroll
-                for (int ww = 0; ww < kRoundsWarps; ++ww) sum += wc[ww * D + e];
+                for (int ww = 0; ww < kWarps; ++ww) sum += wc[ww * D + e];
                 sTot[e] += sum;
             }
             __syncthreads();
             if (logRound && !fresh) a.roundLog[7 * round + 1] = globaltimer();
         }
         if (!failed) {
-            for (int e = tid; e < D; e += kRoundsBlock) {
+            for (int e = tid; e < D; e += kB) {
                 const uint32_t v = sTot[e];
                 a.tot[(size_t)c * Dp + e] = v;
                 if (v) atomicAdd(&a.grpTot[((it & 1u) * kSyncGroups + grp) * Dp + e], v);
@@ -886,7 +908,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             const uint32_t mRows = (uint32_t)(c - grpStart);
             const uint32_t *gSrc = a.grpTot + (size_t)(it & 1u) * kSyncGroups * Dp;
             const uint32_t *mSrc = a.tot + (size_t)grpStart * Dp;
-            for (int e = tid; e < D; e += kRoundsBlock) {
+            for (int e = tid; e < D; e += kB) {
                 dStart[e] = 0u;
                 dBase[e] = 0u;
             }
@@ -909,7 +931,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
                     failed = true;
                     break;
                 }
-                for (int e = tid; e < D; e += kRoundsBlock) {
+                for (int e = tid; e < D; e += kB) {
                     uint32_t tot = 0, before = 0;
                     for (uint32_t rr = 0; rr < rows; ++rr) {
                         const uint32_t row = r0 + rr;
@@ -928,13 +950,13 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             }
         }
         const uint32_t retiredNow = W::kAppendRetired ? dStart[R] : 0u;
-        const uint32_t nNext = rounds_block_scan(dStart, R, tmp);  // ranks only
+        const uint32_t nNext = rounds_block_scan<kB>(dStart, R, tmp);  // ranks only
         if (W::kAppendRetired && tid == 0) dStart[R] = (uint32_t)retiredSoFar;
         __syncthreads();
-        for (int e = tid; e < D; e += kRoundsBlock) dBase[e] += dStart[e];
+        for (int e = tid; e < D; e += kB) dBase[e] += dStart[e];
         if (c == 0) {
-            for (int e = tid; e < R; e += kRoundsBlock) a.inOffset[e] = dStart[e];
-            for (int e = tid; e < kSyncGroups * Dp; e += kRoundsBlock)
+            for (int e = tid; e < R; e += kB) a.inOffset[e] = dStart[e];
+            for (int e = tid; e < kSyncGroups * Dp; e += kB)
                 a.grpTot[(size_t)((it + 1u) & 1u) * kSyncGroups * Dp + e] = 0u;
             if (tid == 0) a.inOffset[R] = nNext;
         }
@@ -965,7 +987,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
             // consecutive threads write consecutive 16-byte vectors of the
             // destination-grouped tile (coalesced runs per destination)
             const uint32_t total = nValid * V;
-            for (uint32_t v = tid; v < total; v += kRoundsBlock) {
+            for (uint32_t v = tid; v < total; v += kB) {
                 const uint32_t slot = v / V;
                 const uint32_t part = v - slot * V;
                 const uint32_t dst = slotDst[slot];
@@ -1007,7 +1029,7 @@ __global__ void __launch_bounds__(kRoundsBlock, W::kMinBlocksPerSM) rounds_kerne
         // the seeded out-queue has been consumed; with nothing seeded the
         // incoming queue is empty
         if (pre)
-            for (int e = tid; e <= R; e += kRoundsBlock) a.inOffset[e] = 0u;
+            for (int e = tid; e <= R; e += kB) a.inOffset[e] = 0u;
         if (tid == 0) *a.seedCount = 0ull;
     }
     if (c == 0 && tid == 0) {
@@ -1046,11 +1068,11 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     }
     const int R = ctx->numRanks;
     const int D = R + (W::kAppendRetired ? 1 : 0);
-    if (D > 8 * kRoundsBlock) {
-        set_error("persistent rounds: %d destinations exceed %d", D, 8 * kRoundsBlock);
+    if (D > 8 * W::kBlock) {
+        set_error("persistent rounds: %d destinations exceed %d", D, 8 * W::kBlock);
         return RF_ERR_ARG;
     }
-    const RoundsLayout L = rounds_layout(itemBytes, D, work.smemBytes(), kRoundsBlock * W::kItemsPerThread);
+    const RoundsLayout L = rounds_layout(itemBytes, D, work.smemBytes(), W::kBlock * W::kItemsPerThread, W::kBlock / 32);
     int optin = 0;
     RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     auto fn = rounds_kernel<W>;
@@ -1070,11 +1092,11 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     const int carve = smPerSM > 0 ? (int)((100 * need + smPerSM - 1) / smPerSM) : 100;
     RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carve < 100 ? carve : 100));
     int perSM = 0;
-    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
+    RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, W::kBlock, L.total));
     if (perSM < W::kMinBlocksPerSM) {
         // the hint did not leave room for the intended occupancy: leave the carve-out to CUDA
         RF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, -1));
-        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, kRoundsBlock, L.total));
+        RF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSM, fn, W::kBlock, L.total));
     }
     if (perSM < 1) {
         set_error("persistent rounds: the kernel does not fit on an SM");
@@ -1115,7 +1137,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     W w = work;
     void *params[] = {&a, &w};
     time_begin(ctx, kTimeRounds, s);
-    RF_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(fn), dim3(G), dim3(kRoundsBlock), params,
+    RF_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(fn), dim3(G), dim3(W::kBlock), params,
                                         L.total, s));
     count_launch();
     time_end(ctx, kTimeRounds, s);
@@ -1132,5 +1154,28 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     }
     return RF_OK;
 }
+
+// The shapes a policy compiles, in order: launch number v of them, or list
+// them for the host.  Every shape runs the same rounds.
+template <class W, class... Ss>
+struct ShapeList {
+    static constexpr int kCount = sizeof...(Ss);
+    static void infos(ShapeInfo *out)
+    {
+        int i = 0;
+        ((out[i++] = ShapeInfo{Ss::kBlock, Ss::kItemsPerThread, Ss::kMinBlocksPerSM}), ...);
+    }
+    template <class... Args>
+    static rf_status launch(int v, rf_ctx *ctx, const W &w, Args &&...args)
+    {
+        rf_status st = RF_ERR_ARG;
+        int i = 0;
+        bool done = false;
+        // only the chosen shape's launch runs, so each argument is used once
+        ((i++ == v ? (st = launch_rounds(ctx, Ss(w), std::forward<Args>(args)...), done = true) : false), ...);
+        if (!done) set_error("persistent rounds: shape %d of %d", v, kCount);
+        return st;
+    }
+};
 
 }  // namespace rfi

@@ -22,22 +22,25 @@ class PartitionedEARender(torch.autograd.Function):
         rafi.rf_c0_make_bricks(vol, n, brick, bricks, s)
         nrays = width * height * spp
         ray_c = torch.empty(nrays, dtype=torch.float32, device=vol.device)
+        ray_c_lo = torch.empty(nrays, dtype=torch.float32, device=vol.device)
         image = torch.empty(width * height, dtype=torch.float32, device=vol.device)
         with rafi.Context(ranks, 64, nrays) as c:
-            rafi.rf_c3_render(c.handle, bricks, cam, n, brick, width, height, spp, seed, ray_c, image, stream=s)
-        ctx.save_for_backward(bricks, ray_c)
+            rafi.rf_c3_render(c.handle, bricks, cam, n, brick, width, height, spp, seed, ray_c, image, stream=s,
+                              ray_c_lo=ray_c_lo)
+        ctx.save_for_backward(bricks, ray_c, ray_c_lo)
         ctx.meta = (cam, n, brick, width, height, spp, seed)
         return image.view(height, width)
 
     @staticmethod
     def backward(ctx, grad_image):
-        bricks, ray_c = ctx.saved_tensors
+        bricks, ray_c, ray_c_lo = ctx.saved_tensors
         cam, n, brick, width, height, spp, seed = ctx.meta
         s = torch.cuda.current_stream(bricks.device)
         grad = torch.zeros((n, n, n), dtype=torch.float32, device=bricks.device)
         g = grad_image.detach().contiguous().view(-1)
         with rafi.Context((n // brick) ** 3, 64, width * height * spp) as c:
-            rafi.rf_c3_adjoint(c.handle, bricks, cam, n, brick, width, height, spp, seed, ray_c, g, grad, stream=s)
+            rafi.rf_c3_adjoint(c.handle, bricks, cam, n, brick, width, height, spp, seed, ray_c, g, grad, stream=s,
+                               ray_c_lo=ray_c_lo)
         return grad, None, None, None, None, None, None
 
 

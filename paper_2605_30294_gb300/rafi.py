@@ -24,6 +24,8 @@ RF_MAX_ITEM_BYTES = 512
 RF_MAX_RANKS = 1024
 RF_MAX_CAPACITY = 0x7FFFFFFF
 RF_C1_UNIFORM, RF_C1_ZIPF, RF_C1_NBR6 = 0, 1, 2
+RF_POLICY_MICROBENCH, RF_POLICY_STREAMLINES, RF_POLICY_TRANSPORT = 0, 1, 2
+RF_FORM_HOST_LOOP, RF_FORM_PERSISTENT, RF_FORM_GRAPH, RF_FORM_TUNED = 0, 1, 2, 3
 
 
 class RafiError(RuntimeError):
@@ -75,6 +77,9 @@ _SIGS = {
     "rf_set_timing": [_P, _i32],
     "rf_get_timing": [_P, ctypes.POINTER(rf_phase_times), _i32],
     "rf_set_wait_limits": [_P, _u64, _u32],
+    "rf_rounds_shapes": [_i32, _P, _P, _i32],
+    "rf_set_batched_config": [_P, _i32, _i32, _i32],
+    "rf_get_batched_config": [_P, _i32, _P, _P],
     "rf_launch_count": [],
     "rf_last_error": [],
     "rf_partition_static": [_P, _P, _u64, _u32, _i32, _P, _P, _P, _P],
@@ -89,8 +94,8 @@ _SIGS = {
     "rf_c2_make_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c4_render": [_P, _P, _i32, _i32, ctypes.c_float, _i32, _P, _P, _i32, _u32, _P, _i32, _u32, _P, _PU64,
                      _PU64],
-    "rf_c3_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _u32, _P, _PU64],
-    "rf_c3_adjoint": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _P, _u32, _P, _PU64],
+    "rf_c3_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _P, _u32, _P, _PU64],
+    "rf_c3_adjoint": [_P, _P, _P, _i32, _i32, _i32, _i32, _i32, _u32, _P, _P, _P, _P, _u32, _P, _PU64],
     "rf_c2_seed": [_P, _P, _P, _u64, _i32, _i32, _P],
     "rf_c2_trace": [_P, _P, _i32, _i32, ctypes.c_float, _u32, _u32, _P, _u64, _P],
     "rf_c2_run": [_P, _P, _P, _P, _u64, _i32, _i32, ctypes.c_float, _u32, _u32, _P, _i32, _u32, _P, _PU64,
@@ -168,6 +173,25 @@ def rf_last_error() -> str:
 
 def rf_set_wait_limits(ctx: int, spin_cycles: int = 0, missing_arrivals: int = 0) -> None:
     _check("rf_set_wait_limits", lib().rf_set_wait_limits(ctx, spin_cycles, missing_arrivals))
+
+
+def rf_rounds_shapes(policy: int):
+    """The persistent kernel's shapes for a policy: [(threads, items per thread, CTAs per SM), ...]."""
+    n = ctypes.c_int32()
+    _check("rf_rounds_shapes", lib().rf_rounds_shapes(policy, ctypes.byref(n), None, 0))
+    arr = (ctypes.c_int32 * (3 * max(n.value, 1)))()
+    _check("rf_rounds_shapes", lib().rf_rounds_shapes(policy, ctypes.byref(n), ctypes.cast(arr, _P), n.value))
+    return [tuple(arr[3 * i:3 * i + 3]) for i in range(n.value)]
+
+
+def rf_set_batched_config(ctx: int, policy: int, form: int, shape: int) -> None:
+    _check("rf_set_batched_config", lib().rf_set_batched_config(ctx, policy, form, shape))
+
+
+def rf_get_batched_config(ctx: int, policy: int):
+    f, sh = ctypes.c_int32(), ctypes.c_int32()
+    _check("rf_get_batched_config", lib().rf_get_batched_config(ctx, policy, ctypes.byref(f), ctypes.byref(sh)))
+    return f.value, sh.value
 
 
 def rf_launch_count() -> int:
@@ -415,24 +439,33 @@ def rf_c2_run(ctx: int, bricks, seeds, set_ids, count: int, n: int, brick: int, 
 
 
 def rf_c3_render(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, spp: int, seed: int, ray_c,
-                 image, max_rounds: int = 64, stream=None) -> int:
+                 image, max_rounds: int = 64, stream=None, ray_c_lo=None) -> int:
     _need_bricks(bricks, n, brick, "rf_c3_render")
+    nr = max(width, 0) * max(height, 0) * max(spp, 0)
+    _need(ray_c, 4 * nr, "rf_c3_render", "ray_c")
+    _need(ray_c_lo, 4 * nr, "rf_c3_render", "ray_c_lo")
+    _need(image, 4 * max(width, 0) * max(height, 0), "rf_c3_render", "image")
     c = _cam(cam)
     rounds = ctypes.c_uint64()
     _check("rf_c3_render", lib().rf_c3_render(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height, spp,
-                                              seed, ptr(ray_c), ptr(image), max_rounds, stream_handle(stream),
-                                              ctypes.byref(rounds)))
+                                              seed, ptr(ray_c), ptr(ray_c_lo), ptr(image), max_rounds,
+                                              stream_handle(stream), ctypes.byref(rounds)))
     return rounds.value
 
 
 def rf_c3_adjoint(ctx: int, bricks, cam, n: int, brick: int, width: int, height: int, spp: int, seed: int, ray_c,
-                  grad_image, grad_volume, max_rounds: int = 64, stream=None) -> int:
+                  grad_image, grad_volume, max_rounds: int = 64, stream=None, ray_c_lo=None) -> int:
     _need_bricks(bricks, n, brick, "rf_c3_adjoint")
+    nr = max(width, 0) * max(height, 0) * max(spp, 0)
+    _need(ray_c, 4 * nr, "rf_c3_adjoint", "ray_c")
+    _need(ray_c_lo, 4 * nr, "rf_c3_adjoint", "ray_c_lo")
+    _need(grad_image, 4 * max(width, 0) * max(height, 0), "rf_c3_adjoint", "grad_image")
+    _need(grad_volume, 4 * max(n, 0) ** 3, "rf_c3_adjoint", "grad_volume")
     c = _cam(cam)
     rounds = ctypes.c_uint64()
     _check("rf_c3_adjoint", lib().rf_c3_adjoint(ctx, ptr(bricks), ctypes.cast(c, _P), n, brick, width, height, spp,
-                                                seed, ptr(ray_c), ptr(grad_image), ptr(grad_volume), max_rounds,
-                                                stream_handle(stream), ctypes.byref(rounds)))
+                                                seed, ptr(ray_c), ptr(ray_c_lo), ptr(grad_image), ptr(grad_volume),
+                                                max_rounds, stream_handle(stream), ctypes.byref(rounds)))
     return rounds.value
 
 

@@ -426,3 +426,22 @@ def test_batched_retirements_in_the_oracle_order(mode, n):
     assert st == rafi.RF_OK and len(got) == n
     assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
     np.testing.assert_array_equal(got, want["retired_items"])
+
+
+@pytest.mark.parametrize("fuse", [True, False], ids=["step_on_arrival", "step_in_place"])
+@pytest.mark.parametrize("shape", range(len(rafi.rf_rounds_shapes(rafi.RF_POLICY_MICROBENCH))))
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n", [20011, 1 << 20])
+def test_every_persistent_shape_retires_in_the_oracle_order(mode, shape, n, fuse):
+    # each shape the autotuner may pick (threads, tile, CTAs per SM) retires the
+    # oracle's items in the oracle's round-by-round order, every word
+    seed = 43
+    items = inputs.c1_items(n, seed=seed)
+    want = oracle.c1_rounds(items, R, seed, mode, grid=GRID)
+    with rafi.Context(R, 64, n) as ctx:
+        rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_MICROBENCH, rafi.RF_FORM_PERSISTENT, shape)
+        assert rafi.rf_get_batched_config(ctx.handle, rafi.RF_POLICY_MICROBENCH) == (rafi.RF_FORM_PERSISTENT, shape)
+        got, rounds, fwd, st = _run_batched(items, seed, mode, ctx=ctx, fuse=fuse)
+    assert st == rafi.RF_OK and len(got) == n
+    assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
+    np.testing.assert_array_equal(got, want["retired_items"])

@@ -26,7 +26,7 @@ def field(n):
     return _FIELDS[n]
 
 
-def run_gpu(f, n, brick, seeds, set_ids=None, h=0.25, max_steps=2000, spr=0, batched=False):
+def run_gpu(f, n, brick, seeds, set_ids=None, h=0.25, max_steps=2000, spr=0, batched=False, shape=0):
     R = (n // brick) ** 3
     s = stream()
     bricks = torch.zeros(rafi.c2_bricks_floats(n, brick), dtype=torch.float32, device=dev())
@@ -35,6 +35,7 @@ def run_gpu(f, n, brick, seeds, set_ids=None, h=0.25, max_steps=2000, spr=0, bat
     out = torch.zeros((cnt, 8), dtype=torch.int32, device=dev())
     sid = to_dev(np.asarray(set_ids, np.uint32)) if set_ids is not None else None
     with rafi.Context(R, 32, cnt) as ctx:
+        rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_STREAMLINES, rafi.RF_FORM_PERSISTENT, shape)
         st, rounds, fwd = rafi.rf_c2_run(ctx.handle, bricks, to_dev(seeds), sid, cnt, n, brick, h, max_steps, spr,
                                          out, batched, stream=s)
     o = out.cpu().numpy().view(np.uint32)
@@ -117,3 +118,17 @@ def test_full_size_sampled():
     sample = np.random.default_rng(1).choice(count, size=256, replace=False)
     want = oracle.c2_trace(f, seeds[sample], brick, 0.25, 2000)
     check_against_oracle(got, want, idx=sample)
+
+
+@pytest.mark.parametrize("shape", range(len(rafi.rf_rounds_shapes(rafi.RF_POLICY_STREAMLINES))))
+@pytest.mark.parametrize("spr", [0, 1])
+def test_every_persistent_shape_matches_oracle(shape, spr):
+    # each shape the autotuner may pick (threads, tile, CTAs per SM) gives the
+    # oracle's particles exactly; RF_FORM_TUNED runs the form set on the context
+    n, brick = 64, 16
+    f = field(n)
+    seeds = inputs.c2_seeds(3000, n, seed=6)
+    max_steps = 600 if spr else 2000
+    want = oracle.c2_trace(f, seeds, brick, 0.25, max_steps)
+    got = run_gpu(f, n, brick, seeds, max_steps=max_steps, spr=spr, batched=rafi.RF_FORM_TUNED, shape=shape)
+    check_against_oracle(got, want)

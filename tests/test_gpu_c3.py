@@ -2,10 +2,21 @@
 
 Forward: images and per-sample colours against the oracle's float render
 (max relative error 1e-5; the sums are in the same order, expf may differ by
-an ulp).  Adjoint: against the oracle's FP64 reverse-accumulation adjoint
-(max-norm relative error 1e-4) and, at the configured size (256^3 over 2x2x2
-ranks, 512x512 at 4 spp), against central finite differences (eps = 1e-3,
-loss summed in FP64) on 32 voxels (relative error 1e-2).
+an ulp); the compensated forward returns the same colours bit for bit.
+
+Adjoint, voxel by voxel against the oracle's FP64 reverse-accumulation
+adjoint: |got - want| <= 1e-4 |want| + 1e-6 K, where K is the voxel's sum of
+absolute contributions (from the oracle).  A voxel's gradient is a sum of
+contributions of both signs, so float arithmetic can only be asked to get
+it right relative to that scale: every float term carries a relative error
+of a few 2^-24, and the atomic adds round each partial sum once more.  The
+bound is checked on a 32^3 copy and at the configured size (256^3 over
+2x2x2 ranks, 512x512 at 4 spp), where the late samples of opaque rays are
+the longest suffixes.  Also at the configured size: central finite
+differences of the FP64 loss (eps = 1e-3) on 32 of the strongest voxels
+(relative 1e-2) and on 32 voxels drawn from every voxel the rays touch,
+weak ones included, within 1e-2 |g| + 1e-4 max|g| (the finite difference
+itself is no closer than that for weak voxels: float images round the loss).
 """
 import numpy as np
 import pytest
@@ -19,17 +30,36 @@ from gpu_util import dev, stream, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def gpu_render(vol, cam, brick, w, h, spp, seed=3):
+def gpu_render(vol, cam, brick, w, h, spp, seed=3, lo=False):
     n = vol.shape[0]
     R = (n // brick) ** 3
     s = stream()
     bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     rafi.rf_c0_make_bricks(to_dev(vol.reshape(-1)), n, brick, bricks, s)
     rayC = torch.zeros(w * h * spp, dtype=torch.float32, device=dev())
+    rayClo = torch.zeros(w * h * spp, dtype=torch.float32, device=dev()) if lo else None
     img = torch.zeros(w * h, dtype=torch.float32, device=dev())
     with rafi.Context(R, 64, w * h * spp) as ctx:
-        rounds = rafi.rf_c3_render(ctx.handle, bricks, cam, n, brick, w, h, spp, seed, rayC, img, stream=s)
+        rounds = rafi.rf_c3_render(ctx.handle, bricks, cam, n, brick, w, h, spp, seed, rayC, img, stream=s,
+                                   ray_c_lo=rayClo)
+    if lo:
+        return img.cpu().numpy(), rayC.cpu().numpy(), bricks, rayC, rounds, rayClo
     return img.cpu().numpy(), rayC.cpu().numpy(), bricks, rayC, rounds
+
+
+def gpu_adjoint(vol, cam, brick, w, h, spp, gimg, lo=True):
+    n = vol.shape[0]
+    _, _, bricks, rayC, _, rayClo = gpu_render(vol, cam, brick, w, h, spp, lo=True)
+    grad = torch.zeros(n ** 3, dtype=torch.float32, device=dev())
+    with rafi.Context((n // brick) ** 3, 64, w * h * spp) as ctx:
+        rafi.rf_c3_adjoint(ctx.handle, bricks, cam, n, brick, w, h, spp, 3, rayC, to_dev(gimg), grad,
+                           stream=stream(), ray_c_lo=rayClo if lo else None)
+    return grad.cpu().numpy().reshape(n, n, n).astype(np.float64)
+
+
+def adjoint_excess(got, want, kappa):
+    """Largest |got - want| / (1e-4 |want| + 1e-6 kappa) over the voxels (1 = at the bound)."""
+    return float(np.max(np.abs(got - want) / (1e-4 * np.abs(want) + 1e-6 * kappa + 1e-300)))
 
 
 def test_forward_matches_oracle():
@@ -44,6 +74,21 @@ def test_forward_matches_oracle():
     assert wimg.max() > 0.05
 
 
+def test_compensated_forward_keeps_the_colours():
+    # with the low parts requested, C is still the plain float sum, bit for
+    # bit, and each low part is below the rounding the sum can have made
+    n, brick, w, h, spp = 64, 32, 64, 48, 4
+    vol = inputs.c0_volume(n)
+    cam = inputs.c0_camera(n, w, h)
+    img, rayC, _, _, _ = gpu_render(vol, cam, brick, w, h, spp)
+    img2, rayC2, _, _, _, lo = gpu_render(vol, cam, brick, w, h, spp, lo=True)
+    np.testing.assert_array_equal(rayC.view(np.uint32), rayC2.view(np.uint32))
+    np.testing.assert_array_equal(img.view(np.uint32), img2.view(np.uint32))
+    lo = lo.cpu().numpy()
+    assert np.all(np.abs(lo) <= 1e-4 * np.abs(rayC) + 1e-30)
+    assert np.any(lo != 0)
+
+
 def test_forward_partition_independent():
     n, w, h, spp = 64, 48, 48, 2
     vol = inputs.c0_volume(n)
@@ -55,21 +100,22 @@ def test_forward_partition_independent():
     np.testing.assert_array_equal(a.view(np.uint32), c.view(np.uint32))
 
 
-def test_adjoint_matches_fp64_oracle():
-    n, brick, w, h, spp = 32, 16, 32, 32, 4
-    vol = inputs.c0_volume(n) * 3.0
+@pytest.mark.parametrize("n,brick,w,h,scale", [(32, 16, 32, 32, 3.0), (256, 128, 512, 512, 1.0)],
+                         ids=["32^3_dense", "configured_256^3"])
+def test_adjoint_matches_fp64_oracle_voxel_by_voxel(n, brick, w, h, scale):
+    spp = 4
+    vol = (inputs.c0_volume(n) * scale).astype(np.float32)
     cam = inputs.c0_camera(n, w, h)
-    _, _, bricks, rayC, _ = gpu_render(vol, cam, brick, w, h, spp)
     gimg = np.random.default_rng(2).normal(size=w * h).astype(np.float32)
-    grad = torch.zeros(n ** 3, dtype=torch.float32, device=dev())
-    s = stream()
-    with rafi.Context((n // brick) ** 3, 64, w * h * spp) as ctx:
-        rafi.rf_c3_adjoint(ctx.handle, bricks, cam, n, brick, w, h, spp, 3, rayC, to_dev(gimg), grad, stream=s)
-    got = grad.cpu().numpy().reshape(n, n, n)
+    got = gpu_adjoint(vol, cam, brick, w, h, spp, gimg)
     dLdC = np.repeat(gimg.astype(np.float64) / spp, spp)
-    want, _ = oracle.c3_adjoint_f64(vol, cam, w, h, spp, dLdC)
-    err = np.abs(got - want).max() / np.abs(want).max()
-    assert err <= 1e-4, err
+    want, _, kappa = oracle.c3_adjoint_f64(vol, cam, w, h, spp, dLdC, with_abs=True)
+    assert np.all(kappa >= np.abs(want) * (1 - 1e-12))
+    assert np.count_nonzero(want) > 0.5 * np.count_nonzero(kappa)
+    ex = adjoint_excess(got, want, kappa)
+    assert ex <= 1.0, ex
+    # and in the max-norm over the grid
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
 
 
 def test_autograd_and_finite_differences_at_full_size():
@@ -91,17 +137,24 @@ def test_autograd_and_finite_differences_at_full_size():
         return ((im - target.cpu().numpy().astype(np.float64)) ** 2).mean()
 
     rng = np.random.default_rng(7)
-    strong = np.argwhere(np.abs(grad) > 0.1 * np.abs(grad).max())
-    picks = strong[rng.choice(len(strong), size=32, replace=False)]
+    gmax = float(np.abs(grad).max())
+    strong = np.argwhere(np.abs(grad) > 0.1 * gmax)
+    touched = np.argwhere(grad != 0)
     eps = 1e-3
     base = to_dev(vol)
-    worst = 0.0
-    for z, y, x in picks:
+
+    def fd_at(z, y, x):
         vp = base.clone()
         vm = base.clone()
         vp[z, y, x] += eps
         vm[z, y, x] -= eps
         step = float(vp[z, y, x].item()) - float(vm[z, y, x].item())
-        fd = (loss64(vp) - loss64(vm)) / step
-        worst = max(worst, abs(fd - grad[z, y, x]) / abs(grad[z, y, x]))
-    assert worst <= 1e-2, worst
+        return (loss64(vp) - loss64(vm)) / step
+
+    worst_strong = max(abs(fd_at(*v) - grad[tuple(v)]) / abs(grad[tuple(v)])
+                       for v in strong[rng.choice(len(strong), size=32, replace=False)])
+    assert worst_strong <= 1e-2, worst_strong
+    # voxels drawn from all the rays touch, weak ones included
+    worst_any = max(abs(fd_at(*v) - grad[tuple(v)]) / (1e-2 * abs(grad[tuple(v)]) + 1e-4 * gmax)
+                    for v in touched[rng.choice(len(touched), size=32, replace=False)])
+    assert worst_any <= 1.0, worst_any

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 SMALL_VIEWS = ((64, 64), (48, 32), (32, 32), (80, 45))
 
 
-def gpu_render(vol, smax, views, brick, spp, batched=True, seed=4):
+def gpu_render(vol, smax, views, brick, spp, batched=True, seed=4, shape=0):
     n = vol.shape[0]
     R = (n // brick) ** 3
     s = stream()
@@ -32,6 +32,7 @@ def gpu_render(vol, smax, views, brick, spp, batched=True, seed=4):
     score = torch.zeros(npix, dtype=torch.float32, device=dev())
     paths = npix * spp
     with rafi.Context(R, 64, paths) as ctx:
+        rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_TRANSPORT, rafi.RF_FORM_PERSISTENT, shape)
         rounds, fwd = rafi.rf_c4_render(ctx.handle, bricks, n, brick, smax, views, spp, seed, score, batched,
                                         stream=s)
     return score.cpu().numpy() / spp, rounds, fwd
@@ -81,3 +82,17 @@ def test_full_size_crop():
     got = img[base:base + w * h].reshape(h, w)[y0:y0 + 64, x0:x0 + 64]
     mae = np.abs(got - want).mean()
     assert mae < 1e-3, mae
+
+
+@pytest.mark.parametrize("shape", range(len(rafi.rf_rounds_shapes(rafi.RF_POLICY_TRANSPORT))))
+def test_every_persistent_shape_gives_the_host_loop_image(shape):
+    # paths are drawn from counter-based streams keyed by (pixel, sample, bounce,
+    # event), so every shape of the persistent kernel renders the host loop's
+    # image bit for bit
+    n = 64
+    vol, smax = inputs.c4_volume(n)
+    views = inputs.c4_views(n, sizes=((48, 32), (24, 24)))
+    a, ra, fa = gpu_render(vol, smax, views, 16, 4, batched=0)
+    b, rb, fb = gpu_render(vol, smax, views, 16, 4, batched=rafi.RF_FORM_TUNED, shape=shape)
+    np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert (ra, fa) == (rb, fb)

@@ -80,3 +80,20 @@ def test_target_volume_recipe():
     ratio = t / np.maximum(vol, 1e-30)
     assert np.all((ratio >= 0.9 - 1e-6) & (ratio <= 1.1 + 1e-6))
     assert abs(ratio.mean() - 1.0) < 0.01
+
+
+def test_fp64_adjoint_absolute_sums():
+    # gabs bounds |grad| voxel by voxel, does not change with the sign of
+    # dL/dC while grad flips, and scales with |dL/dC|
+    n, w, h, spp = 16, 12, 12, 2
+    vol = inputs.c0_volume(n) * 4.0
+    cam = inputs.c0_camera(n, w, h)
+    g = np.random.default_rng(5).normal(size=w * h * spp)
+    grad, _, ab = oracle.c3_adjoint_f64(vol, cam, w, h, spp, g, with_abs=True)
+    grad2, _, ab2 = oracle.c3_adjoint_f64(vol, cam, w, h, spp, -2.0 * g, with_abs=True)
+    grad3, _ = oracle.c3_adjoint_f64(vol, cam, w, h, spp, g)
+    np.testing.assert_array_equal(grad, grad3)
+    assert np.all(ab >= np.abs(grad) - 1e-15 * ab.max())
+    assert np.count_nonzero(ab) > 0 and np.any(ab > np.abs(grad) * (1 + 1e-9))
+    np.testing.assert_allclose(ab2, 2.0 * ab, rtol=1e-12)
+    np.testing.assert_allclose(grad2, -2.0 * grad, rtol=1e-12, atol=1e-15 * ab.max())
