@@ -300,7 +300,8 @@ def c3_adjoint_f64(vol: np.ndarray, cam: np.ndarray, width: int, height: int, sp
                    seed: int = 3, with_abs: bool = False):
     """Reference gradient dL/dvol (float64, N^3) for per-sample dL/dC (W*H*spp)
     (Sec. 5.2 integration, adjoint by reverse accumulation).  Returns (grad, acc),
-    or (grad, acc, gabs) with gabs the per-voxel sum of |contributions|."""
+    or (grad, acc, gabs) with gabs the per-voxel sum, over the contributions,
+    of |dL/dC| x (|first part| + |0.5 S|) x weight (the rounding scale)."""
     vol = _c(vol, np.float32)
     cam = _c(cam, np.float32)
     g = _c(dLdC, np.float64)

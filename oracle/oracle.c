@@ -600,9 +600,11 @@ void or_c3_render(const float *vol, int32_t N, const float *cam, int32_t W, int3
  * then k from last to first with the suffix S = sum_{j>k} T_j alpha_j c_j:
  *   dC/dsigma_k = T_k (0.5 e_k c_k + alpha_k * 20) - 0.5 S,
  * scattered to the 8 voxels with the trilinear weights (clamped taps add).
- * gabs (may be NULL) receives, per voxel, the sum of the absolute values of
- * the same contributions: the scale against which a float sum of them can
- * be judged (it is not part of the gradient).
+ * gabs (may be NULL) receives, per voxel, the same sum taken over the
+ * magnitudes of the parts, |dLdC| (|T_k (0.5 e_k c_k + alpha_k * 20)| +
+ * |0.5 S|) weight: the scale against which a float evaluation and sum of the
+ * contributions can be judged, since each is the difference of its two parts
+ * (it is not part of the gradient).
  * Returns the loss-independent sum of dLdC * C (a consistency value). */
 double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t W, int32_t H, int32_t spp,
                          uint32_t seed, const double *dLdC, double *grad, double *gabs)
@@ -653,7 +655,9 @@ double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t 
                 double S = 0.0;
                 for (int32_t k = K - 1; k >= 0; --k) {
                     double e = exp(-sg[k] * 0.5), al = 1.0 - e, cc = sg[k] * 20.0;
-                    double dCds = Tk[k] * (0.5 * e * cc + al * 20.0) - 0.5 * S;
+                    double first = Tk[k] * (0.5 * e * cc + al * 20.0);
+                    double dCds = first - 0.5 * S;
+                    double scale = fabs(g) * (fabs(first) + 0.5 * fabs(S));
                     S += Tk[k] * al * cc;
                     double gs = g * dCds;
                     double w[3];
@@ -670,7 +674,7 @@ double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t 
                         double wt = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
                                     ((c & 4) ? w[2] : 1.0 - w[2]);
                         grad[((size_t)iz * N + iy) * N + ix] += gs * wt;
-                        if (gabs) gabs[((size_t)iz * N + iy) * N + ix] += fabs(gs * wt);
+                        if (gabs) gabs[((size_t)iz * N + iy) * N + ix] += scale * wt;
                     }
                 }
             }

@@ -83,8 +83,9 @@ def test_target_volume_recipe():
 
 
 def test_fp64_adjoint_absolute_sums():
-    # gabs bounds |grad| voxel by voxel, does not change with the sign of
-    # dL/dC while grad flips, and scales with |dL/dC|
+    # gabs (a sum over the magnitudes of each contribution's two parts) bounds
+    # |grad| voxel by voxel, does not change with the sign of dL/dC while grad
+    # flips, and scales with |dL/dC|
     n, w, h, spp = 16, 12, 12, 2
     vol = inputs.c0_volume(n) * 4.0
     cam = inputs.c0_camera(n, w, h)
