@@ -21,7 +21,9 @@
 // each T alpha c to (C, Clo) and may return Clo beside C (C itself is the
 // plain float sum, bit for bit); the adjoint starts from (C, Clo) and takes
 // each T alpha c off again, so the suffix it uses is exact up to the rounding
-// of the individual terms.
+// of the individual terms.  The derivative's alpha term takes alpha from
+// expm1f (1 - e loses it where sigma is tiny); the suffix keeps subtracting
+// the forward's own float terms.
 //
 // Built with -fmad=false (the written float order, as the oracle's).
 #include "internal.cuh"
@@ -276,7 +278,10 @@ __global__ void __launch_bounds__(kBlock) march_kernel(EAParams P, rf_device_que
                 acc = two_sum(acc, -contrib, err);
                 lo = lo + err;
                 const float suffix = acc + lo;
-                const float dC = T * ((0.5f * e) * cc + al * 20.0f) - 0.5f * suffix;
+                // alpha in the derivative from expm1f: where sigma is tiny, 1 - e
+                // rounds to 0 and would drop the alpha * 20 term, half of dC/dsigma
+                const float alD = -expm1f(-(sg * 0.5f));
+                const float dC = T * ((0.5f * e) * cc + alD * 20.0f) - 0.5f * suffix;
                 grad_add(P.grad, P.N, ga, tp, r.g * dC);
             } else if (COMP) {
                 float err;

@@ -5,18 +5,20 @@ Forward: images and per-sample colours against the oracle's float render
 an ulp); the compensated forward returns the same colours bit for bit.
 
 Adjoint, voxel by voxel against the oracle's FP64 reverse-accumulation
-adjoint: |got - want| <= 1e-4 |want| + 1e-6 K, where K is the voxel's sum of
-absolute contributions (from the oracle).  A voxel's gradient is a sum of
-contributions of both signs, so float arithmetic can only be asked to get
-it right relative to that scale: every float term carries a relative error
-of a few 2^-24, and the atomic adds round each partial sum once more.  The
-bound is checked on a 32^3 copy and at the configured size (256^3 over
-2x2x2 ranks, 512x512 at 4 spp), where the late samples of opaque rays are
-the longest suffixes.  Also at the configured size: central finite
-differences of the FP64 loss (eps = 1e-3) on 32 of the strongest voxels
-(relative 1e-2) and on 32 voxels drawn from every voxel the rays touch,
-weak ones included, within 1e-2 |g| + 1e-4 max|g| (the finite difference
-itself is no closer than that for weak voxels: float images round the loss).
+adjoint: |got - want| <= 1e-4 |want| + 2e-5 K, where K (from the oracle) sums
+over the voxel's contributions |dL/dC| (|T (0.5 e c + 20 alpha)| + |0.5 S|)
+times the trilinear weight.  Each contribution is the difference of those
+two parts and a voxel sums contributions of both signs, so float arithmetic
+can only be held to that scale: each part carries a relative error of a few
+2^-24, and the atomic adds round every partial sum again (a few hundred
+adds of 2^-24 each make the 2e-5).  The bound is checked on a 32^3 copy and
+at the configured size (256^3 over 2x2x2 ranks, 512x512 at 4 spp), where the
+late samples of opaque rays have the longest, smallest suffixes.  Also at the
+configured size: central finite differences of the FP64 loss (eps = 1e-3) on
+32 of the strongest voxels (relative 1e-2), and Richardson-extrapolated
+central differences ((4 D(eps/2) - D(eps)) / 3, which removes the eps^2 term
+that dominates for weak voxels) on 32 voxels drawn from every voxel the rays
+touch, within 1e-2 |g| + 1e-5 max|g|.
 """
 import numpy as np
 import pytest
@@ -58,8 +60,8 @@ def gpu_adjoint(vol, cam, brick, w, h, spp, gimg, lo=True):
 
 
 def adjoint_excess(got, want, kappa):
-    """Largest |got - want| / (1e-4 |want| + 1e-6 kappa) over the voxels (1 = at the bound)."""
-    return float(np.max(np.abs(got - want) / (1e-4 * np.abs(want) + 1e-6 * kappa + 1e-300)))
+    """Largest |got - want| / (1e-4 |want| + 2e-5 kappa) over the voxels (1 = at the bound)."""
+    return float(np.max(np.abs(got - want) / (1e-4 * np.abs(want) + 2e-5 * kappa + 1e-300)))
 
 
 def test_forward_matches_oracle():
@@ -143,18 +145,21 @@ def test_autograd_and_finite_differences_at_full_size():
     eps = 1e-3
     base = to_dev(vol)
 
-    def fd_at(z, y, x):
+    def fd_at(z, y, x, e=eps):
         vp = base.clone()
         vm = base.clone()
-        vp[z, y, x] += eps
-        vm[z, y, x] -= eps
+        vp[z, y, x] += e
+        vm[z, y, x] -= e
         step = float(vp[z, y, x].item()) - float(vm[z, y, x].item())
         return (loss64(vp) - loss64(vm)) / step
+
+    def richardson_at(z, y, x):
+        return (4.0 * fd_at(z, y, x, eps / 2) - fd_at(z, y, x, eps)) / 3.0
 
     worst_strong = max(abs(fd_at(*v) - grad[tuple(v)]) / abs(grad[tuple(v)])
                        for v in strong[rng.choice(len(strong), size=32, replace=False)])
     assert worst_strong <= 1e-2, worst_strong
     # voxels drawn from all the rays touch, weak ones included
-    worst_any = max(abs(fd_at(*v) - grad[tuple(v)]) / (1e-2 * abs(grad[tuple(v)]) + 1e-4 * gmax)
+    worst_any = max(abs(richardson_at(*v) - grad[tuple(v)]) / (1e-2 * abs(grad[tuple(v)]) + 1e-5 * gmax)
                     for v in touched[rng.choice(len(touched), size=32, replace=False)])
     assert worst_any <= 1.0, worst_any
