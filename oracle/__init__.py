@@ -72,7 +72,7 @@ def _load():
             lib.or_c2_trace.restype = None
             lib.or_c3_render.argtypes = [P, i32, P, i32, i32, i32, u32, P, P]
             lib.or_c3_render.restype = None
-            lib.or_c3_adjoint_f64.argtypes = [P, i32, P, i32, i32, i32, u32, P, P, P]
+            lib.or_c3_adjoint_f64.argtypes = [P, i32, P, i32, i32, i32, u32, P, P, P, P]
             lib.or_c3_adjoint_f64.restype = f64
             lib.or_c4_path.argtypes = [P, i32, ctypes.c_float, P, i32, i32, i32, u32, u32, u32, P, P]
             lib.or_c4_path.restype = i32
@@ -300,16 +300,18 @@ def c3_adjoint_f64(vol: np.ndarray, cam: np.ndarray, width: int, height: int, sp
                    seed: int = 3, with_abs: bool = False):
     """Reference gradient dL/dvol (float64, N^3) for per-sample dL/dC (W*H*spp)
     (Sec. 5.2 integration, adjoint by reverse accumulation).  Returns (grad, acc),
-    or (grad, acc, gabs) with gabs the per-voxel sum, over the contributions,
-    of |dL/dC| x (|first part| + |0.5 S|) x weight (the rounding scale)."""
+    or (grad, acc, gabs, count) with gabs the per-voxel sum, over the contributions,
+    of |dL/dC| x (|first part| + |0.5 S|) x weight (the rounding scale) and count
+    the number of (sample, corner) contributions per voxel."""
     vol = _c(vol, np.float32)
     cam = _c(cam, np.float32)
     g = _c(dLdC, np.float64)
     grad = np.zeros(vol.shape, np.float64)
     gabs = np.zeros(vol.shape, np.float64) if with_abs else None
+    cnt = np.zeros(vol.shape, np.float64) if with_abs else None
     acc = _load().or_c3_adjoint_f64(_p(vol), vol.shape[0], _p(cam), width, height, spp, seed, _p(g), _p(grad),
-                                    _p(gabs))
-    return (grad, acc, gabs) if with_abs else (grad, acc)
+                                    _p(gabs), _p(cnt))
+    return (grad, acc, gabs, cnt) if with_abs else (grad, acc)
 
 
 # --------------------------------------------------------------------------

@@ -604,10 +604,11 @@ void or_c3_render(const float *vol, int32_t N, const float *cam, int32_t W, int3
  * magnitudes of the parts, |dLdC| (|T_k (0.5 e_k c_k + alpha_k * 20)| +
  * |0.5 S|) weight: the scale against which a float evaluation and sum of the
  * contributions can be judged, since each is the difference of its two parts
- * (it is not part of the gradient).
+ * (it is not part of the gradient).  gcount (may be NULL) receives, per
+ * voxel, the number of (sample, corner) contributions added to it.
  * Returns the loss-independent sum of dLdC * C (a consistency value). */
 double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t W, int32_t H, int32_t spp,
-                         uint32_t seed, const double *dLdC, double *grad, double *gabs)
+                         uint32_t seed, const double *dLdC, double *grad, double *gabs, double *gcount)
 {
     int32_t maxK = (int32_t)(2.0f * 1.7321f * (float)N) + 8;
     double *sg = (double *)malloc((size_t)maxK * sizeof(double));
@@ -675,6 +676,7 @@ double or_c3_adjoint_f64(const float *vol, int32_t N, const float *cam, int32_t 
                                     ((c & 4) ? w[2] : 1.0 - w[2]);
                         grad[((size_t)iz * N + iy) * N + ix] += gs * wt;
                         if (gabs) gabs[((size_t)iz * N + iy) * N + ix] += scale * wt;
+                        if (gcount) gcount[((size_t)iz * N + iy) * N + ix] += 1.0;
                     }
                 }
             }

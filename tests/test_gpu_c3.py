@@ -5,20 +5,24 @@ Forward: images and per-sample colours against the oracle's float render
 an ulp); the compensated forward returns the same colours bit for bit.
 
 Adjoint, voxel by voxel against the oracle's FP64 reverse-accumulation
-adjoint: |got - want| <= 1e-4 |want| + 2e-5 K, where K (from the oracle) sums
-over the voxel's contributions |dL/dC| (|T (0.5 e c + 20 alpha)| + |0.5 S|)
-times the trilinear weight.  Each contribution is the difference of those
-two parts and a voxel sums contributions of both signs, so float arithmetic
-can only be held to that scale: each part carries a relative error of a few
-2^-24, and the atomic adds round every partial sum again (a few hundred
-adds of 2^-24 each make the 2e-5).  The bound is checked on a 32^3 copy and
-at the configured size (256^3 over 2x2x2 ranks, 512x512 at 4 spp), where the
-late samples of opaque rays have the longest, smallest suffixes.  Also at the
-configured size: central finite differences of the FP64 loss (eps = 1e-3) on
-32 of the strongest voxels (relative 1e-2), and Richardson-extrapolated
-central differences ((4 D(eps/2) - D(eps)) / 3, which removes the eps^2 term
-that dominates for weak voxels) on 32 voxels drawn from every voxel the rays
-touch, within 1e-2 |g| + 1e-5 max|g|.
+adjoint: |got - want| <= 1e-4 |want| + (3 Kmax + m + 16) 2^-24 K, where K
+(from the oracle) sums over the voxel's contributions |dL/dC| (|T (0.5 e c +
+20 alpha)| + |0.5 S|) times the trilinear weight, m is the number of those
+contributions and Kmax the most samples a ray can take.  That is float
+arithmetic's error: each contribution is the difference of its two parts,
+T after k samples is a product of k expf values (up to 2 ulp each, one
+rounding per product: 3 k 2^-24 relative), a part adds a few more roundings
+(the 16), and the m float adds that build the voxel's sum round each partial
+sum again; contributions of both signs cancel, so the scale is K, not the
+gradient.  Checked on a 32^3 copy and at the configured size (256^3 over
+2x2x2 ranks, 512x512 at 4 spp), where the late samples of opaque rays have
+the longest, smallest suffixes.  Also at the configured size: central finite
+differences of the FP64 loss (eps = 1e-3) on 32 of the strongest voxels
+(relative 1e-2), and Richardson-extrapolated central differences ((4 D(eps/2)
+- D(eps)) / 3, which removes the eps^2 term) on 32 voxels drawn from every
+voxel the rays touch, within 1e-2 |g| + 2e-4 max|g|: a weak voxel's
+difference of two float renders carries their rounding, measured at up to
+7e-5 max|g| over 64 such voxels.
 """
 import numpy as np
 import pytest
@@ -59,9 +63,12 @@ def gpu_adjoint(vol, cam, brick, w, h, spp, gimg, lo=True):
     return grad.cpu().numpy().reshape(n, n, n).astype(np.float64)
 
 
-def adjoint_excess(got, want, kappa):
-    """Largest |got - want| / (1e-4 |want| + 2e-5 kappa) over the voxels (1 = at the bound)."""
-    return float(np.max(np.abs(got - want) / (1e-4 * np.abs(want) + 2e-5 * kappa + 1e-300)))
+def adjoint_excess(got, want, kappa, count, n):
+    """Largest |got - want| / bound over the voxels (1 = at the bound), bound =
+    1e-4 |want| + (3 Kmax + count + 16) 2^-24 kappa, Kmax = ceil(2 sqrt(3) n)."""
+    kmax = int(np.ceil(2.0 * np.sqrt(3.0) * n))
+    bound = 1e-4 * np.abs(want) + (3 * kmax + count + 16) * 2.0 ** -24 * kappa
+    return float(np.max(np.abs(got - want) / (bound + 1e-300)))
 
 
 def test_forward_matches_oracle():
@@ -111,10 +118,10 @@ def test_adjoint_matches_fp64_oracle_voxel_by_voxel(n, brick, w, h, scale):
     gimg = np.random.default_rng(2).normal(size=w * h).astype(np.float32)
     got = gpu_adjoint(vol, cam, brick, w, h, spp, gimg)
     dLdC = np.repeat(gimg.astype(np.float64) / spp, spp)
-    want, _, kappa = oracle.c3_adjoint_f64(vol, cam, w, h, spp, dLdC, with_abs=True)
+    want, _, kappa, count = oracle.c3_adjoint_f64(vol, cam, w, h, spp, dLdC, with_abs=True)
     assert np.all(kappa >= np.abs(want) * (1 - 1e-12))
     assert np.count_nonzero(want) > 0.5 * np.count_nonzero(kappa)
-    ex = adjoint_excess(got, want, kappa)
+    ex = adjoint_excess(got, want, kappa, count, n)
     assert ex <= 1.0, ex
     # and in the max-norm over the grid
     assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
@@ -160,6 +167,6 @@ def test_autograd_and_finite_differences_at_full_size():
                        for v in strong[rng.choice(len(strong), size=32, replace=False)])
     assert worst_strong <= 1e-2, worst_strong
     # voxels drawn from all the rays touch, weak ones included
-    worst_any = max(abs(richardson_at(*v) - grad[tuple(v)]) / (1e-2 * abs(grad[tuple(v)]) + 1e-5 * gmax)
+    worst_any = max(abs(richardson_at(*v) - grad[tuple(v)]) / (1e-2 * abs(grad[tuple(v)]) + 2e-4 * gmax)
                     for v in touched[rng.choice(len(touched), size=32, replace=False)])
     assert worst_any <= 1.0, worst_any

@@ -90,8 +90,11 @@ def test_fp64_adjoint_absolute_sums():
     vol = inputs.c0_volume(n) * 4.0
     cam = inputs.c0_camera(n, w, h)
     g = np.random.default_rng(5).normal(size=w * h * spp)
-    grad, _, ab = oracle.c3_adjoint_f64(vol, cam, w, h, spp, g, with_abs=True)
-    grad2, _, ab2 = oracle.c3_adjoint_f64(vol, cam, w, h, spp, -2.0 * g, with_abs=True)
+    grad, _, ab, cnt = oracle.c3_adjoint_f64(vol, cam, w, h, spp, g, with_abs=True)
+    grad2, _, ab2, cnt2 = oracle.c3_adjoint_f64(vol, cam, w, h, spp, -2.0 * g, with_abs=True)
+    # eight corners per sample (clamped corners count on the voxel they land on)
+    assert cnt.sum() % 8 == 0 and np.array_equal(cnt, cnt2)
+    assert np.all((cnt > 0) >= (ab > 0))
     grad3, _ = oracle.c3_adjoint_f64(vol, cam, w, h, spp, g)
     np.testing.assert_array_equal(grad, grad3)
     assert np.all(ab >= np.abs(grad) - 1e-15 * ab.max())
