@@ -333,9 +333,12 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
     bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
     rafi.rf_c0_make_bricks(dvol, n, brick, bricks, s)
     image = torch.zeros(w * h, dtype=torch.float32, device="cuda")
+    sbricks = torch.zeros(rafi.c0_scalar_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
+    rafi.rf_c0_make_scalar_bricks(dvol, n, brick, sbricks, s)
     out = {}
     with rafi.Context(8, 48, w * h) as ctx:
-        for name, render in (("host_loop", rafi.rf_c0_render), ("graph", rafi.rf_c0_render_graph)):
+        for name, render in (("host_loop", rafi.rf_c0_render), ("graph", rafi.rf_c0_render_graph),
+                             ("tma", lambda c, b, *a, **k: rafi.rf_c0_render_tma(c, sbricks, *a, **k))):
             for _ in range(3):
                 render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
             torch.cuda.synchronize()
@@ -346,7 +349,8 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
             e1.record(s)
             torch.cuda.synchronize()
             out[name] = e0.elapsed_time(e1) / reps
-    return w * h / (out["host_loop"] * 1e-3), out["host_loop"], w * h / (out["graph"] * 1e-3), out["graph"]
+    return (w * h / (out["host_loop"] * 1e-3), out["host_loop"], w * h / (out["graph"] * 1e-3), out["graph"],
+            w * h / (out["tma"] * 1e-3), out["tma"])
 
 
 LOG_CAP = 4096  # rounds logged by the persistent kernel
@@ -766,7 +770,7 @@ def run_ours(args):
                          "into the pinned host buffer, read-back of the counts; rest = launches, host calls "
                          "and synchronisation"}
 
-    rays_s, c0_ms, rays_g, c0_ms_g = c0_rays_per_s(torch, rafi, inputs, s)
+    rays_s, c0_ms, rays_g, c0_ms_g, rays_t, c0_ms_t = c0_rays_per_s(torch, rafi, inputs, s)
     ctx.close()
     del d_items, retired, h_items, h_ret
     torch.cuda.empty_cache()
@@ -860,7 +864,10 @@ def run_ours(args):
         "rays_per_s": {"value": rays_s, "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
                        "ms_per_frame": c0_ms, "form": "host loop (rf_c0_render)",
                        "graph": {"value": rays_g, "ms_per_frame": c0_ms_g,
-                                 "form": "rounds in a kept CUDA graph (rf_c0_render_graph)"}},
+                                 "form": "rounds in a kept CUDA graph (rf_c0_render_graph)"},
+                       "tma": {"value": rays_t, "ms_per_frame": c0_ms_t,
+                               "form": "host loop, each rank's brick staged whole in shared memory by one 3-D "
+                                       "tensor copy (rf_c0_render_tma)"}},
         "streamlines": streamlines,
         "differentiable_ea": ea,
         "delta_tracking": transport,
@@ -879,6 +886,7 @@ def run_section(args):
     """One workload alone, at a size for a profiler capture (a few GB on the
     device, each workload launched once, no warm-up), printing one JSON line of
     its own (not the bench line):
+      c0: the marching workload, one frame with quad bricks, one with TMA-staged bricks;
       c1: the microbenchmark, one rf_c1_run_batched call (one persistent launch);
       c2: streamlines, 512^3 field in 4x4x4 bricks, 2^18 seeds, until brick exit;
       c3: EA renderer at its configured size, one forward and one adjoint render;
@@ -915,6 +923,29 @@ def run_section(args):
             with open(args.round_log, "w") as f:
                 json.dump({"columns": ["t_start", "t_count_end", "t_barrier1", "t_scatter_end", "t_barrier2",
                                        "n_in", "n_next"], "rows": [[int(x) for x in r] for r in rows]}, f)
+    elif args.section == "c0":
+        # the marching workload once with quad bricks read through L1 and once
+        # with each brick staged whole in shared memory by a tensor copy
+        n, w, h, brick = 64, 128, 128, 32
+        vol = inputs.c0_volume(n)
+        cam = inputs.c0_camera(n, w, h)
+        dvol = torch.from_numpy(vol.reshape(-1)).cuda()
+        bricks = torch.zeros(rafi.c0_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
+        rafi.rf_c0_make_bricks(dvol, n, brick, bricks, s)
+        sbricks = torch.zeros(rafi.c0_scalar_bricks_floats(n, brick), dtype=torch.float32, device="cuda")
+        rafi.rf_c0_make_scalar_bricks(dvol, n, brick, sbricks, s)
+        image = torch.zeros(w * h, dtype=torch.float32, device="cuda")
+        out["workload"] = "64^3 blob volume, 2x2x2 ranks of 32^3, 128x128 rays, one frame each way"
+        with rafi.Context(8, 48, w * h) as ctx:
+            for name, fn in (("quad_l1", lambda: rafi.rf_c0_render(ctx.handle, bricks, cam, n, brick, w, h, image,
+                                                                    stream=s)),
+                             ("tma_smem", lambda: rafi.rf_c0_render_tma(ctx.handle, sbricks, cam, n, brick, w, h,
+                                                                         image, stream=s))):
+                e0.record(s)
+                rounds = fn()
+                e1.record(s)
+                torch.cuda.synchronize()
+                out[name] = {"ms": e0.elapsed_time(e1), "rounds": rounds}
     elif args.section == "c2":
         n, brick, count = 512, 128, 1 << 18
         R = (n // brick) ** 3
@@ -991,7 +1022,7 @@ def main():
     ap.add_argument("--items", type=int, default=N_ITEMS)
     ap.add_argument("--skip-extra", action="store_true",
                     help="leave out the streamline, differentiable and transport workloads")
-    ap.add_argument("--section", choices=["c1", "c2", "c3", "c4"], default=None,
+    ap.add_argument("--section", choices=["c0", "c1", "c2", "c3", "c4"], default=None,
                     help="run one workload alone at a profiling size and print its own JSON line (c1: one "
                          "persistent-kernel launch of the microbenchmark at --items; c2-c4: a host loop)")
     ap.add_argument("--law", type=int, default=0, choices=list(MODES), help="destination law of --section c1")

@@ -416,6 +416,24 @@ rf_status rf_c0_render_graph(rf_ctx *ctx, const float *bricks, const float *cam,
                              int32_t H, float *image, int32_t *hopLog, int32_t maxHops, int32_t *hopCount,
                              uint32_t maxRounds, void *stream, uint64_t *rounds);
 
+/* Marching with each rank's brick staged whole in shared memory by one 3-D
+ * tensor copy (TMA, cp.async.bulk.tensor), the alternative to the quad bricks
+ * read through L1 (VoPaT's per-rank trace, Sec. 5.1).  Bricks come from
+ * rf_c0_make_scalar_bricks: per rank (B+2)^3 scalars with a one-voxel halo,
+ * each index clamped to the volume, rows padded to rf_c0_scalar_row(B) =
+ * (B + 2) rounded up to a multiple of 4 floats (TMA copies rows of whole
+ * 16-byte units); device memory, 16-byte aligned, R x row x (B+2)^2 floats.
+ * A CTA takes up to 256 rays of one rank's incoming segment and marches them
+ * from the staged brick with the same corners and float operations as
+ * rf_c0_march, so the image is bit-identical.  The staged brick must fit in
+ * one CTA's shared memory (B = 32: 166 KB); larger bricks get RF_ERR_ARG.
+ * RF_ERR_CUDA if the driver offers no tensor-map encoder.  rf_c0_render_tma
+ * is rf_c0_render with this march (no hop log). */
+rf_status rf_c0_make_scalar_bricks(const float *volume, int32_t N, int32_t B, float *bricks, void *stream);
+rf_status rf_c0_march_tma(rf_ctx *ctx, const float *scalarBricks, int32_t N, int32_t B, float *image, void *stream);
+rf_status rf_c0_render_tma(rf_ctx *ctx, const float *scalarBricks, const float *cam, int32_t N, int32_t B, int32_t W,
+                           int32_t H, float *image, uint32_t maxRounds, void *stream, uint64_t *rounds);
+
 /* --- streamlines through bricks (32-byte particles) ------------------------ */
 
 /* Particle: {x, y, z (float bits), id} {steps, hops, set, status}; status 1 =

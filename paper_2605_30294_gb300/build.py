@@ -22,8 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 # per-source extra flags: the marching, streamline, emission-absorption and
 # transport kernels follow the written float operation order (no FMA contraction)
-EXTRA = {"c0_march.cu": ["-fmad=false"], "c2_streamlines.cu": ["-fmad=false"], "c3_ea_render.cu": ["-fmad=false"],
-         "c4_transport.cu": ["-fmad=false"]}
+EXTRA = {"c0_march.cu": ["-fmad=false"], "c0_march_tma.cu": ["-fmad=false"], "c2_streamlines.cu": ["-fmad=false"],
+         "c3_ea_render.cu": ["-fmad=false"], "c4_transport.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

@@ -104,6 +104,9 @@ _SIGS = {
     "rf_c0_march": [_P, _P, _i32, _i32, _P, _P, _i32, _P, _P],
     "rf_c0_render": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
     "rf_c0_render_graph": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
+    "rf_c0_make_scalar_bricks": [_P, _i32, _i32, _P, _P],
+    "rf_c0_march_tma": [_P, _P, _i32, _i32, _P, _P],
+    "rf_c0_render_tma": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _u32, _P, _PU64],
     "rf_create_with_buffers": [_i32, _u32, _u64, _P, _P, _P, _P],
     "rf_c1_run_graph": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _u32, _P, _PU64, _PU64],
     "rf_get_exchange_config": [_P, _P],
@@ -329,6 +332,17 @@ def c0_bricks_floats(n: int, brick: int) -> int:
     """Floats of the bricks rf_c0_make_bricks writes: (n/brick)^3 bricks of
     (brick+2)^3 x-y quads of 4 floats."""
     return (n // brick) ** 3 * (brick + 2) ** 3 * 4
+
+
+def c0_scalar_row(brick: int) -> int:
+    """Floats per row of a scalar brick: brick + 2 rounded up to a multiple of 4."""
+    return (brick + 2 + 3) // 4 * 4
+
+
+def c0_scalar_bricks_floats(n: int, brick: int) -> int:
+    """Floats of the bricks rf_c0_make_scalar_bricks writes: (n/brick)^3 bricks of
+    c0_scalar_row(brick) x (brick+2)^2 scalars."""
+    return (n // brick) ** 3 * c0_scalar_row(brick) * (brick + 2) ** 2
 
 
 def c2_bricks_floats(n: int, brick: int) -> int:
@@ -597,3 +611,33 @@ def rf_c1_run_graph(ctx: int, items, n: int, seed: int, mode: int, zipf_s: float
                                ctypes.byref(fwd))
     _check("rf_c1_run_graph", st, allow)
     return st, cnt.value, rounds.value, fwd.value
+
+
+def rf_c0_make_scalar_bricks(volume, n: int, brick: int, bricks, stream=None) -> None:
+    _need(volume, 4 * max(n, 0) ** 3, "rf_c0_make_scalar_bricks", "volume")
+    if brick > 0 and n > 0 and n % brick == 0:
+        _need(bricks, 4 * c0_scalar_bricks_floats(n, brick), "rf_c0_make_scalar_bricks", "bricks")
+    _check("rf_c0_make_scalar_bricks", lib().rf_c0_make_scalar_bricks(ptr(volume), n, brick, ptr(bricks),
+                                                                      stream_handle(stream)))
+
+
+def rf_c0_render_tma(ctx: int, scalar_bricks, cam, n: int, brick: int, width: int, height: int, image,
+                     max_rounds: int = 16, stream=None) -> int:
+    """Marching with each brick staged in shared memory by a tensor copy; returns rounds."""
+    if brick > 0 and n > 0 and n % brick == 0:
+        _need(scalar_bricks, 4 * c0_scalar_bricks_floats(n, brick), "rf_c0_render_tma", "scalar_bricks")
+    _need(image, 4 * max(width, 0) * max(height, 0), "rf_c0_render_tma", "image")
+    c = _cam(cam)
+    rounds = ctypes.c_uint64()
+    _check("rf_c0_render_tma", lib().rf_c0_render_tma(ctx, ptr(scalar_bricks), ctypes.cast(c, _P), n, brick, width,
+                                                      height, ptr(image), max_rounds, stream_handle(stream),
+                                                      ctypes.byref(rounds)))
+    return rounds.value
+
+
+def rf_c0_march_tma(ctx: int, scalar_bricks, n: int, brick: int, image, stream=None) -> None:
+    """One marching round with TMA-staged bricks over the context's incoming queue."""
+    if brick > 0 and n > 0 and n % brick == 0:
+        _need(scalar_bricks, 4 * c0_scalar_bricks_floats(n, brick), "rf_c0_march_tma", "scalar_bricks")
+    _check("rf_c0_march_tma", lib().rf_c0_march_tma(ctx, ptr(scalar_bricks), n, brick, ptr(image),
+                                                    stream_handle(stream)))

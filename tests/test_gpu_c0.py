@@ -145,3 +145,49 @@ def test_graph_form_matches_host_loop_and_is_relaunched():
         torch.cuda.synchronize()
         assert rounds == want2["rounds"]
         np.testing.assert_array_equal(image.cpu().numpy().view(np.uint32), want2["T"].view(np.uint32))
+
+
+def render_tma(vol, cam, n, brick, w, h):
+    s = stream()
+    dvol = to_dev(vol.reshape(-1))
+    sb = torch.zeros(rafi.c0_scalar_bricks_floats(n, brick), dtype=torch.float32, device=dev())
+    rafi.rf_c0_make_scalar_bricks(dvol, n, brick, sb, s)
+    image = torch.full((w * h,), -1.0, dtype=torch.float32, device=dev())
+    with rafi.Context((n // brick) ** 3, RAY_BYTES, w * h) as ctx:
+        rounds = rafi.rf_c0_render_tma(ctx.handle, sb, cam, n, brick, w, h, image, stream=s)
+    torch.cuda.synchronize()
+    return image.cpu().numpy(), rounds, sb
+
+
+@pytest.mark.parametrize("n,brick,w,h", [(64, 32, 128, 128), (64, 16, 96, 80), (16, 4, 33, 17)])
+def test_tma_staged_bricks_give_the_same_image(n, brick, w, h):
+    # bricks staged whole in shared memory by a 3-D tensor copy: same corners,
+    # same float operations, so the image equals the quad-brick path's bit for
+    # bit (and so the oracle's within its tolerance)
+    vol = inputs.c0_volume(n)
+    cam = inputs.c0_camera(n, w, h)
+    img, rounds, sb = render_tma(vol, cam, n, brick, w, h)
+    ref = render(vol, cam, n, brick, w, h)
+    np.testing.assert_array_equal(img.view(np.uint32), ref["T"].view(np.uint32))
+    assert rounds == ref["rounds"]
+    want = oracle.c0_render(vol, cam, w, h, brick=brick)
+    assert np.max(np.abs(img - want["T"]) / want["T"]) <= 1e-5
+    # the scalar bricks hold the clamped halo (rows padded to whole 16-byte units)
+    nb, S, X = n // brick, brick + 2, rafi.c0_scalar_row(brick)
+    b = sb.cpu().numpy().reshape(nb ** 3, S, S, X)
+    r = nb ** 3 - 1  # the last brick: its halo leaves the volume on three faces
+    bx = by = bz = nb - 1
+    idx = lambda o, l: np.clip(o - 1 + l, 0, n - 1)  # noqa: E731
+    zz, yy, xx = np.meshgrid(idx(bz * brick, np.arange(S)), idx(by * brick, np.arange(S)),
+                             idx(bx * brick, np.arange(X)), indexing="ij")
+    np.testing.assert_array_equal(b[r], vol[zz, yy, xx])
+
+
+def test_tma_refuses_bricks_beyond_shared_memory():
+    # a 128^3 brick with its halo (132 x 130 x 130 floats, 8.9 MB) cannot be staged whole
+    n, brick = 256, 128
+    sb = torch.zeros(16, dtype=torch.float32, device=dev())
+    image = torch.zeros(16, dtype=torch.float32, device=dev())
+    with rafi.Context(8, RAY_BYTES, 16) as ctx:
+        st = rafi.lib().rf_c0_march_tma(ctx.handle, sb.data_ptr(), n, brick, image.data_ptr(), None)
+    assert st == rafi.RF_ERR_ARG and "shared memory" in rafi.rf_last_error()
