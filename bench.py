@@ -338,7 +338,9 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
     out = {}
     with rafi.Context(8, 48, w * h) as ctx:
         for name, render in (("host_loop", rafi.rf_c0_render), ("graph", rafi.rf_c0_render_graph),
-                             ("tma", lambda c, b, *a, **k: rafi.rf_c0_render_tma(c, sbricks, *a, **k))):
+                             ("tma", lambda c, b, *a, **k: rafi.rf_c0_render_tma(c, sbricks, *a, **k)),
+                             ("tma_graph", lambda c, b, *a, **k: rafi.rf_c0_render_tma(c, sbricks, *a, **k,
+                                                                                       form=rafi.RF_FORM_GRAPH))):
             for _ in range(3):
                 render(ctx.handle, bricks, cam, n, brick, w, h, image, stream=s)
             torch.cuda.synchronize()
@@ -349,8 +351,7 @@ def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
             e1.record(s)
             torch.cuda.synchronize()
             out[name] = e0.elapsed_time(e1) / reps
-    return (w * h / (out["host_loop"] * 1e-3), out["host_loop"], w * h / (out["graph"] * 1e-3), out["graph"],
-            w * h / (out["tma"] * 1e-3), out["tma"])
+    return {k: {"value": w * h / (v * 1e-3), "ms_per_frame": v} for k, v in out.items()}
 
 
 LOG_CAP = 4096  # rounds logged by the persistent kernel
@@ -770,7 +771,7 @@ def run_ours(args):
                          "into the pinned host buffer, read-back of the counts; rest = launches, host calls "
                          "and synchronisation"}
 
-    rays_s, c0_ms, rays_g, c0_ms_g, rays_t, c0_ms_t = c0_rays_per_s(torch, rafi, inputs, s)
+    c0 = c0_rays_per_s(torch, rafi, inputs, s)
     ctx.close()
     del d_items, retired, h_items, h_ret
     torch.cuda.empty_cache()
@@ -861,13 +862,13 @@ def run_ours(args):
         "e2e": {"value": e2e_fwd / e2e_s, "unit": "items/s",
                 "h2d_bytes_per_step": len(MODES) * n * ITEM_BYTES,
                 "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8), "split": e2e_split},
-        "rays_per_s": {"value": rays_s, "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
-                       "ms_per_frame": c0_ms, "form": "host loop (rf_c0_render)",
-                       "graph": {"value": rays_g, "ms_per_frame": c0_ms_g,
-                                 "form": "rounds in a kept CUDA graph (rf_c0_render_graph)"},
-                       "tma": {"value": rays_t, "ms_per_frame": c0_ms_t,
-                               "form": "host loop, each rank's brick staged whole in shared memory by one 3-D "
-                                       "tensor copy (rf_c0_render_tma)"}},
+        "rays_per_s": {"value": c0["tma_graph"]["value"],
+                       "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
+                       "ms_per_frame": c0["tma_graph"]["ms_per_frame"],
+                       "form": "bricks staged whole in shared memory by one 3-D tensor copy, rounds in a kept CUDA "
+                               "graph (rf_c0_render_tma, graph form)",
+                       "forms": {"quad_bricks_host_loop": c0["host_loop"], "quad_bricks_graph": c0["graph"],
+                                 "tma_bricks_host_loop": c0["tma"], "tma_bricks_graph": c0["tma_graph"]}},
         "streamlines": streamlines,
         "differentiable_ea": ea,
         "delta_tracking": transport,

@@ -428,11 +428,13 @@ rf_status rf_c0_render_graph(rf_ctx *ctx, const float *bricks, const float *cam,
  * rf_c0_march, so the image is bit-identical.  The staged brick must fit in
  * one CTA's shared memory (B = 32: 166 KB); larger bricks get RF_ERR_ARG.
  * RF_ERR_CUDA if the driver offers no tensor-map encoder.  rf_c0_render_tma
- * is rf_c0_render with this march (no hop log). */
+ * is rf_c0_render with this march (no hop log), as the host loop (form
+ * RF_FORM_HOST_LOOP) or with its rounds in a kept CUDA graph whose
+ * conditional while node repeats them (RF_FORM_GRAPH, as rf_c0_render_graph). */
 rf_status rf_c0_make_scalar_bricks(const float *volume, int32_t N, int32_t B, float *bricks, void *stream);
 rf_status rf_c0_march_tma(rf_ctx *ctx, const float *scalarBricks, int32_t N, int32_t B, float *image, void *stream);
 rf_status rf_c0_render_tma(rf_ctx *ctx, const float *scalarBricks, const float *cam, int32_t N, int32_t B, int32_t W,
-                           int32_t H, float *image, uint32_t maxRounds, void *stream, uint64_t *rounds);
+                           int32_t H, float *image, int32_t form, uint32_t maxRounds, void *stream, uint64_t *rounds);
 
 /* --- streamlines through bricks (32-byte particles) ------------------------ */
 

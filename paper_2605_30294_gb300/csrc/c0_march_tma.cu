@@ -199,6 +199,75 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
     return fn;
 }
 
+// Everything a march launch takes, checked and encoded outside any stream capture.
+struct TmaMarch {
+    CUtensorMap tmap;
+    const float *bricks;
+    int32_t N, B;
+    float *image;
+    size_t smem;
+    unsigned chunks;
+};
+
+rf_status prepare_tma(rf_ctx *ctx, const float *scalarBricks, int32_t N, int32_t B, float *image, const char *fn,
+                      TmaMarch &m)
+{
+    if (!ctx || ctx->itemBytes != sizeof(Ray)) {
+        set_error("%s: context of 48-byte rays required", fn);
+        return RF_ERR_ARG;
+    }
+    if (!scalarBricks || !image || N < 1 || B < 1 || N % B || (int64_t)(N / B) * (N / B) * (N / B) != ctx->numRanks ||
+        (reinterpret_cast<uintptr_t>(scalarBricks) & 15u) || B + 2 > 256) {
+        set_error("%s: bad arguments (bricks 16-byte aligned, B + 2 <= 256)", fn);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    const int32_t S = B + 2, X = row_floats(B), R = ctx->numRanks;
+    m.smem = (size_t)X * S * S * 4u;
+    int optin = 0;
+    RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (m.smem + 64 > (size_t)optin) {
+        set_error("%s: a %d^3 brick with halo (%zu bytes) does not fit in shared memory (%d)", fn, B, m.smem, optin);
+        return RF_ERR_ARG;
+    }
+    auto enc = encoder();
+    if (!enc) {
+        set_error("%s: cuTensorMapEncodeTiled is not available", fn);
+        return RF_ERR_CUDA;
+    }
+    // the bricks as one 3-D tensor: x (padded rows), y, and z of all bricks in turn
+    const cuuint64_t dims[3] = {(cuuint64_t)X, (cuuint64_t)S, (cuuint64_t)S * R};
+    const cuuint64_t strides[2] = {(cuuint64_t)X * 4u, (cuuint64_t)X * S * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)X, (cuuint32_t)S, (cuuint32_t)S};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult cr = enc(&m.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(scalarBricks), dims,
+                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) {
+        set_error("%s: cuTensorMapEncodeTiled failed (%d)", fn, (int)cr);
+        return RF_ERR_CUDA;
+    }
+    RF_CUDA(cudaFuncSetAttribute(march_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem));
+    m.bricks = scalarBricks;
+    m.N = N;
+    m.B = B;
+    m.image = image;
+    // an upper bound on the chunks of all ranks' segments
+    m.chunks = (unsigned)((ctx->capacity + kChunk - 1) / kChunk + (uint64_t)R);
+    return RF_OK;
+}
+
+rf_status launch_tma(rf_ctx *ctx, const TmaMarch &m, cudaStream_t s)
+{
+    rf_device_queues q;
+    rf_get_device_queues(ctx, &q);
+    time_begin(ctx, kTimeWork, s);
+    march_tma_kernel<<<m.chunks, kBlock, m.smem, s>>>(m.tmap, m.N, m.B, m.image, q, &ctx->dev->status);
+    RF_LAUNCHED("march_tma_kernel");
+    time_end(ctx, kTimeWork, s);
+    return RF_OK;
+}
+
 }  // namespace
 }  // namespace rfi
 
@@ -224,61 +293,68 @@ rf_status rf_c0_make_scalar_bricks(const float *volume, int32_t N, int32_t B, fl
 
 rf_status rf_c0_march_tma(rf_ctx *ctx, const float *scalarBricks, int32_t N, int32_t B, float *image, void *stream)
 {
-    if (!ctx || ctx->itemBytes != sizeof(Ray)) {
-        set_error("rf_c0_march_tma: context of 48-byte rays required");
-        return RF_ERR_ARG;
-    }
-    if (!scalarBricks || !image || N < 1 || B < 1 || N % B || (int64_t)(N / B) * (N / B) * (N / B) != ctx->numRanks ||
-        (reinterpret_cast<uintptr_t>(scalarBricks) & 15u) || B + 2 > 256) {
-        set_error("rf_c0_march_tma: bad arguments (bricks 16-byte aligned, B + 2 <= 256)");
-        return RF_ERR_ARG;
-    }
+    TmaMarch m;
+    if (rf_status st = prepare_tma(ctx, scalarBricks, N, B, image, "rf_c0_march_tma", m)) return st;
     DeviceGuard g(ctx->device);
-    const int32_t S = B + 2, X = row_floats(B), R = ctx->numRanks;
-    const size_t smem = (size_t)X * S * S * 4u;
-    int optin = 0;
-    RF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    if (smem + 64 > (size_t)optin) {
-        set_error("rf_c0_march_tma: a %d^3 brick with halo (%zu bytes) does not fit in shared memory (%d)", B, smem,
-                  optin);
-        return RF_ERR_ARG;
-    }
-    auto enc = encoder();
-    if (!enc) {
-        set_error("rf_c0_march_tma: cuTensorMapEncodeTiled is not available");
-        return RF_ERR_CUDA;
-    }
-    // the bricks as one 3-D tensor: x (padded rows), y, and z of all bricks in turn
-    CUtensorMap tmap;
-    const cuuint64_t dims[3] = {(cuuint64_t)X, (cuuint64_t)S, (cuuint64_t)S * R};
-    const cuuint64_t strides[2] = {(cuuint64_t)X * 4u, (cuuint64_t)X * S * 4u};
-    const cuuint32_t box[3] = {(cuuint32_t)X, (cuuint32_t)S, (cuuint32_t)S};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(scalarBricks), dims,
-                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) {
-        set_error("rf_c0_march_tma: cuTensorMapEncodeTiled failed (%d)", (int)cr);
-        return RF_ERR_CUDA;
-    }
-    RF_CUDA(cudaFuncSetAttribute(march_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    rf_device_queues q;
-    rf_get_device_queues(ctx, &q);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // an upper bound on the chunks of all ranks' segments
-    const uint64_t chunks = (ctx->capacity + kChunk - 1) / kChunk + (uint64_t)R;
-    time_begin(ctx, kTimeWork, s);
-    march_tma_kernel<<<(unsigned)chunks, kBlock, smem, s>>>(tmap, N, B, image, q, &ctx->dev->status);
-    RF_LAUNCHED("march_tma_kernel");
-    time_end(ctx, kTimeWork, s);
-    return RF_OK;
+    return launch_tma(ctx, m, static_cast<cudaStream_t>(stream));
 }
 
 rf_status rf_c0_render_tma(rf_ctx *ctx, const float *scalarBricks, const float *cam, int32_t N, int32_t B, int32_t W,
-                           int32_t H, float *image, uint32_t maxRounds, void *stream, uint64_t *rounds)
+                           int32_t H, float *image, int32_t form, uint32_t maxRounds, void *stream, uint64_t *rounds)
 {
+    if (form != RF_FORM_HOST_LOOP && form != RF_FORM_GRAPH) {
+        set_error("rf_c0_render_tma: form %d is neither the host loop nor the graph loop", form);
+        return RF_ERR_ARG;
+    }
+    TmaMarch m;
+    if (rf_status st = prepare_tma(ctx, scalarBricks, N, B, image, "rf_c0_render_tma", m)) return st;
+    if (!cam || W < 1 || H < 1 || (uint64_t)W * H > ctx->capacity) {
+        set_error("rf_c0_render_tma: bad camera or W*H above capacity");
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t r = 0;
+    if (form == RF_FORM_GRAPH) {
+        // the march and the exchange repeated by a conditional while node; raygen
+        // and the first exchange run in the graph before the loop
+        struct Key {
+            const float *bricks;
+            float cam[12];
+            int32_t N, B, W, H;
+            float *image;
+        } key;
+        memset(&key, 0, sizeof key);
+        key.bricks = scalarBricks;
+        for (int a = 0; a < 12; ++a) key.cam[a] = cam[a];
+        key.N = N;
+        key.B = B;
+        key.W = W;
+        key.H = H;
+        key.image = image;
+        rf_status st = run_graph_loop(
+            ctx, s, maxRounds,
+            [&](cudaStream_t cs) -> rf_status {
+                if (rf_status ms = launch_tma(ctx, m, cs)) return ms;
+                return launch_exchange(ctx, cs);
+            },
+            &r, nullptr,
+            [&](cudaStream_t cs) -> rf_status {
+                if (rf_status rs = rf_c0_raygen(ctx, cam, N, B, W, H, image, cs)) return rs;
+                return launch_exchange(ctx, cs);
+            },
+            &key, sizeof key);
+        if (st != RF_OK) return st;
+        if (rounds) *rounds = r;
+        if (ctx->host->numActive) {
+            set_error("rf_c0_render_tma: %llu rays still active after %u rounds",
+                      (unsigned long long)ctx->host->numActive, maxRounds);
+            return RF_ERR_MAX_ROUNDS;
+        }
+        return RF_OK;
+    }
     if (rf_status st = rf_c0_raygen(ctx, cam, N, B, W, H, image, stream)) return st;
-    uint64_t active = 0, r = 0;
+    uint64_t active = 0;
     rf_status st = rf_exchange(ctx, stream, &active);
     if (st != RF_OK) return st;
     while (active > 0) {
@@ -288,7 +364,7 @@ rf_status rf_c0_render_tma(rf_ctx *ctx, const float *scalarBricks, const float *
             if (rounds) *rounds = r;
             return RF_ERR_MAX_ROUNDS;
         }
-        if ((st = rf_c0_march_tma(ctx, scalarBricks, N, B, image, stream))) return st;
+        if ((st = launch_tma(ctx, m, s))) return st;
         if ((st = rf_exchange(ctx, stream, &active))) return st;
         ++r;
     }

@@ -106,7 +106,7 @@ _SIGS = {
     "rf_c0_render_graph": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _P, _i32, _P, _u32, _P, _PU64],
     "rf_c0_make_scalar_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c0_march_tma": [_P, _P, _i32, _i32, _P, _P],
-    "rf_c0_render_tma": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _u32, _P, _PU64],
+    "rf_c0_render_tma": [_P, _P, _P, _i32, _i32, _i32, _i32, _P, _i32, _u32, _P, _PU64],
     "rf_create_with_buffers": [_i32, _u32, _u64, _P, _P, _P, _P],
     "rf_c1_run_graph": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _u32, _P, _PU64, _PU64],
     "rf_get_exchange_config": [_P, _P],
@@ -622,15 +622,16 @@ def rf_c0_make_scalar_bricks(volume, n: int, brick: int, bricks, stream=None) ->
 
 
 def rf_c0_render_tma(ctx: int, scalar_bricks, cam, n: int, brick: int, width: int, height: int, image,
-                     max_rounds: int = 16, stream=None) -> int:
-    """Marching with each brick staged in shared memory by a tensor copy; returns rounds."""
+                     max_rounds: int = 16, stream=None, form: int = RF_FORM_HOST_LOOP) -> int:
+    """Marching with each brick staged in shared memory by a tensor copy, as the host
+    loop or the graph loop (form); returns rounds."""
     if brick > 0 and n > 0 and n % brick == 0:
         _need(scalar_bricks, 4 * c0_scalar_bricks_floats(n, brick), "rf_c0_render_tma", "scalar_bricks")
     _need(image, 4 * max(width, 0) * max(height, 0), "rf_c0_render_tma", "image")
     c = _cam(cam)
     rounds = ctypes.c_uint64()
     _check("rf_c0_render_tma", lib().rf_c0_render_tma(ctx, ptr(scalar_bricks), ctypes.cast(c, _P), n, brick, width,
-                                                      height, ptr(image), max_rounds, stream_handle(stream),
+                                                      height, ptr(image), form, max_rounds, stream_handle(stream),
                                                       ctypes.byref(rounds)))
     return rounds.value
 

@@ -147,26 +147,30 @@ def test_graph_form_matches_host_loop_and_is_relaunched():
         np.testing.assert_array_equal(image.cpu().numpy().view(np.uint32), want2["T"].view(np.uint32))
 
 
-def render_tma(vol, cam, n, brick, w, h):
+def render_tma(vol, cam, n, brick, w, h, form=rafi.RF_FORM_HOST_LOOP):
     s = stream()
     dvol = to_dev(vol.reshape(-1))
     sb = torch.zeros(rafi.c0_scalar_bricks_floats(n, brick), dtype=torch.float32, device=dev())
     rafi.rf_c0_make_scalar_bricks(dvol, n, brick, sb, s)
     image = torch.full((w * h,), -1.0, dtype=torch.float32, device=dev())
     with rafi.Context((n // brick) ** 3, RAY_BYTES, w * h) as ctx:
-        rounds = rafi.rf_c0_render_tma(ctx.handle, sb, cam, n, brick, w, h, image, stream=s)
+        rounds = rafi.rf_c0_render_tma(ctx.handle, sb, cam, n, brick, w, h, image, stream=s, form=form)
+        if form == rafi.RF_FORM_GRAPH:  # a second frame relaunches the kept graph
+            image.fill_(-1.0)
+            assert rafi.rf_c0_render_tma(ctx.handle, sb, cam, n, brick, w, h, image, stream=s, form=form) == rounds
     torch.cuda.synchronize()
     return image.cpu().numpy(), rounds, sb
 
 
+@pytest.mark.parametrize("form", [rafi.RF_FORM_HOST_LOOP, rafi.RF_FORM_GRAPH], ids=["host_loop", "graph"])
 @pytest.mark.parametrize("n,brick,w,h", [(64, 32, 128, 128), (64, 16, 96, 80), (16, 4, 33, 17)])
-def test_tma_staged_bricks_give_the_same_image(n, brick, w, h):
+def test_tma_staged_bricks_give_the_same_image(n, brick, w, h, form):
     # bricks staged whole in shared memory by a 3-D tensor copy: same corners,
     # same float operations, so the image equals the quad-brick path's bit for
     # bit (and so the oracle's within its tolerance)
     vol = inputs.c0_volume(n)
     cam = inputs.c0_camera(n, w, h)
-    img, rounds, sb = render_tma(vol, cam, n, brick, w, h)
+    img, rounds, sb = render_tma(vol, cam, n, brick, w, h, form)
     ref = render(vol, cam, n, brick, w, h)
     np.testing.assert_array_equal(img.view(np.uint32), ref["T"].view(np.uint32))
     assert rounds == ref["rounds"]
