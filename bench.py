@@ -325,6 +325,42 @@ def rounds_kernel_code_hash() -> str:
     return hashlib.sha256(re.sub(r"\s+", "", text).encode()).hexdigest()
 
 
+def sm_clock_mhz() -> float:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
+def l1_peak_gbs(torch) -> float:
+    """Nominal L1 load bandwidth: 128 B per clock per SM at the SM clock."""
+    return torch.cuda.get_device_properties(0).multi_processor_count * 128 * sm_clock_mhz() * 1e6 / 1e9
+
+
+def issue_peak(torch) -> float:
+    """Warp instructions per second: four schedulers per SM, one issue each per clock."""
+    return torch.cuda.get_device_properties(0).multi_processor_count * 4 * sm_clock_mhz() * 1e6
+
+
+def ea_march_instructions() -> dict:
+    """Warp instructions of the EA march kernels per render at the configured size
+    (profiles/ea_march_instructions.json), or {} when their code changed since."""
+    import hashlib
+    import re
+
+    p = os.path.join(ROOT, "profiles", "ea_march_instructions.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        d = json.load(f)
+    text = open(os.path.join(ROOT, "paper_2605_30294_gb300/csrc/c3_ea_render.cu")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    code = hashlib.sha256(re.sub(r"\s+", "", text).encode()).hexdigest()
+    return d.get("warp_instructions", {}) if d.get("code_sha256") == code else {}
+
+
 def c0_rays_per_s(torch, rafi, inputs, s, reps=20):
     n, w, h, brick = 64, 128, 128, 32
     vol = inputs.c0_volume(n)
@@ -480,6 +516,23 @@ def c2_streamlines(torch, rafi, inputs, s, reps=3, cpu=None):
             res[key]["batched_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["batched"]["ms_per_run"]
             res[key]["graph_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["graph"]["ms_per_run"]
             res[key]["tuned_over_plain"] = res[key]["plain"]["ms_per_run"] / res[key]["tuned"]["ms_per_run"]
+            if spr == 0:
+                # the trace kernel's L1 roofline: an RK4 step samples the velocity four
+                # times, each sample four aligned 32-byte loads of x-paired voxels
+                rafi.rf_set_timing(ctx.handle, True)
+                rafi.rf_get_timing(ctx.handle, reset=True)
+                rafi.rf_c2_run(ctx.handle, bricks, d_seeds, d_sets, count, n, brick, 0.25, 2000, spr, out,
+                               rafi.RF_FORM_HOST_LOOP, stream=s)
+                t = rafi.rf_get_timing(ctx.handle, reset=True)
+                rafi.rf_set_timing(ctx.handle, False)
+                steps = res[key]["plain"]["particle_steps"]
+                achieved = steps * 512 / (t.workMs * 1e-3) / 1e9
+                peak = l1_peak_gbs(torch)
+                res[key]["roofline_trace"] = {
+                    "bound": "l1", "kernel": "trace_kernel", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "kernel_ms": t.workMs, "launches": t.workLaunches,
+                    "alg_bytes": "512 B per particle-step (4 samples x 4 loads x 32 B, from L1)",
+                    "peak_kind": "derived: SMs x 128 B per clock x the SM clock"}
     if cpu is not None:  # the cpu_baseline leg: the oracle on a subset of the seeds
         cpu["streamlines_subset"] = oracle_c2_subset(field, seeds, brick)
     return res
@@ -518,6 +571,22 @@ def c3_ea(torch, rafi, inputs, s, reps=5):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             out[name] = {"ms": ms, "rays_per_s": nr / (ms * 1e-3)}
+            # the march kernels issue-bound roofline: their warp instructions (counted once
+            # by ncu at this size) over their time in one more render
+            rafi.rf_set_timing(ctx.handle, True)
+            rafi.rf_get_timing(ctx.handle, reset=True)
+            fn()
+            t = rafi.rf_get_timing(ctx.handle, reset=True)
+            rafi.rf_set_timing(ctx.handle, False)
+            inst = ea_march_instructions().get(name)
+            peak = issue_peak(torch)
+            ach = inst / (t.workMs * 1e-3) if inst else None
+            out[name]["roofline"] = {
+                "bound": "issue", "kernel": f"march_kernel ({name})", "achieved": ach, "peak": peak,
+                "unit": "warp instructions/s", "frac": ach / peak if ach else None, "kernel_ms": t.workMs,
+                "warp_instructions": inst, "peak_kind": "derived: SMs x 4 schedulers x 1 warp instruction per clock "
+                                                        "x the SM clock",
+                "instructions_from": "profiles/ea_march_instructions.json (null when the kernel's code changed)"}
     return out
 
 
