@@ -431,8 +431,8 @@ def phase_rates(log_rows, item_bytes, min_items=1 << 20):
     small = ~big
     if small.any():
         out["us_per_round_lt_2^20"] = float((lg[small, 4] - lg[small, 0]).mean() * 1e-3)
-    # rounds of at most 2048 items run on one CTA; the ones between run on the whole grid
-    for name, sel in (("solo_le_2048", lg[:, 5] <= 2048), ("grid_lt_2^20", small & (lg[:, 5] > 2048)),
+    # rounds of at most one 512-item tile run on one CTA; the ones between run on the whole grid
+    for name, sel in (("solo_le_512", lg[:, 5] <= 512), ("grid_lt_2^20", small & (lg[:, 5] > 512)),
                       ("ge_2^20", big)):
         if sel.any():
             out["rounds_" + name] = int(sel.sum())

@@ -358,9 +358,9 @@ rf_status rf_c1_run_graph(rf_ctx *ctx, const void *items, uint64_t n, uint32_t s
  * items straight into it during the run; other host buffers are filled from
  * a device staging buffer after it.  The kernel runs in the shape set for
  * RF_POLICY_MICROBENCH on the context (rf_set_batched_config; shape 0 by
- * default: tiles of 512 items, 3 CTAs per SM).  Rounds of at most four tiles
- * run on one CTA (the others return); with steps on arrival, rounds of at
- * most one tile keep the whole queue in that CTA's shared memory.  roundLog (device, 7 x roundLogCap
+ * default: tiles of 512 items, 3 CTAs per SM).  Rounds of at most one tile
+ * run on one CTA (the others return); with steps on arrival such rounds keep
+ * the whole queue in that CTA's shared memory.  roundLog (device, 7 x roundLogCap
  * words, nullable) receives per round, as seen by CTA 0, the %globaltimer ns
  * at round start, end of its work step (or count), after the first barrier,
  * end of its scatter and after the second barrier, then the incoming and the

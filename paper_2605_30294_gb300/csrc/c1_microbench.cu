@@ -68,15 +68,25 @@ __device__ __forceinline__ int32_t choose_dest(int32_t mode, int32_t src, uint32
     return torus_neighbour(src, (int32_t)(((unsigned long long)r1 * 6u) >> 32), gx, gy, gz);
 }
 
-// Per-rank work kernel: one thread per incoming item; the owning rank comes
-// from the segment offsets.  DET: out slot = incoming index (retired slots
-// get destination -1), otherwise a block-aggregated append.
+// Per-rank work kernel.  Each thread takes kWorkItems incoming items per pass
+// (base + u * kBlock + tid: a warp reads 32 consecutive items for each u), so
+// four items' loads are in flight per thread; the owning rank comes from the
+// segment offsets.  DET: out slot = incoming index (retired slots get
+// destination -1).  Otherwise forwarded items are appended to the out-queue.
+// Retired items are appended to the retirement buffer in both modes.  A pass
+// reserves its forwarded and retired slots together: one block scan of the
+// warps' two counts, then both atomic adds at once, so the pass waits for one
+// atomic round trip.
+constexpr int kWorkItems = 4;
+
 template <bool DET>
 __global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
 {
+    constexpr int kWarps = kBlock / 32;
     __shared__ uint32_t sOff[RF_MAX_RANKS + 1];
     __shared__ uint32_t sThr[RF_MAX_RANKS];
-    __shared__ typename rf::BlockAppend<kBlock>::Storage sFwd, sRet;
+    __shared__ uint32_t sWarpF[kWarps], sWarpR[kWarps];
+    __shared__ unsigned long long sBaseF, sBaseR;
     const int R = a.q.numRanks;
     for (int e = threadIdx.x; e <= R; e += kBlock) sOff[e] = a.q.inOffset[e];
     if (a.mode == RF_C1_ZIPF)
@@ -85,62 +95,105 @@ __global__ void __launch_bounds__(kBlock) work_kernel(WorkArgs a)
     const uint32_t n = sOff[R];
     const uint32_t hop = a.hopPtr ? (uint32_t)*a.hopPtr : a.hop;
     if (DET && blockIdx.x == 0 && threadIdx.x == 0) *a.q.outCount = n;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 
     const uint4 *inq = static_cast<const uint4 *>(a.q.in);
     uint4 *outq = static_cast<uint4 *>(a.q.out);
-    for (uint32_t base = blockIdx.x * kBlock; base < n; base += gridDim.x * kBlock) {
-        const uint32_t i = base + threadIdx.x;
-        const bool active = i < n;
-        uint4 w0 = {}, w1 = {}, w2 = {}, w3 = {};
-        bool retire = false;
-        int32_t d = -1;
-        if (active) {
-            const uint4 *p = inq + (size_t)i * 4;
-            w0 = __ldg(p);
-            w1 = __ldg(p + 1);
-            w2 = __ldg(p + 2);
-            w3 = __ldg(p + 3);
-            const uint4 r = philox4x32_10(make_uint4(w0.x, w0.y, w3.w, hop), make_uint2(a.seed, 1u));
-            if (r.x < kRetire) {
-                retire = true;
+    constexpr uint32_t kPass = kBlock * kWorkItems;
+    for (uint32_t base = blockIdx.x * kPass; base < n; base += gridDim.x * kPass) {
+        uint4 w[kWorkItems][4];
+        int32_t d[kWorkItems];
+        bool act[kWorkItems], ret[kWorkItems];
+#pragma unroll
+        for (int u = 0; u < kWorkItems; ++u) {
+            const uint32_t i = base + (uint32_t)u * kBlock + threadIdx.x;
+            act[u] = i < n;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[u][q] = act[u] ? __ldg(inq + (size_t)i * 4 + q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < kWorkItems; ++u) {
+            const uint32_t i = base + (uint32_t)u * kBlock + threadIdx.x;
+            ret[u] = false;
+            d[u] = -1;
+            if (act[u]) {
+                const uint4 r = philox4x32_10(make_uint4(w[u][0].x, w[u][0].y, w[u][3].w, hop), make_uint2(a.seed, 1u));
+                if (r.x < kRetire) {
+                    ret[u] = true;
+                } else {
+                    d[u] = choose_dest(a.mode, rf::rankOf(sOff, R, i), r.y, R, sThr, a.gx, a.gy, a.gz);
+                    w[u][3].z = (uint32_t)d[u];
+                    w[u][3].y ^= r.z;
+                    w[u][3].w += 1u;
+                }
+            }
+        }
+        // per-item ranks within the warp (item index u first, then lane) and the
+        // warp's counts, for the appended forwards (not in DET) and retirements
+        const uint32_t lt = lanemask_lt();
+        uint32_t rankF[kWorkItems], rankR[kWorkItems], cf = 0, cr = 0;
+#pragma unroll
+        for (int u = 0; u < kWorkItems; ++u) {
+            const uint32_t bf = __ballot_sync(0xFFFFFFFFu, !DET && act[u] && !ret[u]);
+            const uint32_t br = __ballot_sync(0xFFFFFFFFu, act[u] && ret[u]);
+            rankF[u] = cf + (uint32_t)__popc(bf & lt);
+            rankR[u] = cr + (uint32_t)__popc(br & lt);
+            cf += (uint32_t)__popc(bf);
+            cr += (uint32_t)__popc(br);
+        }
+        if (lane == 0) {
+            sWarpF[warp] = cf;
+            sWarpR[warp] = cr;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const uint32_t vf = lane < (unsigned)kWarps ? sWarpF[lane] : 0u;
+            const uint32_t vr = lane < (unsigned)kWarps ? sWarpR[lane] : 0u;
+            uint32_t inF = vf, inR = vr;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t tf = __shfl_up_sync(0xFFFFFFFFu, inF, o);
+                const uint32_t tr = __shfl_up_sync(0xFFFFFFFFu, inR, o);
+                if ((int)lane >= o) {
+                    inF += tf;
+                    inR += tr;
+                }
+            }
+            if (lane < (unsigned)kWarps) {
+                sWarpF[lane] = inF - vf;
+                sWarpR[lane] = inR - vr;
+            }
+            if (lane == 31) {
+                // both reservations in flight at once
+                const unsigned long long bF = inF ? atomicAdd(a.q.outCount, (unsigned long long)inF) : 0ull;
+                const unsigned long long bR = inR ? atomicAdd(a.retiredCount, (unsigned long long)inR) : 0ull;
+                sBaseF = bF;
+                sBaseR = bR;
+            }
+        }
+        __syncthreads();
+        const unsigned long long baseF = sBaseF + sWarpF[warp], baseR = sBaseR + sWarpR[warp];
+#pragma unroll
+        for (int u = 0; u < kWorkItems; ++u) {
+            if (!act[u]) continue;
+            const uint32_t i = base + (uint32_t)u * kBlock + threadIdx.x;
+            if (ret[u]) {
+                const unsigned long long rs = baseR + rankR[u];
+                if (rs < a.retiredCap) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) a.retired[(size_t)rs * 4 + q] = w[u][q];
+                }
+                if (DET) a.q.dest[i] = -1;
             } else {
-                const int32_t src = rf::rankOf(sOff, R, i);
-                d = choose_dest(a.mode, src, r.y, R, sThr, a.gx, a.gy, a.gz);
-                w3.z = (uint32_t)d;
-                w3.y ^= r.z;
-                w3.w += 1u;
+                const unsigned long long slot = DET ? (unsigned long long)i : baseF + rankF[u];
+                if (slot < a.q.capacity) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) outq[(size_t)slot * 4 + q] = w[u][q];
+                    a.q.dest[slot] = d[u];
+                }
             }
         }
-        const bool fwd = active && !retire;
-        if (DET) {
-            if (fwd) {
-                uint4 *o = outq + (size_t)i * 4;
-                o[0] = w0;
-                o[1] = w1;
-                o[2] = w2;
-                o[3] = w3;
-            }
-            if (active) a.q.dest[i] = fwd ? d : -1;
-        } else {
-            const unsigned long long slot = rf::BlockAppend<kBlock>::reserve(sFwd, a.q.outCount, fwd);
-            if (fwd && slot < a.q.capacity) {
-                uint4 *o = outq + (size_t)slot * 4;
-                o[0] = w0;
-                o[1] = w1;
-                o[2] = w2;
-                o[3] = w3;
-                a.q.dest[slot] = d;
-            }
-        }
-        const bool ret = active && retire;
-        const unsigned long long rs = rf::BlockAppend<kBlock>::reserve(sRet, a.retiredCount, ret);
-        if (ret && rs < a.retiredCap) {
-            uint4 *o = a.retired + (size_t)rs * 4;
-            o[0] = w0;
-            o[1] = w1;
-            o[2] = w2;
-            o[3] = w3;
-        }
+        __syncthreads();  // the shared counts are rewritten by the next pass
     }
 }
 
@@ -329,7 +382,7 @@ rf_status launch_c1_work(rf_ctx *ctx, uint32_t seed, uint32_t hop, const unsigne
     a.gz = gz;
     // the incoming count is only known on the device: size the grid for the
     // capacity, up to 8 resident blocks per SM, and loop
-    const int grid = grid_for(ctx, ctx->capacity, 8);
+    const int grid = grid_for(ctx, (ctx->capacity + kWorkItems - 1) / kWorkItems, 8);
     time_begin(ctx, kTimeWork, s);
     if (deterministic) work_kernel<true><<<grid, kBlock, 0, s>>>(a);
     else work_kernel<false><<<grid, kBlock, 0, s>>>(a);
