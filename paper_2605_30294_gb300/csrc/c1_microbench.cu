@@ -215,18 +215,28 @@ struct C1Work {
     uint32_t seed;
     int32_t mode, gx, gy, gz, R;
 
-    // shared memory: the Zipf thresholds, or (up to 256 ranks) the torus
-    // neighbour table [rank][6] in bytes, small enough to keep three CTAs per SM
+    // shared memory: the Zipf thresholds (up to 256 ranks followed by a guide of
+    // 256 byte entries: guide[b] = the destination of r1 = b 2^24, the first
+    // threshold above it), or (up to 256 ranks) the torus neighbour table
+    // [rank][6] in bytes; small enough to keep three CTAs per SM
     __host__ __device__ bool nbrTable() const { return mode == RF_C1_NBR6 && R <= 256; }
+    __host__ __device__ bool zipfGuide() const { return mode == RF_C1_ZIPF && R <= 256; }
+    __host__ __device__ uint32_t thrBytes() const { return ((uint32_t)(R > 1 ? R - 1 : 1) * 4u + 15u) / 16u * 16u; }
     __host__ __device__ uint32_t smemBytes() const
     {
-        return nbrTable() ? ((uint32_t)R * 6u + 15u) / 16u * 16u : (uint32_t)(R > 1 ? R : 1) * 4u;
+        return nbrTable() ? ((uint32_t)R * 6u + 15u) / 16u * 16u
+                          : (zipfGuide() ? thrBytes() + 256u : (uint32_t)(R > 1 ? R : 1) * 4u);
     }
     __device__ void load_smem(void *s) const
     {
         if (mode == RF_C1_ZIPF) {
             uint32_t *t = static_cast<uint32_t *>(s);
             for (int e = threadIdx.x; e < R - 1; e += blockDim.x) t[e] = zipfThr[e];
+            if (zipfGuide()) {
+                uint8_t *g = static_cast<uint8_t *>(s) + thrBytes();
+                for (int b = threadIdx.x; b < 256; b += blockDim.x)
+                    g[b] = (uint8_t)choose_dest(RF_C1_ZIPF, 0, (uint32_t)b << 24, R, zipfThr, gx, gy, gz);
+            }
         }
         if (nbrTable()) {
             uint8_t *t = static_cast<uint8_t *>(s);
@@ -238,9 +248,18 @@ struct C1Work {
     {
         const uint4 r = philox4x32_10(make_uint4(w[0].x, w[0].y, w[3].w, round), make_uint2(seed, 1u));
         if (r.x < kRetire) return -1;
-        const int32_t d =
-            nbrTable() ? (int32_t)static_cast<const uint8_t *>(s)[rank * 6 + (int32_t)(((unsigned long long)r.y * 6u) >> 32)]
-                       : choose_dest(mode, rank, r.y, R, static_cast<const uint32_t *>(s), gx, gy, gz);
+        int32_t d;
+        if (nbrTable()) {
+            d = (int32_t)static_cast<const uint8_t *>(s)[rank * 6 + (int32_t)(((unsigned long long)r.y * 6u) >> 32)];
+        } else if (zipfGuide()) {
+            // start at the destination of the bucket's lowest r1 and walk up the
+            // (ascending) thresholds: the first k with r1 < thr[k], or R - 1
+            const uint32_t *t = static_cast<const uint32_t *>(s);
+            d = static_cast<const uint8_t *>(s)[thrBytes() + (r.y >> 24)];
+            while (d < R - 1 && r.y >= t[d]) ++d;
+        } else {
+            d = choose_dest(mode, rank, r.y, R, static_cast<const uint32_t *>(s), gx, gy, gz);
+        }
         w[3].z = (uint32_t)d;
         w[3].y ^= r.z;
         w[3].w += 1u;
