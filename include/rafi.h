@@ -240,6 +240,17 @@ rf_status rf_rounds_shapes(int32_t policy, int32_t *count, int32_t *shapes, int3
 rf_status rf_set_batched_config(rf_ctx *ctx, int32_t policy, int32_t form, int32_t shape);
 rf_status rf_get_batched_config(rf_ctx *ctx, int32_t policy, int32_t *form, int32_t *shape);
 
+/* Counts pushed ahead, for persistent runs that step on arrival (the
+ * microbenchmark's rf_c1_run_batched): when the next round holds at most
+ * maxItems items, each round's scatter also adds every item's next
+ * destination into the count row of the CTA that owns the item's slot in
+ * that round, so the round skips its count pass and its first grid barrier.
+ * Segment offsets and queue order are those of Sec. 4.2 either way; only the
+ * time differs.  0 turns it off; the default is 2^16 items.  The kernel caps
+ * the limit at (2^32 - 1) / CTAs - 1.  RF_ERR_ARG above 2^32 - 1. */
+rf_status rf_set_push_limit(rf_ctx *ctx, uint64_t maxItems);
+rf_status rf_get_push_limit(rf_ctx *ctx, uint64_t *maxItems);
+
 /* Kernels this library launched in this process so far (all contexts). */
 uint64_t rf_launch_count(void);
 

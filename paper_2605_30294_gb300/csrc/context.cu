@@ -501,6 +501,28 @@ rf_status rf_set_wait_limits(rf_ctx *ctx, uint64_t spinCycles, uint32_t missingA
     return RF_OK;
 }
 
+rf_status rf_set_push_limit(rf_ctx *ctx, uint64_t maxItems)
+{
+    if (rf_status st = check_ctx(ctx, "rf_set_push_limit")) return st;
+    if (maxItems > 0xFFFFFFFFull) {
+        set_error("rf_set_push_limit: %llu items above 2^32 - 1", (unsigned long long)maxItems);
+        return RF_ERR_ARG;
+    }
+    ctx->pushMax = (uint32_t)maxItems;
+    return RF_OK;
+}
+
+rf_status rf_get_push_limit(rf_ctx *ctx, uint64_t *maxItems)
+{
+    if (rf_status st = check_ctx(ctx, "rf_get_push_limit")) return st;
+    if (!maxItems) {
+        set_error("rf_get_push_limit: maxItems is NULL");
+        return RF_ERR_ARG;
+    }
+    *maxItems = ctx->pushMax;
+    return RF_OK;
+}
+
 rf_status rf_rounds_shapes(int32_t policy, int32_t *count, int32_t *shapes, int32_t cap)
 {
     if (!count || cap < 0 || (cap > 0 && !shapes)) {

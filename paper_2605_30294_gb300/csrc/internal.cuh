@@ -37,6 +37,10 @@ enum : unsigned int { RF_DEV_TIMEOUT = 1u };
 // 2 GHz); a wait that runs out sets RF_DEV_TIMEOUT and the kernel returns.
 constexpr long long kSpinLimitCycles = 1000000000ll;
 
+// Default largest round whose destination counts the persistent kernel's
+// scatter pushes ahead (steps on arrival), in items.
+constexpr uint32_t kPushMaxDefault = 1u << 16;
+
 }  // namespace rfi
 
 struct rf_ctx {
@@ -84,6 +88,7 @@ struct rf_ctx {
     int32_t batchedShape[3] = {0, 0, 0};
     unsigned long long waitLimitCycles = 0;  // bound of the persistent kernel's barrier waits (0: kSpinLimitCycles)
     uint32_t missingArrivals = 0;            // > 0 only to exercise the timeout path
+    uint32_t pushMax = rfi::kPushMaxDefault;  // rf_set_push_limit
 
     bool timing = false;
     unsigned pendingSlots = 0;  // timing slots recorded since the last read-back

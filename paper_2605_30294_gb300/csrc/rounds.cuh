@@ -24,7 +24,10 @@
 // Step on arrival (policies with kFuseStep): phase 3 applies the next
 // round's step to each item as it lands, so later rounds skip phase 1 and
 // only count the destinations the scatter wrote; each item crosses HBM once
-// per round.
+// per round.  When the next round is small enough (at most pushMax items)
+// the scatter also adds each item's next destination into the count row of
+// the CTA that will own the item's slot next round, so that round starts at
+// phase 2: no count pass and one barrier instead of two.
 //
 // Because every step is per item and every scatter stable, queue order never
 // depends on scheduling: round k's incoming queue equals the one of a serial
@@ -56,8 +59,9 @@ struct RoundsArgs {
     int32_t *dest;             // capacity rounded up to 4 entries + 4 (bulk-copied in 16-byte units)
     int32_t *dest2;            // the same size: second destination array (policies with kFuseStep)
     uint32_t *inOffset;        // numRanks + 1
-    uint32_t *tot;             // gridDim.x rows of per-CTA destination counts (row stride: digits rounded to 4)
-    uint32_t *grpTot;          // 2 x kSyncGroups rows (stride as tot): per-group destination totals (round parity)
+    uint32_t *tot;             // 3 x gridDim.x rows of per-CTA destination counts (row stride: digits rounded to 4)
+    uint32_t *grpTot;          // 3 x kSyncGroups rows (stride as tot): per-group destination totals
+                               // (both tables: one set per iteration modulo 3, zero when the launch starts)
     GridSync *sync;
     unsigned long long *result;  // {rounds, forwarded, status, retired}
     unsigned long long *numActiveOut;  // items still active when the kernel returns
@@ -69,6 +73,7 @@ struct RoundsArgs {
     const uint4 *seedItems;         // nullable: the seeded items, read in place instead of from the out-queue
     long long spinLimit;       // bound of every grid-barrier wait, in SM clock cycles
     uint32_t missingArrivals;  // CTAs a grid barrier waits for beyond the grid (0; > 0 only to test timeouts)
+    uint32_t pushMax;          // largest next round whose counts the scatter pushes (0: never; kFuseStep)
     uint32_t maxRounds;
     uint32_t roundLogCap;
     uint32_t fuseStep;  // apply steps on arrival (policies with kFuseStep)
@@ -534,6 +539,9 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
     // `fresh`: the incoming queue holds unstepped items (round 0, or after a
     // plain scatter), which phase 1 steps into P0.
     bool fresh = !pre;
+    // `pushed`: the previous scatter already added this round's destinations
+    // into the count rows, so the round starts at phase 2.
+    bool pushed = false;
     uint32_t xsel = 0u;
     auto curItemsOf = [&](uint32_t x) { return x ? a.in : a.out; };
     auto curDestOf = [&](uint32_t x) { return x ? a.dest2 : a.dest; };
@@ -690,7 +698,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                 const int32_t *dA = sDst + A * (kTile + 4u);
                 for (uint32_t v = tid; v < n * V; v += kB) a.out[v] = iA[v];
                 for (uint32_t i = tid; i < n; i += kB) a.dest[i] = dA[i];
-                for (int e = tid; e < 2 * kSyncGroups * Dp; e += kB) a.grpTot[e] = 0u;
+                for (int e = tid; e < 3 * kSyncGroups * Dp; e += kB) a.grpTot[e] = 0u;
                 xsel = 0u;
             } else {
                 for (int e = tid; e <= R; e += kB) a.inOffset[e] = 0u;
@@ -701,6 +709,9 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
             continue;
         }
         const int g = solo ? 1 : G;
+        // count tables of this iteration: set it mod 3 (the previous scatter may
+        // push into it; phase 2 clears the set two iterations ahead)
+        const uint32_t b3 = it % 3u;
         const bool logRound = !pre && a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
         if (logRound) a.roundLog[7 * round + 0] = globaltimer();
         for (int e = tid; e <= R; e += kB) sOff[e] = a.inOffset[e];
@@ -828,7 +839,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                 break;
             }
         }
-        if (dynamic || !fresh) {
+        if (dynamic || (!fresh && !pushed)) {
             // count the destinations of this CTA's range into per-warp rows:
             // 16-byte loads (lo is a multiple of 16 items), four in flight
             // per thread; the padded array covers the last vector's tail
@@ -862,11 +873,11 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
             __syncthreads();
             if (logRound && !fresh) a.roundLog[7 * round + 1] = globaltimer();
         }
-        if (!failed) {
+        if (!failed && !pushed) {
             for (int e = tid; e < D; e += kB) {
                 const uint32_t v = sTot[e];
-                a.tot[(size_t)c * Dp + e] = v;
-                if (v) atomicAdd(&a.grpTot[((it & 1u) * kSyncGroups + grp) * Dp + e], v);
+                a.tot[((size_t)b3 * G + c) * Dp + e] = v;
+                if (v) atomicAdd(&a.grpTot[(b3 * kSyncGroups + grp) * Dp + e], v);
             }
         }
         fence_proxy_async_global();
@@ -877,7 +888,10 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         int myD0[kK];
         uint32_t myR0[kK];
         bool earlyDone = false;
-        if (!solo && prefetched) {
+        if (pushed) {
+            // every count row was complete when the previous round's last barrier passed
+            if (logRound) a.roundLog[7 * round + 1] = globaltimer();
+        } else if (!solo && prefetched) {
             grid_arrive(a.sync, barrierSeq, sFlag + 1, a.missingArrivals);
             for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
             __syncwarp();
@@ -907,8 +921,8 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         {
             const uint32_t nGroups = (uint32_t)((G + grpSize - 1) / grpSize);
             const uint32_t mRows = (uint32_t)(c - grpStart);
-            const uint32_t *gSrc = a.grpTot + (size_t)(it & 1u) * kSyncGroups * Dp;
-            const uint32_t *mSrc = a.tot + (size_t)grpStart * Dp;
+            const uint32_t *gSrc = a.grpTot + (size_t)b3 * kSyncGroups * Dp;
+            const uint32_t *mSrc = a.tot + ((size_t)b3 * G + grpStart) * Dp;
             for (int e = tid; e < D; e += kB) {
                 dStart[e] = 0u;
                 dBase[e] = 0u;
@@ -955,12 +969,22 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         if (W::kAppendRetired && tid == 0) dStart[R] = (uint32_t)retiredSoFar;
         __syncthreads();
         for (int e = tid; e < D; e += kB) dBase[e] += dStart[e];
+        // clear the count tables of iteration it + 2 (last read in phase 2 of
+        // iteration it - 1; first written after this round's last barrier)
+        const uint32_t bz = (b3 + 2u) % 3u;
+        for (int e = tid; e < D; e += kB) a.tot[((size_t)bz * G + c) * Dp + e] = 0u;
         if (c == 0) {
             for (int e = tid; e < R; e += kB) a.inOffset[e] = dStart[e];
-            for (int e = tid; e < kSyncGroups * Dp; e += kB)
-                a.grpTot[(size_t)((it + 1u) & 1u) * kSyncGroups * Dp + e] = 0u;
+            for (int e = tid; e < kSyncGroups * Dp; e += kB) a.grpTot[(size_t)bz * kSyncGroups * Dp + e] = 0u;
             if (tid == 0) a.inOffset[R] = nNext;
         }
+        // Push the next round's counts from this scatter when that round is a
+        // grid round of at most pushMax items: its owner of slot p is the last
+        // CTA whose range starts at or before p's 16-item chunk.  Every CTA
+        // takes the same decision (nNext is a grid-wide total).
+        const bool push = kFuse && fuse && !solo && nNext > kSoloItems && nNext <= a.pushMax;
+        uint32_t *const totNext = a.tot + (size_t)((b3 + 1u) % 3u) * G * Dp;
+        uint32_t *const grpNext = a.grpTot + (size_t)((b3 + 1u) % 3u) * kSyncGroups * Dp;
         if (!pre) forwarded += nNext;
         retiredSoFar += retiredNow;
         __syncthreads();
@@ -999,7 +1023,15 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                     if (r < a.retiredCap) a.retiredOut[(size_t)r * V + part] = val;
                 } else {
                     nxtItems[(size_t)dst * V + part] = val;
-                    if (kFuse && fuse && part == 0u) nxtDest[dst] = dts[src];
+                    if (kFuse && fuse && part == 0u) {
+                        const int32_t d2 = dts[src];
+                        nxtDest[dst] = d2;
+                        if (push && (uint32_t)d2 < (uint32_t)D) {
+                            const uint32_t oc = ((uint32_t)G * ((dst & ~15u) + 1u) - 1u) / nNext;
+                            atomicAdd(&totNext[(size_t)oc * Dp + d2], 1u);
+                            atomicAdd(&grpNext[(size_t)(oc / (uint32_t)grpSize) * Dp + d2], 1u);
+                        }
+                    }
                 }
             }
             __syncthreads();  // the buffer is read before its next bulk load is issued
@@ -1016,6 +1048,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         }
         if (logRound) a.roundLog[7 * round + 4] = globaltimer();
         n = nNext;
+        pushed = push;
         fresh = !fuse;
         xsel = fuse ? xsel ^ 1u : 0u;
         if (pre) pre = false;
@@ -1104,8 +1137,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         return RF_ERR_ARG;
     }
     const int G = ctx->numSMs * perSM;
-    const size_t totBytes = (size_t)G * rounds_row_stride(D) * sizeof(uint32_t);
-    const size_t grpBytes = (size_t)2 * kSyncGroups * rounds_row_stride(D) * sizeof(uint32_t);
+    const size_t totBytes = (size_t)3 * G * rounds_row_stride(D) * sizeof(uint32_t);
+    const size_t grpBytes = (size_t)3 * kSyncGroups * rounds_row_stride(D) * sizeof(uint32_t);
     const size_t tailBytes = grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
     // second destination array (step on arrival), padded like ctx->dest
     const size_t dest2Bytes = W::kFuseStep ? rounds_align_sz((size_t)(ctx->capacity + 3) / 4 * 16 + 16, 256) : 0;
@@ -1132,9 +1165,12 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.fuseStep = stepOnArrival ? 1u : 0u;
     a.spinLimit = ctx->waitLimitCycles ? (long long)ctx->waitLimitCycles : kSpinLimitCycles;
     a.missingArrivals = ctx->missingArrivals;
+    // the owner of a pushed count is computed in 32 bits: G x (pushMax + 1) < 2^32
+    const uint32_t pushCap = (uint32_t)(0xFFFFFFFFu / (uint32_t)G) - 1u;
+    a.pushMax = W::kFuseStep && stepOnArrival ? (ctx->pushMax < pushCap ? ctx->pushMax : pushCap) : 0u;
     a.maxRounds = maxRounds;
     a.numRanks = R;
-    RF_CUDA(cudaMemsetAsync(base + totBytes, 0, tailBytes, s));
+    RF_CUDA(cudaMemsetAsync(base, 0, totBytes + tailBytes, s));
     W w = work;
     void *params[] = {&a, &w};
     time_begin(ctx, kTimeRounds, s);

@@ -80,6 +80,8 @@ _SIGS = {
     "rf_rounds_shapes": [_i32, _P, _P, _i32],
     "rf_set_batched_config": [_P, _i32, _i32, _i32],
     "rf_get_batched_config": [_P, _i32, _P, _P],
+    "rf_set_push_limit": [_P, _u64],
+    "rf_get_push_limit": [_P, _P],
     "rf_launch_count": [],
     "rf_last_error": [],
     "rf_partition_static": [_P, _P, _u64, _u32, _i32, _P, _P, _P, _P],
@@ -195,6 +197,16 @@ def rf_get_batched_config(ctx: int, policy: int):
     f, sh = ctypes.c_int32(), ctypes.c_int32()
     _check("rf_get_batched_config", lib().rf_get_batched_config(ctx, policy, ctypes.byref(f), ctypes.byref(sh)))
     return f.value, sh.value
+
+
+def rf_set_push_limit(ctx: int, max_items: int) -> None:
+    _check("rf_set_push_limit", lib().rf_set_push_limit(ctx, max_items))
+
+
+def rf_get_push_limit(ctx: int) -> int:
+    v = ctypes.c_uint64()
+    _check("rf_get_push_limit", lib().rf_get_push_limit(ctx, ctypes.byref(v)))
+    return v.value
 
 
 def rf_launch_count() -> int:

@@ -94,3 +94,11 @@ def test_wait_limits_refuse_a_null_context_and_wild_values():
     with pytest.raises(rafi.RafiError) as e:
         rafi.rf_set_wait_limits(0, 1000, 0)
     assert e.value.status == rafi.RF_ERR_ARG
+
+
+def test_push_limit_refuses_a_null_context():
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_set_push_limit(0, 1 << 17)
+    assert e.value.status == rafi.RF_ERR_ARG
+    with pytest.raises(rafi.RafiError):
+        rafi.rf_get_push_limit(0)

@@ -445,3 +445,22 @@ def test_every_persistent_shape_retires_in_the_oracle_order(mode, shape, n, fuse
     assert st == rafi.RF_OK and len(got) == n
     assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
     np.testing.assert_array_equal(got, want["retired_items"])
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("push", [0, 1024, 1 << 17, 1 << 21, (1 << 32) - 1])
+def test_pushed_counts_keep_the_oracle_order(mode, push):
+    # Whether a round's counts come from its own count pass or were pushed by
+    # the previous scatter (every round of at most `push` items; 2^21 and
+    # above push every round after the first, 2^32 - 1 is capped by the
+    # kernel), the retirement buffer is the oracle's, every word
+    n, seed = 1 << 21, 47
+    items = inputs.c1_items(n, seed=seed)
+    want = oracle.c1_rounds(items, R, seed, mode, grid=GRID)
+    with rafi.Context(R, 64, n) as ctx:
+        rafi.rf_set_push_limit(ctx.handle, push)
+        assert rafi.rf_get_push_limit(ctx.handle) == push
+        got, rounds, fwd, st = _run_batched(items, seed, mode, ctx=ctx)
+    assert st == rafi.RF_OK and len(got) == n
+    assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
+    np.testing.assert_array_equal(got, want["retired_items"])
