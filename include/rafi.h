@@ -251,6 +251,18 @@ rf_status rf_get_batched_config(rf_ctx *ctx, int32_t policy, int32_t *form, int3
 rf_status rf_set_push_limit(rf_ctx *ctx, uint64_t maxItems);
 rf_status rf_get_push_limit(rf_ctx *ctx, uint64_t *maxItems);
 
+/* Rank skew, for persistent runs that step on arrival: CTAs that share an SM
+ * are served unevenly by its memory pipeline (the earlier-launched first), so
+ * equal ranges finish at different times and the SM idles on its last CTA.
+ * With skew > 0, rounds of at least 2^19 items give each CTA a range in
+ * proportion to 256 + skew x (k - 1 - 2 rho), rho its launch order among the k
+ * CTAs on its SM (read from %smid once per launch, at the cost of one grid
+ * barrier).  Queue order is that of Sec. 4.2.1 for any partition of the
+ * queue into CTA ranges, so only the time differs.  0 (equal ranges) up to
+ * 32, default 10; RF_ERR_ARG above 32. */
+rf_status rf_set_rank_skew(rf_ctx *ctx, uint32_t skew);
+rf_status rf_get_rank_skew(rf_ctx *ctx, uint32_t *skew);
+
 /* Kernels this library launched in this process so far (all contexts). */
 uint64_t rf_launch_count(void);
 

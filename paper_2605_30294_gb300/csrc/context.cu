@@ -523,6 +523,28 @@ rf_status rf_get_push_limit(rf_ctx *ctx, uint64_t *maxItems)
     return RF_OK;
 }
 
+rf_status rf_set_rank_skew(rf_ctx *ctx, uint32_t skew)
+{
+    if (rf_status st = check_ctx(ctx, "rf_set_rank_skew")) return st;
+    if (skew > 32u) {
+        set_error("rf_set_rank_skew: skew %u above 32", skew);
+        return RF_ERR_ARG;
+    }
+    ctx->rankSkew = skew;
+    return RF_OK;
+}
+
+rf_status rf_get_rank_skew(rf_ctx *ctx, uint32_t *skew)
+{
+    if (rf_status st = check_ctx(ctx, "rf_get_rank_skew")) return st;
+    if (!skew) {
+        set_error("rf_get_rank_skew: skew is NULL");
+        return RF_ERR_ARG;
+    }
+    *skew = ctx->rankSkew;
+    return RF_OK;
+}
+
 rf_status rf_rounds_shapes(int32_t policy, int32_t *count, int32_t *shapes, int32_t cap)
 {
     if (!count || cap < 0 || (cap > 0 && !shapes)) {

@@ -41,6 +41,9 @@ constexpr long long kSpinLimitCycles = 1000000000ll;
 // scatter pushes ahead (steps on arrival), in items.
 constexpr uint32_t kPushMaxDefault = 1u << 16;
 
+// Default rank skew of the persistent kernel's large-round ranges, in 1/256.
+constexpr uint32_t kRankSkewDefault = 10u;
+
 }  // namespace rfi
 
 struct rf_ctx {
@@ -89,6 +92,7 @@ struct rf_ctx {
     unsigned long long waitLimitCycles = 0;  // bound of the persistent kernel's barrier waits (0: kSpinLimitCycles)
     uint32_t missingArrivals = 0;            // > 0 only to exercise the timeout path
     uint32_t pushMax = rfi::kPushMaxDefault;  // rf_set_push_limit
+    uint32_t rankSkew = rfi::kRankSkewDefault;  // rf_set_rank_skew
 
     bool timing = false;
     unsigned pendingSlots = 0;  // timing slots recorded since the last read-back

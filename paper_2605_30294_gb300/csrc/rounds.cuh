@@ -74,6 +74,8 @@ struct RoundsArgs {
     long long spinLimit;       // bound of every grid-barrier wait, in SM clock cycles
     uint32_t missingArrivals;  // CTAs a grid barrier waits for beyond the grid (0; > 0 only to test timeouts)
     uint32_t pushMax;          // largest next round whose counts the scatter pushes (0: never; kFuseStep)
+    uint32_t *smOf;            // gridDim.x words: each CTA's SM (rank skew)
+    uint32_t skew;             // rank skew of large rounds' ranges, in 1/256 (0: equal ranges; <= 32)
     uint32_t maxRounds;
     uint32_t roundLogCap;
     uint32_t fuseStep;  // apply steps on arrival (policies with kFuseStep)
@@ -513,6 +515,8 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
     // CTAs return and the round barriers become block barriers.  (Rounds of two
     // to four tiles measured 10-17 us on one CTA against about 10 us on the grid.)
     constexpr uint32_t kSoloItems = kTile;
+    constexpr uint32_t kSkewItems = 1u << 19;
+    constexpr int kCountLoads = 4;  // 16-byte destination loads in flight per thread in the count pass
     bool solo = false;
     unsigned int barrierSeq = 0;  // grid barriers passed (every CTA passes the same ones)
     auto round_barrier = [&]() -> bool {
@@ -634,8 +638,61 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         return rank_b(ownBases, carryPrev, myD, myR);
     };
 
+    // Co-resident CTAs do not get equal shares of their SM's memory
+    // bandwidth: the older ones (lower blockIdx among the CTAs on an SM) are
+    // served first and finish equal ranges early, and the SM idles on its
+    // last CTA.  With a.skew > 0, rounds of at least kSkewItems items give
+    // CTA c a range in proportion to w = 256 + skew (k - 1 - 2 rho), rho its
+    // launch order among the k CTAs on its SM: [W0, W1) of the grid's Wt.
+    // The weights come from every CTA's %smid, exchanged once per launch.
+    unsigned long long W0 = 0, W1 = 0, Wt = 0;
+    bool skewed = a.skew > 0u && G > 1;
+    if (skewed) {
+        if (tid == 0) {
+            unsigned sm;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+            a.smOf[c] = sm;
+        }
+        if (!grid_barrier(a.sync, sFlag, barrierSeq++, a.spinLimit, a.missingArrivals)) {
+            failed = true;
+        } else {
+            // every CTA's SM in the tile buffer (unused until round 0 stages a tile)
+            uint32_t *sSm = reinterpret_cast<uint32_t *>(sBuf);
+            uint32_t *acc = sSm + G;
+            for (int e = tid; e < G; e += kB) sSm[e] = __ldcg(a.smOf + e);
+            if (tid < 3) acc[tid] = 0u;
+            __syncthreads();
+            uint32_t below = 0, all = 0, mine = 0;
+            for (int e = tid; e < G; e += kB) {
+                int rho = 0, k = 0;
+                for (int f = 0; f < G; ++f) {
+                    const bool same = sSm[f] == sSm[e];
+                    k += same;
+                    rho += same && f < e;
+                }
+                const uint32_t w = (uint32_t)max(1, 256 + (int)a.skew * (k - 1 - 2 * rho));
+                all += w;
+                if (e < c) below += w;
+                if (e == c) mine = w;
+            }
+            atomicAdd(&acc[0], below);
+            atomicAdd(&acc[1], mine);
+            atomicAdd(&acc[2], all);
+            __syncthreads();
+            W0 = acc[0];
+            W1 = W0 + acc[1];
+            Wt = acc[2];
+            __syncthreads();  // the tile buffer is free again
+        }
+    }
+    // CTA c's range under the skew: boundaries rounded up to 16 items
+    auto wbound = [&](uint32_t m, unsigned long long W) -> uint32_t {
+        const unsigned long long v = ((unsigned long long)m * W / Wt + 15ull) & ~15ull;
+        return (uint32_t)(v < m ? v : m);
+    };
+
     for (;; ++it) {
-        if (n == 0 || (!pre && round >= a.maxRounds)) break;
+        if (failed || n == 0 || (!pre && round >= a.maxRounds)) break;
         if (!solo && n <= kSoloItems) {
             solo = true;
             if (c != 0) break;
@@ -714,11 +771,15 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         const uint32_t b3 = it % 3u;
         const bool logRound = !pre && a.roundLog && c == 0 && tid == 0 && round < a.roundLogCap;
         if (logRound) a.roundLog[7 * round + 0] = globaltimer();
-        for (int e = tid; e <= R; e += kB) sOff[e] = a.inOffset[e];
+        // segment offsets: phase 1 ranks its items by them (a stepped queue needs none)
+        if (fresh || W::kDynamicWork)
+            for (int e = tid; e <= R; e += kB) sOff[e] = a.inOffset[e];
         for (int e = tid; e < D; e += kB) sTot[e] = 0u;
         __syncthreads();
-        const uint32_t lo = bound(n, c, g);
-        const uint32_t hi = bound(n, c + 1, g);
+        // (a round whose counts were pushed keeps the equal ranges the push assumed)
+        const bool weighted = skewed && !solo && !pushed && n >= kSkewItems;
+        const uint32_t lo = weighted ? wbound(n, W0) : bound(n, c, g);
+        const uint32_t hi = weighted ? wbound(n, W1) : bound(n, c + 1, g);
         const uint32_t nt = (hi - lo + kTile - 1) / kTile;
 
         // ---- phase 1: work step, write back to the same slots ------------------
@@ -841,21 +902,21 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         }
         if (dynamic || (!fresh && !pushed)) {
             // count the destinations of this CTA's range into per-warp rows:
-            // 16-byte loads (lo is a multiple of 16 items), four in flight
-            // per thread; the padded array covers the last vector's tail
+            // 16-byte loads (lo is a multiple of 16 items), kCountLoads in
+            // flight per thread; the padded array covers the last vector's tail
             for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
             __syncwarp();
             const int4 *dv = reinterpret_cast<const int4 *>(curDest + lo);
             const uint32_t nv = (hi - lo + 3u) / 4u;
-            for (uint32_t v0 = 0; v0 < nv; v0 += 4u * kB) {
-                int4 x[4];
+            for (uint32_t v0 = 0; v0 < nv; v0 += (uint32_t)kCountLoads * kB) {
+                int4 x[kCountLoads];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kCountLoads; ++u) {
                     const uint32_t v = v0 + (uint32_t)u * kB + tid;
                     x[u] = v < nv ? __ldcg(dv + v) : make_int4(-1, -1, -1, -1);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kCountLoads; ++u) {
                     const uint32_t i = lo + 4u * (v0 + (uint32_t)u * kB + tid);
                     const int32_t e4[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
 #pragma unroll
@@ -1139,7 +1200,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     const int G = ctx->numSMs * perSM;
     const size_t totBytes = (size_t)3 * G * rounds_row_stride(D) * sizeof(uint32_t);
     const size_t grpBytes = (size_t)3 * kSyncGroups * rounds_row_stride(D) * sizeof(uint32_t);
-    const size_t tailBytes = grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long);
+    const size_t smBytes = rounds_align_sz((size_t)G * sizeof(uint32_t), 16);
+    const size_t tailBytes = grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long) + smBytes;
     // second destination array (step on arrival), padded like ctx->dest
     const size_t dest2Bytes = W::kFuseStep ? rounds_align_sz((size_t)(ctx->capacity + 3) / 4 * 16 + 16, 256) : 0;
     if (rf_status st = ensure_rounds_scratch(ctx, rounds_align_sz(totBytes + tailBytes, 256) + dest2Bytes)) return st;
@@ -1153,6 +1215,11 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.grpTot = reinterpret_cast<uint32_t *>(base + totBytes);
     a.sync = reinterpret_cast<GridSync *>(base + totBytes + grpBytes);
     a.result = reinterpret_cast<unsigned long long *>(base + totBytes + grpBytes + sizeof(GridSync));
+    a.smOf = reinterpret_cast<uint32_t *>(base + totBytes + grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long));
+    // the SM table is staged in the tile buffers: G + 3 words must fit
+    a.skew = W::kFuseStep && ((size_t)G + 3) * 4 <= (size_t)2 * W::kBlock * W::kItemsPerThread * itemBytes
+                 ? (ctx->rankSkew < 32u ? ctx->rankSkew : 32u)
+                 : 0u;
     a.dest2 = W::kFuseStep ? reinterpret_cast<int32_t *>(base + rounds_align_sz(totBytes + tailBytes, 256)) : nullptr;
     a.numActiveOut = &ctx->dev->numActive;
     a.roundLog = roundLog;

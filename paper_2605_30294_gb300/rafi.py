@@ -82,6 +82,8 @@ _SIGS = {
     "rf_get_batched_config": [_P, _i32, _P, _P],
     "rf_set_push_limit": [_P, _u64],
     "rf_get_push_limit": [_P, _P],
+    "rf_set_rank_skew": [_P, _u32],
+    "rf_get_rank_skew": [_P, _P],
     "rf_launch_count": [],
     "rf_last_error": [],
     "rf_partition_static": [_P, _P, _u64, _u32, _i32, _P, _P, _P, _P],
@@ -206,6 +208,16 @@ def rf_set_push_limit(ctx: int, max_items: int) -> None:
 def rf_get_push_limit(ctx: int) -> int:
     v = ctypes.c_uint64()
     _check("rf_get_push_limit", lib().rf_get_push_limit(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def rf_set_rank_skew(ctx: int, skew: int) -> None:
+    _check("rf_set_rank_skew", lib().rf_set_rank_skew(ctx, skew))
+
+
+def rf_get_rank_skew(ctx: int) -> int:
+    v = ctypes.c_uint32()
+    _check("rf_get_rank_skew", lib().rf_get_rank_skew(ctx, ctypes.byref(v)))
     return v.value
 
 

@@ -102,3 +102,11 @@ def test_push_limit_refuses_a_null_context():
     assert e.value.status == rafi.RF_ERR_ARG
     with pytest.raises(rafi.RafiError):
         rafi.rf_get_push_limit(0)
+
+
+def test_rank_skew_refuses_a_null_context():
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_set_rank_skew(0, 4)
+    assert e.value.status == rafi.RF_ERR_ARG
+    with pytest.raises(rafi.RafiError):
+        rafi.rf_get_rank_skew(0)

@@ -464,3 +464,39 @@ def test_pushed_counts_keep_the_oracle_order(mode, push):
     assert st == rafi.RF_OK and len(got) == n
     assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
     np.testing.assert_array_equal(got, want["retired_items"])
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("skew", [0, 5, 32])
+def test_rank_skewed_ranges_keep_the_oracle_order(mode, skew):
+    # Large rounds (2^19 items and up) split by SM launch order instead of
+    # evenly: the same queues, so the retirement buffer is the oracle's
+    n, seed = 1 << 21, 53
+    items = inputs.c1_items(n, seed=seed)
+    want = oracle.c1_rounds(items, R, seed, mode, grid=GRID)
+    with rafi.Context(R, 64, n) as ctx:
+        rafi.rf_set_rank_skew(ctx.handle, skew)
+        assert rafi.rf_get_rank_skew(ctx.handle) == skew
+        with pytest.raises(rafi.RafiError):
+            rafi.rf_set_rank_skew(ctx.handle, 33)
+        got, rounds, fwd, st = _run_batched(items, seed, mode, ctx=ctx)
+    assert st == rafi.RF_OK and len(got) == n
+    assert rounds == int(want["rounds"]) and fwd == int(want["active"][1:].sum())
+    np.testing.assert_array_equal(got, want["retired_items"])
+
+
+def test_rank_skew_setup_barrier_timeout_is_reported():
+    # the launch-time exchange of SM ids waits at a grid barrier too: with a
+    # missing arrival it gives up, and the context then runs normally
+    n, seed = 300007, 59
+    items = inputs.c1_items(n, seed=seed)
+    final, hops, _, _ = oracle.c1_walk(items, R, seed, rafi.RF_C1_UNIFORM, grid=GRID)
+    with rafi.Context(R, 64, n) as ctx:
+        rafi.rf_set_rank_skew(ctx.handle, 8)
+        rafi.rf_set_wait_limits(ctx.handle, 20000, 1)
+        got, rounds, fwd, st = _run_batched(items, seed, rafi.RF_C1_UNIFORM, ctx=ctx, allow=(rafi.RF_ERR_TIMEOUT,))
+        assert st == rafi.RF_ERR_TIMEOUT
+        rafi.rf_set_wait_limits(ctx.handle, 0, 0)
+        got, rounds, fwd, st = _run_batched(items, seed, rafi.RF_C1_UNIFORM, ctx=ctx)
+        assert st == rafi.RF_OK and len(got) == n
+        np.testing.assert_array_equal(canonical_rows(got), canonical_rows(final))
