@@ -176,8 +176,11 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *p, unsign
 // before the barrier with every read after it.  `missing` is 0 in normal
 // runs; a positive value names CTAs that never arrive, so every wait runs
 // out after `limit` cycles (the timeout path, exercised without a fault).
-// A wait that runs out raises the abort flag; every CTA that sees it gives up.
-// Returns false when any CTA has given up; the caller must then return.
+// A wait that runs out raises the abort flag; every CTA that sees it while
+// waiting gives up.  Returns false when this CTA gave up; the caller must
+// then return.  A CTA that gave up arrives at no later barrier, so the others
+// give up at their next one at the latest: a barrier that completes needs no
+// extra read of the flag on its critical path.
 __device__ inline bool barrier_wait_bounded(GridSync *gs, unsigned int target, long long limit)
 {
     const long long t0 = clock64();
@@ -201,9 +204,7 @@ __device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned 
     if (threadIdx.x == 0) {
         const unsigned int target = (gridDim.x + missing) * (seq + 1u);
         const bool last = atom_add_release(&gs->count, 1u) + 1u == target;
-        unsigned int ok = last ? 1u : (barrier_wait_bounded(gs, target, limit) ? 1u : 0u);
-        if (ld_acquire(&gs->abort)) ok = 0;
-        *sFlag = ok;
+        *sFlag = last ? 1u : (barrier_wait_bounded(gs, target, limit) ? 1u : 0u);
     }
     __syncthreads();
     return *sFlag != 0;
@@ -213,7 +214,7 @@ __device__ inline bool grid_barrier(GridSync *gs, unsigned int *sFlag, unsigned 
 // CTA between arriving and waiting: grid_arrive (all threads; thread 0 adds
 // to the counter, its earlier writes released) returns whether this CTA
 // arrived last; grid_wait (all threads) waits for the rest, bounded, and
-// returns false when any CTA has given up.
+// returns false when this CTA gave up.
 __device__ inline void grid_arrive(GridSync *gs, unsigned int seq, unsigned int *sLast, unsigned int missing)
 {
     __syncthreads();
@@ -226,10 +227,7 @@ __device__ inline bool grid_wait(GridSync *gs, unsigned int *sFlag, unsigned int
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned int ok = 1;
-        if (!*sLast) ok = barrier_wait_bounded(gs, (gridDim.x + missing) * (seq + 1u), limit) ? 1u : 0u;
-        if (ld_acquire(&gs->abort)) ok = 0;
-        *sFlag = ok;
+        *sFlag = *sLast ? 1u : (barrier_wait_bounded(gs, (gridDim.x + missing) * (seq + 1u), limit) ? 1u : 0u);
     }
     __syncthreads();
     return *sFlag != 0;
