@@ -55,7 +55,7 @@ WORKLOAD = ("forwarding microbenchmark: 2^24 x 64-byte items (Philox payloads), 
             "destinations uniform / Zipf s=1.1 / 6-neighbour 4x4x4 torus, retire p=0.1, seed 1; "
             "one step = the three runs, each seeded and run to zero active items")
 SAMPLE_ITEMS = 1 << 21  # oracle sample per destination law, per reference-arm step (all host threads)
-BASELINE_ITEMS = 1 << 22  # single-thread oracle sample per destination law for cpu_baseline (about 5 s)
+CPU_SAMPLE_ITEMS = 1 << 22  # single-thread oracle sample per destination law for cpu_baseline (about 5 s)
 C2_ORACLE_SEEDS = 1 << 14  # streamline seeds the oracle traces for cpu_baseline
 C4_ORACLE_CROP = 64  # 64 x 64 pixel crop of the first view the oracle renders for cpu_baseline
 
@@ -199,7 +199,7 @@ def oracle_baseline(n=N_ITEMS):
 
     items = inputs.c1_items(n, seed=SEED)
     t0 = time.perf_counter()
-    fwd1 = oracle_sample_step(items[:BASELINE_ITEMS])
+    fwd1 = oracle_sample_step(items[:CPU_SAMPLE_ITEMS])
     dt1 = time.perf_counter() - t0
     threads = host_threads()
     t0 = time.perf_counter()
@@ -210,7 +210,7 @@ def oracle_baseline(n=N_ITEMS):
                       f"run round by round through the oracle's queues, one host thread each, {dt:.1f} s",
             "cpu": cpu_model(),
             "single_thread": {"value": fwd1 / dt1, "unit": "items/s", "cores": 1,
-                              "sample": f"{BASELINE_ITEMS} items per destination law, {dt1:.1f} s"}}
+                              "sample": f"{CPU_SAMPLE_ITEMS} items per destination law, {dt1:.1f} s"}}
 
 
 def repeat_for(fn, min_s=1.0):
