@@ -240,6 +240,34 @@ __device__ inline uint32_t rounds_block_scan(uint32_t *v, int n, uint32_t *tmp)
     constexpr int kWarps = kB / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __syncthreads();
+    if (n <= 256) {
+        // up to 256 entries: warp 0 alone, eight per lane, between two barriers
+        if (warp == 0) {
+            uint32_t x[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int i = lane * 8 + j;
+                const uint32_t t = i < n ? v[i] : 0u;
+                x[j] = sum;
+                sum += t;
+            }
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t base = incl - sum;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int i = lane * 8 + j;
+                if (i < n) v[i] = base + x[j];
+            }
+            if (lane == 31) tmp[kWarps] = incl;
+        }
+        __syncthreads();
+        return tmp[kWarps];  // the next scan starts with a barrier before it writes tmp
+    }
     uint32_t x[8], sum = 0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
