@@ -1082,11 +1082,14 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
             const int buf = t & 1;
             const uint32_t b = lo + t * kTile;
             const uint32_t cnt = min(kTile, hi - b);
-            if (tid == 0 && t + 1 < nt) issue3(buf ^ 1, b + kTile);
             int32_t *dts = sDst + buf * (kTile + 4u);
             uint4 *sItems = sBuf + buf * kTileVecs;
             uint32_t nValid;
+            // The next tile goes into the other buffer once every thread is past
+            // the scatter that last read it: after this tile's wait (a block
+            // barrier), or at once for the first tile (phase 2 ended with one).
             if (t == 0 && earlyDone) {
+                if (tid == 0 && t + 1 < nt) issue3(buf ^ 1, b + kTile);
                 nValid = rank_b(false, false, myD0, myR0);
             } else {
                 for (int e = lane; e < D; e += 32) wc[warp * D + e] = 0u;
@@ -1094,6 +1097,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                     failed = true;
                     break;
                 }
+                if (tid == 0 && t + 1 < nt) issue3(buf ^ 1, b + kTile);
                 nValid = rank_tile(sItems, dts, cnt, fuse, q, false, t > 0);
             }
             // consecutive threads write consecutive 16-byte vectors of the
@@ -1121,7 +1125,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                     }
                 }
             }
-            __syncthreads();  // the buffer is read before its next bulk load is issued
+            // (no barrier: the next tile's wait is the one before this buffer is refilled)
         }
         fence_proxy_async_global();
         if (logRound) {
