@@ -5,23 +5,28 @@ One step = the forwarding microbenchmark run to termination three times
 64-byte items over 64 logical ranks, seed, exchange, then {work; exchange}
 rounds until no item is active.  ``value`` counts items delivered by the
 exchanges of work rounds (the seed exchange is timed but not counted) per
-second of device time, for the batched form (all rounds of a run in one
-persistent kernel, rf_c1_run_batched); inputs are resident in HBM before
-timing, and the 1 GiB queues are larger than L2.
+second of device time, for the batched form: the three runs in one
+persistent kernel (rf_c1_run_batched_runs), every round of every run inside
+it; each run keeps its own queues and retirement order, exactly those of a
+launch of its own.  Inputs are resident in HBM before timing, and the
+queues (3 GiB) are larger than L2.
 
 Also reported on the same line: the persistent kernel's roofline
 (algorithmic bytes over its CUDA-event time) and its per-round count and
-scatter phase rates from its round log; the plain per-round host loop
-(rf_c1_run) with the scatter kernel's roofline; the same run end to end
-through rf_c1_run_batched with host buffers; rays/s of the 64^3 marching
-workload; particle-steps/s of the streamline workload (512^3 field, 16
-uneven seed sets in one launch, batched and plain forms); rays/s of the
-differentiable renderer (forward and adjoint) and paths/s of the delta-tracking
-transport (1024^3, 512 ranks, four views at 16 spp); the oracle timed
-on the host (cpu_baseline, one GPU only): single-threaded on a bounded
-sample, on all host threads over the whole microbenchmark, and on subsets
-of the streamline and transport workloads; SM clocks sampled during the
-timed region and the number of kernels launched.
+scatter phase rates from its round log; the same runs as three separate
+persistent launches (rf_c1_run_batched) with per-law times; the
+step-in-place persistent form, the host loop's kernels in a CUDA graph and
+the plain per-round host loop (rf_c1_run) with the scatter kernel's
+roofline; the same step end to end through rf_c1_run_batched_runs with host
+buffers; rays/s of the 64^3 marching workload; particle-steps/s of the
+streamline workload (512^3 field, 16 uneven seed sets in one launch, batched
+and plain forms); rays/s of the differentiable renderer (forward and
+adjoint) and paths/s of the delta-tracking transport (1024^3, 512 ranks,
+four views at 16 spp); the oracle timed on the host (cpu_baseline, one GPU
+only): single-threaded on a bounded sample, on all host threads over the
+whole microbenchmark, and on subsets of the streamline and transport
+workloads; SM clocks sampled during the timed region and the number of
+kernels launched.
 
 ``--impl reference`` times the oracle (the CPU reference of this method) on a
 bounded sample of the same workload instead, on all host threads.
@@ -696,12 +701,27 @@ def run_ours(args):
     n = args.items
     items = inputs.c1_items(n, seed=SEED)
     d_items = torch.from_numpy(items.view(np.int32)).to(dev)
-    retired = torch.zeros((n, 16), dtype=torch.int32, device=dev)
+    # the three runs of a step hold the same seeded items (one copy per run for
+    # the joint launch, whose run k reads items [k n, (k + 1) n))
+    d_items3 = torch.cat([d_items] * len(MODES))
+    retired = torch.zeros((len(MODES) * n, 16), dtype=torch.int32, device=dev)
     log = torch.zeros(7 * LOG_CAP, dtype=torch.int64, device=dev)
     s = torch.cuda.current_stream(dev)
-    ctx = rafi.Context(RANKS, ITEM_BYTES, n)
+    ctx = rafi.Context(RANKS, ITEM_BYTES, n)  # one run at a time
+    ctx3 = rafi.Context(RANKS, ITEM_BYTES, len(MODES) * n)  # the three runs in one launch
+
+    def joint(round_log=None):
+        # one step: the three runs in one persistent launch
+        st, cnt, rounds, f = rafi.rf_c1_run_batched_runs(ctx3.handle, d_items3, n, SEED, list(MODES), 1.1, GRID,
+                                                         retired, stream=s, round_log=round_log,
+                                                         round_log_cap=LOG_CAP if round_log is not None else 0)
+        if cnt != [n] * len(MODES):
+            raise RuntimeError(f"joint runs: {cnt} of {n} items retired per run")
+        return f
 
     def step(batched, round_log=None, fuse=True, per_mode=None):
+        if batched == "joint":
+            return joint(round_log)
         fwd = 0
         for mode in MODES:
             if per_mode is not None:
@@ -727,8 +747,9 @@ def run_ours(args):
         return fwd
 
     def timed(batched, steps, fuse=True):
-        rafi.rf_set_timing(ctx.handle, True)
-        rafi.rf_get_timing(ctx.handle, reset=True)
+        c = ctx3 if batched == "joint" else ctx
+        rafi.rf_set_timing(c.handle, True)
+        rafi.rf_get_timing(c.handle, reset=True)
         barrier()
         launches0 = rafi.rf_launch_count()
         per_mode = {}
@@ -741,8 +762,8 @@ def run_ours(args):
             e1.record(s)
             barrier()
         launches = rafi.rf_launch_count() - launches0
-        t = rafi.rf_get_timing(ctx.handle, reset=True)
-        rafi.rf_set_timing(ctx.handle, False)
+        t = rafi.rf_get_timing(c.handle, reset=True)
+        rafi.rf_set_timing(c.handle, False)
         # per destination law: ms per run and forwarded items/s (events around each run)
         laws = {}
         for mode, runs in per_mode.items():
@@ -755,8 +776,11 @@ def run_ours(args):
     # the autotuner picks the persistent kernel's shape on one step of the workload itself
     from paper_2605_30294_gb300 import autotune
 
-    tuned_c1 = autotune.tune(ctx.handle, rafi.RF_POLICY_MICROBENCH, lambda form: step(True), item_bytes=ITEM_BYTES,
-                             ranks=RANKS, n=n, tag="steps on arrival, three laws", reps=1, stream=s)
+    tuned_c1 = autotune.tune(ctx3.handle, rafi.RF_POLICY_MICROBENCH, lambda form: joint(), item_bytes=ITEM_BYTES,
+                             ranks=RANKS, n=len(MODES) * n, tag="three laws in one launch, steps on arrival",
+                             reps=1, stream=s)
+    # the separate launches run in the same shape
+    rafi.rf_set_batched_config(ctx.handle, rafi.RF_POLICY_MICROBENCH, rafi.RF_FORM_PERSISTENT, tuned_c1["shape"])
 
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
@@ -765,11 +789,15 @@ def run_ours(args):
         gpu_id = str(uuid) if str(uuid).startswith("GPU-") else "GPU-" + str(uuid)
 
     for _ in range(args.warmup):
+        joint()
         step(True)
         step(False)
-    fwd, ms, tb, launches, clocks = timed(True, args.steps)
-    laws_batched = timed.laws
+    fwd, ms, tb, launches, clocks = timed("joint", args.steps)
     p_steps = max(3, args.steps // 4)
+    # the same three runs, one persistent launch each
+    sep_steps = max(3, args.steps // 2)
+    s_fwd, s_ms, ts, s_launches, s_clocks = timed(True, sep_steps)
+    laws_batched = timed.laws
     p_fwd, p_ms, tp, p_launches, p_clocks = timed(False, p_steps)
     # the persistent form with the work step as its own pass (no step on arrival)
     step(True, fuse=False)
@@ -780,68 +808,77 @@ def run_ours(args):
     g_fwd, g_ms, _, g_launches, _ = timed("graph", p_steps)
     laws_graph = timed.laws
 
-    # per-round phase rates of the persistent kernel (one extra, untimed step)
-    step(True, round_log=log)
-    lg = log.cpu().numpy().reshape(-1, 7)
-    rows = [r for r in lg if r[0] > 0]
-    rates = phase_rates(rows, ITEM_BYTES)
+    # per-round phase rates of the persistent kernel (one extra, untimed step
+    # of each form)
+    def round_rates(form):
+        log.zero_()
+        step(form, round_log=log)
+        lg = log.cpu().numpy().reshape(-1, 7)
+        return phase_rates([r for r in lg if r[0] > 0], ITEM_BYTES)
+
+    rates = round_rates("joint")
+    rates_sep = round_rates(True)
 
     # end to end through the public call with host buffers (H2D + D2H inside)
-    h_items = torch.from_numpy(items.view(np.int32)).pin_memory()
-    h_ret = torch.zeros((n, 16), dtype=torch.int32).pin_memory()
+    h_items = torch.empty((len(MODES) * n, 16), dtype=torch.int32).pin_memory()
+    h_items.copy_(d_items3)
+    h_ret = torch.zeros((len(MODES) * n, 16), dtype=torch.int32).pin_memory()
 
     def e2e_step():
-        f = 0
-        for mode in MODES:
-            st, cnt, rounds, ff = rafi.rf_c1_run_batched(ctx.handle, h_items.data_ptr(), n, SEED, mode, 1.1, GRID,
-                                                         h_ret.data_ptr(), host_memory=True, stream=s)
-            f += ff
+        st, cnt, rounds, f = rafi.rf_c1_run_batched_runs(ctx3.handle, h_items.data_ptr(), n, SEED, list(MODES), 1.1,
+                                                         GRID, h_ret.data_ptr(), host_memory=True, stream=s)
+        if cnt != [n] * len(MODES):
+            raise RuntimeError(f"joint runs from host buffers: {cnt} of {n} items retired per run")
         return f
 
     e2e_step()
     barrier()
     t0 = time.perf_counter()
     e2e_fwd = 0
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
+    e2e_step_ms = []
     for _ in range(e2e_steps):
-        e2e_fwd += e2e_step()
+        t1 = time.perf_counter()
+        e2e_fwd += e2e_step()  # returns after the stream has drained
+        e2e_step_ms.append((time.perf_counter() - t1) * 1e3)
     barrier()
     e2e_s = time.perf_counter() - t0
 
     # where the end-to-end time goes: one more step with the persistent kernel
     # timed on the device (it writes the retired items straight into the pinned
-    # host buffer), and the host-to-device copy of one run's items timed alone
-    rafi.rf_set_timing(ctx.handle, True)
-    rafi.rf_get_timing(ctx.handle, reset=True)
+    # host buffer), and the host-to-device copy of one step's items timed alone
+    rafi.rf_set_timing(ctx3.handle, True)
+    rafi.rf_get_timing(ctx3.handle, reset=True)
     barrier()
     t0 = time.perf_counter()
     e2e_step()
     barrier()
     one_step_s = time.perf_counter() - t0
-    te = rafi.rf_get_timing(ctx.handle, reset=True)
-    rafi.rf_set_timing(ctx.handle, False)
+    te = rafi.rf_get_timing(ctx3.handle, reset=True)
+    rafi.rf_set_timing(ctx3.handle, False)
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    retired.copy_(h_items.view(n, 16), non_blocking=True)  # first copy: untimed
+    retired.copy_(h_items, non_blocking=True)  # first copy: untimed
     ev[0].record(s)
     for _ in range(3):
-        retired.copy_(h_items.view(n, 16), non_blocking=True)
+        retired.copy_(h_items, non_blocking=True)
     ev[1].record(s)
     torch.cuda.synchronize()
     h2d_ms = ev[0].elapsed_time(ev[1]) / 3
-    run_ms = one_step_s * 1e3 / len(MODES)
+    step_ms = one_step_s * 1e3
     kern_ms = te.roundsMs / max(te.roundsLaunches, 1)
-    e2e_split = {"ms_per_run": run_ms, "h2d_items_ms": h2d_ms,
-                 "h2d_gbs": n * ITEM_BYTES / (h2d_ms * 1e-3) / 1e9,
+    e2e_split = {"ms_per_step": step_ms, "h2d_items_ms": h2d_ms,
+                 "h2d_gbs": len(MODES) * n * ITEM_BYTES / (h2d_ms * 1e-3) / 1e9,
                  "rounds_kernel_ms": kern_ms,
                  "rounds_kernel_ms_device_buffers": tb.roundsMs / max(tb.roundsLaunches, 1),
-                 "rest_ms": run_ms - h2d_ms - kern_ms,
-                 "what": "one run = copy of the items in, seed kernel, persistent kernel writing retired items "
-                         "into the pinned host buffer, read-back of the counts; rest = launches, host calls "
-                         "and synchronisation"}
+                 "rest_ms": step_ms - h2d_ms - kern_ms,
+                 "what": "one step = copy of the three runs' items in, seed kernel, one persistent kernel writing "
+                         "retired items into the pinned host buffer, read-back of the counts; rest = launches, "
+                         "host calls and synchronisation"}
 
     c0 = c0_rays_per_s(torch, rafi, inputs, s)
     ctx.close()
-    del d_items, retired, h_items, h_ret
+    ctx3.close()
+    del d_items, d_items3, retired, h_items, h_ret
     torch.cuda.empty_cache()
     # the oracle's timings (cpu_baseline) run at one GPU only
     cpu_extra = {} if world == 1 else None
@@ -868,12 +905,16 @@ def run_ours(args):
     # exchange), so `fwd` items move 128 * fwd bytes over all timed launches.
     # Also reported: the bytes the kernel actually has to move, the queued
     # items of every round (each read once and written once, to its next
-    # segment or to the retirement sink) plus the seed exchange's n items.
+    # segment or to the retirement sink) plus the seed exchange's items (3 n
+    # per joint launch, n per separate one).
     runs = tb.roundsLaunches
     alg_bytes = 2 * ITEM_BYTES * fwd
     achieved = alg_bytes / (tb.roundsMs * 1e-3) / 1e9 if tb.roundsMs > 0 else 0.0
-    moved_bytes = 2 * ITEM_BYTES * (2 * runs * n + fwd)
+    moved_bytes = 2 * ITEM_BYTES * (2 * runs * len(MODES) * n + fwd)
     moved = moved_bytes / (tb.roundsMs * 1e-3) / 1e9 if tb.roundsMs > 0 else 0.0
+    s_runs = ts.roundsLaunches
+    s_ach = 2 * ITEM_BYTES * s_fwd / (ts.roundsMs * 1e-3) / 1e9 if ts.roundsMs > 0 else 0.0
+    s_moved = 2 * ITEM_BYTES * (2 * s_runs * n + s_fwd) / (ts.roundsMs * 1e-3) / 1e9 if ts.roundsMs > 0 else 0.0
     p_bytes = tp.scatterItems * 2 * ITEM_BYTES
     p_ach = p_bytes / (tp.scatterMs * 1e-3) / 1e9 if tp.scatterMs > 0 else 0.0
     p_ach_l = (tp.scatterItemsLarge * 2 * ITEM_BYTES / (tp.scatterMsLarge * 1e-3) / 1e9
@@ -889,7 +930,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "items": n, "item_bytes": ITEM_BYTES, "ranks": RANKS,
-                   "form": "batched: all rounds in one persistent cooperative kernel per run, each step applied on arrival",
+                   "form": "batched: the three runs (laws) of a step in one persistent cooperative kernel "
+                           "(rf_c1_run_batched_runs), all their rounds inside it, each step applied on arrival; "
+                           "each run's queues and retirements are those of its own launch",
                    "shape": {"threads": tuned_c1["threads"], "items_per_thread": tuned_c1["items_per_thread"],
                              "ctas_per_sm": tuned_c1["ctas_per_sm"], "chosen_by": "autotune"},
                    "parallelism": "replicas" if world > 1 else "single GPU",
@@ -908,8 +951,16 @@ def run_ours(args):
                                   "scatter_frac_ge_2^20": rates.get("scatter_gbs_ge_2^20", 0.0) / peak,
                                   "round_frac_ge_2^20": rates.get("round_gbs_ge_2^20", 0.0) / peak,
                                   "fwd_frac_ge_2^20": rates.get("fwd_gbs_ge_2^20", 0.0) / peak},
-        "per_law": laws_batched,
         "autotune": tuned_c1,
+        "separate_launches": {
+            "value": s_fwd / (s_ms / 1e3), "ms_per_step": s_ms / sep_steps, "steps": sep_steps,
+            "per_law": laws_batched, "gpu_launches": s_launches, "clocks": s_clocks,
+            "form": "the same persistent kernel, one launch per run (rf_c1_run_batched, steps on arrival)",
+            "roofline": {"achieved": s_ach, "frac": s_ach / peak, "launches": s_runs,
+                         "ms_per_launch": ts.roundsMs / max(s_runs, 1),
+                         "frac_rounds_ge_2^20": rates_sep.get("fwd_gbs_ge_2^20", 0.0) / peak,
+                         "moved_frac": s_moved / peak},
+            "phases_from_round_log": rates_sep},
         "batched_step_in_place": {
             "value": u_fwd / (u_ms / 1e3), "ms_per_step": u_ms / p_steps, "steps": p_steps, "per_law": laws_in_place,
             "form": "persistent kernel; each round steps every item in its queue slot, then scatters",
@@ -929,7 +980,10 @@ def run_ours(args):
                   "gpu_launches": p_launches, "clocks": p_clocks},
         "e2e": {"value": e2e_fwd / e2e_s, "unit": "items/s",
                 "h2d_bytes_per_step": len(MODES) * n * ITEM_BYTES,
-                "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8), "split": e2e_split},
+                "d2h_bytes_per_step": len(MODES) * (n * ITEM_BYTES + 8), "steps": e2e_steps,
+                "step_ms": [round(x, 3) for x in e2e_step_ms], "split": e2e_split,
+                "note": "the host link of the shared GPU hosts carries other jobs' copies too: step_ms shows "
+                        "the spread"},
         "rays_per_s": {"value": c0["tma_graph"]["value"],
                        "workload": "64^3 blob volume, 2x2x2 ranks, 128x128 rays, 1 spp",
                        "ms_per_frame": c0["tma_graph"]["ms_per_frame"],
@@ -956,7 +1010,8 @@ def run_section(args):
     device, each workload launched once, no warm-up), printing one JSON line of
     its own (not the bench line):
       c0: the marching workload, one frame with quad bricks, one with TMA-staged bricks;
-      c1: the microbenchmark, one rf_c1_run_batched call (one persistent launch);
+      c1: the microbenchmark, one rf_c1_run_batched call (one persistent launch),
+          or with --joint one rf_c1_run_batched_runs call of the three laws;
       c2: streamlines, 512^3 field in 4x4x4 bricks, 2^18 seeds, until brick exit;
       c3: EA renderer at its configured size, one forward and one adjoint render;
       c4: delta tracking, 512^3 noise in 4x4x4 bricks, one 512x512 view at 16 spp."""
@@ -973,21 +1028,29 @@ def run_section(args):
         # one persistent-kernel launch of the microbenchmark (steps on arrival),
         # one destination law, no warm-up: the launch a profiler captures
         n = args.items
+        k = len(MODES) if args.joint else 1
         items = inputs.c1_items(n, seed=SEED)
-        d_items = torch.from_numpy(items.view(np.int32)).cuda()
-        retired = torch.zeros((n, 16), dtype=torch.int32, device="cuda")
+        d_items = torch.cat([torch.from_numpy(items.view(np.int32)).cuda()] * k)
+        retired = torch.zeros((k * n, 16), dtype=torch.int32, device="cuda")
         log = torch.zeros(7 * LOG_CAP, dtype=torch.int64, device="cuda")
-        with rafi.Context(RANKS, ITEM_BYTES, n) as ctx:
+        with rafi.Context(RANKS, ITEM_BYTES, k * n) as ctx:
             e0.record(s)
-            st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, d_items, n, SEED, args.law, 1.1, GRID, retired,
-                                                          stream=s, round_log=log, round_log_cap=LOG_CAP)
+            if args.joint:
+                st, cnt, rounds, fwd = rafi.rf_c1_run_batched_runs(ctx.handle, d_items, n, SEED, list(MODES), 1.1,
+                                                                   GRID, retired, stream=s, round_log=log,
+                                                                   round_log_cap=LOG_CAP)
+            else:
+                st, cnt, rounds, fwd = rafi.rf_c1_run_batched(ctx.handle, d_items, n, SEED, args.law, 1.1, GRID,
+                                                              retired, stream=s, round_log=log, round_log_cap=LOG_CAP)
             e1.record(s)
             torch.cuda.synchronize()
         lg = log.cpu().numpy().reshape(-1, 7)
         rows = [r for r in lg if r[0] > 0]
-        out.update(workload=f"microbenchmark, {n} x 64 B items, 64 ranks, law {LAW_NAMES[args.law]}, one "
-                            f"rf_c1_run_batched call", items=n, ms=e0.elapsed_time(e1), rounds=rounds, forwarded=fwd,
-                   retired=cnt, phases=phase_rates(rows, ITEM_BYTES))
+        what = ("the three laws in one rf_c1_run_batched_runs call" if args.joint else
+                f"law {LAW_NAMES[args.law]}, one rf_c1_run_batched call")
+        out.update(workload=f"microbenchmark, {n} x 64 B items per run, 64 ranks, {what}", items=k * n,
+                   ms=e0.elapsed_time(e1), rounds=rounds, forwarded=fwd, retired=cnt,
+                   phases=phase_rates(rows, ITEM_BYTES))
         if args.round_log:
             with open(args.round_log, "w") as f:
                 json.dump({"columns": ["t_start", "t_count_end", "t_barrier1", "t_scatter_end", "t_barrier2",
@@ -1095,6 +1158,7 @@ def main():
                     help="run one workload alone at a profiling size and print its own JSON line (c1: one "
                          "persistent-kernel launch of the microbenchmark at --items; c2-c4: a host loop)")
     ap.add_argument("--law", type=int, default=0, choices=list(MODES), help="destination law of --section c1")
+    ap.add_argument("--joint", action="store_true", help="--section c1: the three laws in one launch")
     ap.add_argument("--round-log", default=None, help="--section c1: write the kernel's round log to this JSON file")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -395,6 +395,32 @@ rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t
                             uint64_t *rounds, uint64_t *forwarded, unsigned long long *roundLog,
                             uint32_t roundLogCap);
 
+/* Several independent runs of the microbenchmark (1 to 4) in one persistent
+ * launch, steps on arrival: the batched form over several seed sets.  Run k
+ * holds items [k n, (k + 1) n) of items (numRuns x n x 64 bytes, device or,
+ * with hostMemory != 0, host memory); its item i starts at rank i mod
+ * numRanks, as in a run of its own, and hops under modes[k] (host array of
+ * numRuns laws; gx, gy, gz as rf_c1_run when a run is RF_C1_NBR6).  The runs
+ * share the ranks' queues: a round's queue of rank r holds every run's items
+ * bound for r, and the stable partition of Sec. 4.2.1, restricted to one run,
+ * is that run's own partition, so each run's round queues and retirement
+ * order are exactly those of rf_c1_run_batched on it alone.  Each run has a
+ * retirement destination of its own: run k's retired items land, stably, in
+ * retired slots [k n, (k + 1) n) (numRuns x n x 64 bytes; page-locked host
+ * memory receives them during the run, other host memory after it).
+ * Results (host): retiredCountsOut[k] and roundsOut[k] (nullable) per run,
+ * *forwarded (nullable) the deliveries of all runs' work rounds.  The
+ * context's capacity must hold numRuns x n items (below 2^31).  A launch that
+ * stops at maxRounds (RF_ERR_MAX_ROUNDS) leaves a queue that no later call
+ * resumes.  roundLog as rf_c1_run_batched, over the joint rounds.  RF_ERR_ARG
+ * for 0 or more than 4 runs, a bad mode, a NULL array or a size above the
+ * capacity; RF_ERR_TIMEOUT if a bounded wait gave up. */
+rf_status rf_c1_run_batched_runs(rf_ctx *ctx, const void *items, uint64_t n, int32_t numRuns, uint32_t seed,
+                                 const int32_t *modes, double zipfS, int32_t gx, int32_t gy, int32_t gz,
+                                 void *retired, uint64_t *retiredCountsOut, int32_t hostMemory, uint32_t maxRounds,
+                                 void *stream, uint64_t *roundsOut, uint64_t *forwarded,
+                                 unsigned long long *roundLog, uint32_t roundLogCap);
+
 /* --- absorption marching through bricks (48-byte rays) ------------------- */
 
 /* Cut an N^3 float volume (device, x fastest) into (N/B)^3 bricks of

@@ -214,13 +214,29 @@ struct C1Work {
     const uint32_t *zipfThr;
     uint32_t seed;
     int32_t mode, gx, gy, gz, R;
+    // A launch of several independent runs (runs > 1): run k's law in bits
+    // 2k, 2k + 1 of laws, the run in the high bits of each destination word.
+    int32_t runs = 1;
+    uint32_t laws = 0;
+    int32_t lgx = -1, lgy = -1;  // log2 of gx, gy when gx, gy and gz are powers of two (else -1)
 
+    __host__ __device__ int32_t lawOf(uint32_t run) const
+    {
+        return runs > 1 ? (int32_t)((laws >> (2u * run)) & 3u) : mode;
+    }
+    __host__ __device__ bool anyLaw(int32_t m) const
+    {
+        for (int32_t k = 0; k < runs; ++k)
+            if (lawOf((uint32_t)k) == m) return true;
+        return false;
+    }
     // shared memory: the Zipf thresholds (up to 256 ranks followed by a guide of
     // 256 byte entries: guide[b] = the destination of r1 = b 2^24, the first
-    // threshold above it), or (up to 256 ranks) the torus neighbour table
-    // [rank][6] in bytes; small enough to keep three CTAs per SM
-    __host__ __device__ bool nbrTable() const { return mode == RF_C1_NBR6 && R <= 256; }
-    __host__ __device__ bool zipfGuide() const { return mode == RF_C1_ZIPF && R <= 256; }
+    // threshold above it), or (up to 256 ranks, one run) the torus neighbour
+    // table [rank][6] in bytes; small enough to keep three CTAs per SM (a launch
+    // of several runs computes torus neighbours instead of keeping the table)
+    __host__ __device__ bool nbrTable() const { return runs <= 1 && mode == RF_C1_NBR6 && R <= 256; }
+    __host__ __device__ bool zipfGuide() const { return anyLaw(RF_C1_ZIPF) && R <= 256; }
     __host__ __device__ uint32_t thrBytes() const { return ((uint32_t)(R > 1 ? R - 1 : 1) * 4u + 15u) / 16u * 16u; }
     __host__ __device__ uint32_t smemBytes() const
     {
@@ -229,7 +245,7 @@ struct C1Work {
     }
     __device__ void load_smem(void *s) const
     {
-        if (mode == RF_C1_ZIPF) {
+        if (anyLaw(RF_C1_ZIPF)) {
             uint32_t *t = static_cast<uint32_t *>(s);
             for (int e = threadIdx.x; e < R - 1; e += blockDim.x) t[e] = zipfThr[e];
             if (zipfGuide()) {
@@ -244,26 +260,40 @@ struct C1Work {
                 t[e] = (uint8_t)torus_neighbour(e / 6, e % 6, gx, gy, gz);
         }
     }
-    __device__ int32_t step(uint4 (&w)[4], int32_t rank, uint32_t round, const void *s) const
+    // word: the item's destination word (its current rank; with several runs,
+    // the run in the high bits); returns the next one (same run) or -1
+    __device__ int32_t step(uint4 (&w)[4], int32_t word, uint32_t round, const void *s) const
     {
         const uint4 r = philox4x32_10(make_uint4(w[0].x, w[0].y, w[3].w, round), make_uint2(seed, 1u));
         if (r.x < kRetire) return -1;
+        const uint32_t run = (uint32_t)word >> 16;
+        const int32_t rank = word & 0xFFFF;
+        const int32_t law = lawOf(run);
         int32_t d;
-        if (nbrTable()) {
+        if (law == RF_C1_NBR6 && nbrTable()) {
             d = (int32_t)static_cast<const uint8_t *>(s)[rank * 6 + (int32_t)(((unsigned long long)r.y * 6u) >> 32)];
-        } else if (zipfGuide()) {
+        } else if (law == RF_C1_NBR6 && lgx >= 0) {
+            // power-of-two torus: coordinates by shifts and masks
+            const int32_t k = (int32_t)(((unsigned long long)r.y * 6u) >> 32);
+            int32_t x = rank & (gx - 1), y = (rank >> lgx) & (gy - 1), z = rank >> (lgx + lgy);
+            const int32_t dir = (k & 1) ? -1 : 1;
+            if (k < 2) x = (x + dir) & (gx - 1);
+            else if (k < 4) y = (y + dir) & (gy - 1);
+            else z = (z + dir) & (gz - 1);
+            d = x | (y << lgx) | (z << (lgx + lgy));
+        } else if (law == RF_C1_ZIPF && R <= 256) {  // the guide is loaded whenever a run is Zipf
             // start at the destination of the bucket's lowest r1 and walk up the
             // (ascending) thresholds: the first k with r1 < thr[k], or R - 1
             const uint32_t *t = static_cast<const uint32_t *>(s);
             d = static_cast<const uint8_t *>(s)[thrBytes() + (r.y >> 24)];
             while (d < R - 1 && r.y >= t[d]) ++d;
         } else {
-            d = choose_dest(mode, rank, r.y, R, static_cast<const uint32_t *>(s), gx, gy, gz);
+            d = choose_dest(law, rank, r.y, R, static_cast<const uint32_t *>(s), gx, gy, gz);
         }
         w[3].z = (uint32_t)d;
         w[3].y ^= r.z;
         w[3].w += 1u;
-        return d;
+        return d | (int32_t)(run << 16);
     }
     __device__ void retire(const uint4 (&)[4]) const {}
 };
@@ -298,6 +328,16 @@ __global__ void __launch_bounds__(kBlock) seed_dest_kernel(uint32_t n, rf_device
     for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock)
         q.dest[i] = (int32_t)(i % (uint32_t)q.numRanks);
     if (blockIdx.x == 0 && threadIdx.x == 0) *q.outCount = n;
+}
+
+// Seed for several runs' items copied (or read in place) as one array of
+// numRuns x n: item i of run k, at slot k n + i, starts at rank i mod R, with
+// the run in the high bits of its destination word.
+__global__ void __launch_bounds__(kBlock) seed_dest_runs_kernel(uint32_t total, uint32_t n, rf_device_queues q)
+{
+    for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < total; i += gridDim.x * kBlock)
+        q.dest[i] = (int32_t)(((i / n) << 16) | ((i % n) % (uint32_t)q.numRanks));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *q.outCount = total;
 }
 
 __global__ void reserve_kernel(unsigned long long *counter, unsigned long long n, unsigned long long *base)
@@ -646,6 +686,117 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
     if (forwarded) *forwarded = res[1];
     if (ctx->host->numActive) {
         set_error("rf_c1_run_batched: %llu items still active after %u rounds",
+                  (unsigned long long)ctx->host->numActive, maxRounds);
+        return RF_ERR_MAX_ROUNDS;
+    }
+    return RF_OK;
+}
+
+// Several independent runs of the microbenchmark in one persistent launch.
+// Run k holds items [k n, (k + 1) n) of `items`, all of them starting at rank
+// i mod R as in a run of its own, and moves under its own destination law
+// modes[k]; its retired items land, in its own order, in retired slots
+// [k n, (k + 1) n).  The runs share the ranks' queues: a round's queue of
+// rank r holds the items of every run bound for r, and a stable partition of
+// the whole queue, restricted to one run, is that run's own stable partition,
+// so every run's queues and retirements equal those of its own launch.
+extern "C" rf_status rf_c1_run_batched_runs(rf_ctx *ctx, const void *items, uint64_t n, int32_t numRuns,
+                                            uint32_t seed, const int32_t *modes, double zipfS, int32_t gx,
+                                            int32_t gy, int32_t gz, void *retired, uint64_t *retiredCountsOut,
+                                            int32_t hostMemory, uint32_t maxRounds, void *stream,
+                                            uint64_t *roundsOut, uint64_t *forwarded, unsigned long long *roundLog,
+                                            uint32_t roundLogCap)
+{
+    using namespace rfi;
+    if (rf_status st = check_c1(ctx, "rf_c1_run_batched_runs")) return st;
+    if (numRuns < 1 || numRuns > kMaxRuns || !modes || !retiredCountsOut) {
+        set_error("rf_c1_run_batched_runs: %d runs (1 to %d) or a NULL mode / count array", numRuns, kMaxRuns);
+        return RF_ERR_ARG;
+    }
+    const unsigned long long total = (unsigned long long)numRuns * n;
+    if (total > ctx->capacity || total >= (1ull << 31) || (n && (!items || !retired))) {
+        set_error("rf_c1_run_batched_runs: %d x %llu items above capacity %llu or 2^31, or a NULL buffer", numRuns,
+                  (unsigned long long)n, (unsigned long long)ctx->capacity);
+        return RF_ERR_ARG;
+    }
+    bool anyZipf = false, anyTorus = false;
+    uint32_t laws = 0;
+    for (int32_t k = 0; k < numRuns; ++k) {
+        if (modes[k] < RF_C1_UNIFORM || modes[k] > RF_C1_NBR6) {
+            set_error("rf_c1_run_batched_runs: run %d has bad mode %d", k, modes[k]);
+            return RF_ERR_ARG;
+        }
+        laws |= (uint32_t)modes[k] << (2 * k);
+        anyZipf |= modes[k] == RF_C1_ZIPF;
+        anyTorus |= modes[k] == RF_C1_NBR6;
+    }
+    if (anyTorus && (gx < 1 || gy < 1 || gz < 1 || gx * gy * gz != ctx->numRanks)) {
+        set_error("rf_c1_run_batched_runs: torus %dx%dx%d does not have %d ranks", gx, gy, gz, ctx->numRanks);
+        return RF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (anyZipf)
+        if (rf_status st = ensure_zipf(ctx, zipfS)) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void *devRetired = retired;
+    bool direct = false;
+    if (hostMemory) {
+        // as rf_c1_run_batched: page-locked host memory receives the retired
+        // items from the kernel, any other host buffer through a staging copy
+        cudaPointerAttributes pa;
+        if (n && cudaPointerGetAttributes(&pa, retired) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            devRetired = pa.devicePointer;
+            direct = true;
+        } else {
+            (void)cudaGetLastError();
+            if (rf_status st = ensure_staging(ctx)) return st;
+            devRetired = ctx->staging;
+        }
+    }
+    RF_CUDA(cudaMemsetAsync(ctx->stagingCount, 0, sizeof(unsigned long long), s));
+    rf_device_queues q;
+    rf_get_device_queues(ctx, &q);
+    // the seeded items are read where the caller keeps them when they are
+    // 16-byte aligned device memory, else copied into the out-queue first
+    const bool inPlace = !hostMemory && ((uintptr_t)items & 15u) == 0;
+    if (total && !inPlace)
+        RF_CUDA(cudaMemcpyAsync(q.out, items, (size_t)total * 64u,
+                                hostMemory ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    seed_dest_runs_kernel<<<grid_for(ctx, total, 8), kBlock, 0, s>>>((uint32_t)total, n ? (uint32_t)n : 1u, q);
+    RF_LAUNCHED("seed_dest_runs_kernel");
+
+    C1Work w;
+    w.zipfThr = ctx->zipfThr;
+    w.seed = seed;
+    w.mode = modes[0];
+    w.gx = gx;
+    w.gy = gy;
+    w.gz = gz;
+    w.R = ctx->numRanks;
+    w.runs = numRuns;
+    w.laws = laws;
+    auto lg2 = [](int32_t v) { return (v > 0 && (v & (v - 1)) == 0) ? __builtin_ctz((unsigned)v) : -1; };
+    if (anyTorus && lg2(gx) >= 0 && lg2(gy) >= 0 && lg2(gz) >= 0) {
+        w.lgx = lg2(gx);
+        w.lgy = lg2(gy);
+    }
+    unsigned long long res[4], runRes[2 * kMaxRuns];
+    rf_status st = C1Shapes::launch(ctx->batchedShape[RF_POLICY_MICROBENCH], ctx, w, maxRounds, s, roundLog,
+                                    roundLogCap, static_cast<uint4 *>(devRetired), total, ctx->stagingCount, res,
+                                    true, true, inPlace ? items : nullptr, (uint32_t)numRuns,
+                                    (unsigned long long)n, runRes);
+    if (st != RF_OK) return st;
+    if (hostMemory && !direct && total)
+        RF_CUDA(cudaMemcpyAsync(retired, ctx->staging, (size_t)total * 64u, cudaMemcpyDeviceToHost, s));
+    RF_CUDA(cudaStreamSynchronize(s));
+    for (int32_t k = 0; k < numRuns; ++k) {
+        retiredCountsOut[k] = runRes[kMaxRuns + k];
+        if (roundsOut) roundsOut[k] = runRes[k];
+    }
+    if (forwarded) *forwarded = res[1];
+    if (ctx->host->numActive) {
+        set_error("rf_c1_run_batched_runs: %llu items still active after %u rounds",
                   (unsigned long long)ctx->host->numActive, maxRounds);
         return RF_ERR_MAX_ROUNDS;
     }

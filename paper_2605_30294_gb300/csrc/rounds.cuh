@@ -45,6 +45,19 @@
 namespace rfi {
 
 constexpr int kSyncGroups = 16;  // runs of consecutive CTAs whose destination counts are summed per round
+// Independent runs one launch may carry (policies with kAppendRetired and
+// steps on arrival): their items share the rank digits, each run has a
+// retirement digit and a sink of its own.
+constexpr int kMaxRuns = 4;
+// a.result: {rounds, forwarded, status, retired}, then per run its rounds,
+// then per run its retired count
+constexpr int kResultWords = 4 + 2 * kMaxRuns;
+
+// A destination word names a digit in its low 16 bits; the run an item
+// belongs to rides in the high bits (0 for a launch of one run).  -1 (no
+// destination) maps to digit 0xFFFF, above every valid digit.
+__host__ __device__ __forceinline__ uint32_t digit_of(int32_t w) { return (uint32_t)w & 0xFFFFu; }
+__host__ __device__ __forceinline__ uint32_t run_of(int32_t w) { return (uint32_t)w >> 16; }
 
 struct GridSync {
     unsigned int count;    // arrivals at grid barriers so far
@@ -63,7 +76,7 @@ struct RoundsArgs {
     uint32_t *grpTot;          // 3 x kSyncGroups rows (stride as tot): per-group destination totals
                                // (both tables: one set per iteration modulo 3, zero when the launch starts)
     GridSync *sync;
-    unsigned long long *result;  // {rounds, forwarded, status, retired}
+    unsigned long long *result;  // kResultWords: {rounds, forwarded, status, retired}, per-run rounds, per-run retired
     unsigned long long *numActiveOut;  // items still active when the kernel returns
     unsigned long long *roundLog;  // nullable: per round {t_start, t_work_end, t_barrier1, t_scatter_end, t_barrier2, n_in, n_next}
     uint4 *retiredOut;         // retirement sink (policies with kAppendRetired)
@@ -80,6 +93,8 @@ struct RoundsArgs {
     uint32_t roundLogCap;
     uint32_t fuseStep;  // apply steps on arrival (policies with kFuseStep)
     int32_t numRanks;
+    uint32_t numRuns;   // independent runs (1..kMaxRuns); retirement digit R + k is run k's
+    uint32_t runCap;    // sink slots per run: run k retires into [k runCap, (k + 1) runCap)
 };
 
 constexpr int kRoundsBlock = 256;  // threads per CTA of a policy's default shape
@@ -393,7 +408,7 @@ __device__ __forceinline__ void store_step(uint4 *s, uint32_t j, const uint4 (&w
 }
 
 struct RoundsLayout {
-    uint32_t items, dests, wc, cnt, start, base, tot, off, slotSrc, slotDst, tmp, flag, bar, work, total;
+    uint32_t items, dests, wc, cnt, start, base, tot, off, slotSrc, slotDst, tmp, flag, bar, ret, work, total;
 };
 
 __host__ __device__ inline uint32_t rounds_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -412,15 +427,19 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
     L.dests = o;   o = rounds_align(o + 2u * (tile + 4u) * 4u, 16);
     L.wc = o;      o = rounds_align(o + warps * D * 4u, 16);
     L.cnt = o;     o = rounds_align(o + D * 4u, 16);
+    // The CTA's range counts (tot) live from a round's start until its count
+    // row is written out, a tile's counts (cnt) from the scatter's first
+    // ranking until the round ends: one array holds both.
+    L.tot = L.cnt;
     L.start = o;   o = rounds_align(o + D * 4u, 16);
     L.base = o;    o = rounds_align(o + D * 4u, 16);
-    L.tot = o;     o = rounds_align(o + D * 4u, 16);
     L.off = o;     o = rounds_align(o + (D + 1) * 4u, 16);
     L.slotSrc = o; o = rounds_align(o + tile * 2u, 16);
     L.slotDst = o; o = rounds_align(o + tile * 4u, 16);
     L.tmp = o;     o = rounds_align(o + (warps + 1) * 4u, 16);
     L.flag = o;    o = rounds_align(o + 4u, 16);
     L.bar = o;     o = rounds_align(o + 16u, 16);
+    L.ret = o;     o = rounds_align(o + kMaxRuns * 4u, 16);
     L.work = o;    o = rounds_align(o + workBytes, 16);
     L.total = o;
     return L;
@@ -442,7 +461,9 @@ __host__ __device__ inline RoundsLayout rounds_layout(uint32_t itemBytes, int D,
 //   uint32_t smemBytes() const;           its own shared memory
 //   void load_smem(void *s) const;        fill it (all threads; a barrier follows)
 //   int32_t step(uint4 (&w)[V], int32_t rank, uint32_t round, const void *s) const;
-//       advances one item: returns the destination rank (w updated) or -1 to retire
+//       advances one item: returns the destination rank (w updated) or -1 to retire;
+//       in a launch of several runs `rank` is the item's destination word (run in
+//       the high bits, see digit_of) and the returned rank carries the same run
 //   void retire(const uint4 (&w)[V]) const;  (used when !kAppendRetired)
 template <class W>
 __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(RoundsArgs a, W work)
@@ -459,7 +480,8 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
     static_assert((W::kStepReadMask & ((1u << V) - 1u)) != 0u, "a step reads part of its item");
     extern __shared__ __align__(128) unsigned char smem[];
     const int R = a.numRanks;
-    const int D = R + (W::kAppendRetired ? 1 : 0);  // digits: ranks (+ retirement)
+    const int K = W::kAppendRetired ? (int)a.numRuns : 1;  // independent runs in the launch
+    const int D = R + (W::kAppendRetired ? K : 0);  // digits: ranks (+ one retirement digit per run)
     const int Dp = rounds_row_stride(D);
     const RoundsLayout L = rounds_layout(kItemBytes, D, work.smemBytes(), kTile, kWarps);
     uint4 *sBuf = reinterpret_cast<uint4 *>(smem + L.items);  // two tiles of kTileVecs
@@ -475,6 +497,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
     uint32_t *slotDst = reinterpret_cast<uint32_t *>(smem + L.slotDst);
     uint32_t *tmp = reinterpret_cast<uint32_t *>(smem + L.tmp);
     unsigned int *sFlag = reinterpret_cast<unsigned int *>(smem + L.flag);
+    uint32_t *sRet = reinterpret_cast<uint32_t *>(smem + L.ret);  // per run: items retired so far
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);  // bar[0], bar[1]: one per tile buffer
     void *sWork = smem + L.work;
 
@@ -491,6 +514,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         mbar_init(&bar[1], 1);
         fence_proxy_async_smem();
     }
+    if (tid < kMaxRuns) sRet[tid] = 0u;
     work.load_smem(sWork);
     __syncthreads();
 
@@ -581,8 +605,9 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
     // bound for a rank when doFuse (its new destination replaces the staged
     // one); fills dCnt, dStart (the tile's slots grouped by digit) and
     // slotSrc / slotDst (position = dBase[d] + rank within d; the retirement
-    // flag for digit R).  With ownBases the tile is a whole round on its own:
-    // dBase[d] = dStart[d] for ranks and the retired count so far for R.
+    // flag for the retirement digits R + k).  With ownBases the tile is a whole
+    // round on its own: dBase[d] = dStart[d] for ranks, and for run k's
+    // retirement digit its sink base k runCap plus its retired count so far.
     // Returns the number of valid items.  All threads; ends with a barrier.
     // carryPrev: first add the previous tile's counts (still in dCnt) to dBase.
     // First half (needs no other CTA): per-warp ranks (myD, myR, wc) and the
@@ -592,7 +617,8 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
             const uint32_t idx = (uint32_t)(warp * 32 * kK + k * 32 + lane);
-            const int32_t d = idx < cnt ? dts[idx] : -1;
+            const int32_t dw = idx < cnt ? dts[idx] : -1;  // destination word (digit and run)
+            const int32_t d = (int32_t)digit_of(dw);
             const bool valid = (uint32_t)d < (uint32_t)D;
             const int key = valid ? d : D;
             const unsigned peers = peers_of(key, nbits);
@@ -610,11 +636,11 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                 uint4 w[V];
                 if constexpr (W::kAppendRetired) load_step<W>(sItems, idx, w);
                 else load_item_rot<V>(sItems, idx, w);  // retire() takes the whole item
-                int32_t d2 = work.step(w, d, qs, sWork);
+                int32_t d2 = work.step(w, dw, qs, sWork);
                 if (d2 >= 0) {
                     store_step<W>(sItems, idx, w);
                 } else if (W::kAppendRetired) {
-                    d2 = R;
+                    d2 = R + (int32_t)run_of(dw);  // the run's retirement digit
                 } else {
                     work.retire(w);
                 }
@@ -640,7 +666,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         const uint32_t nValid = rounds_block_scan<kB>(dStart, D, tmp);
         if (ownBases) {
             for (int e = tid; e < D; e += kB)
-                dBase[e] = (W::kAppendRetired && e == R) ? (uint32_t)retiredSoFar : dStart[e];
+                dBase[e] = (W::kAppendRetired && e >= R) ? (uint32_t)(e - R) * a.runCap + sRet[e - R] : dStart[e];
             __syncthreads();
         }
 #pragma unroll
@@ -650,7 +676,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                 const uint32_t within = wc[warp * D + d] + myR[k];
                 const uint32_t slot = dStart[d] + within;
                 slotSrc[slot] = (uint16_t)(warp * 32 * kK + k * 32 + lane);
-                slotDst[slot] = (dBase[d] + within) | (W::kAppendRetired && d == R ? kRetFlag : 0u);
+                slotDst[slot] = (dBase[d] + within) | (W::kAppendRetired && d >= R ? kRetFlag : 0u);
             }
         }
         __syncthreads();
@@ -745,7 +771,15 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                 int32_t *dA = sDst + A * (kTile + 4u), *dB = sDst + (A ^ 1u) * (kTile + 4u);
                 const uint32_t nValid = rank_tile(iA, dA, n, true, round + 1u, true, false);
                 const uint32_t nNext = W::kAppendRetired ? dStart[R] : nValid;
-                const uint32_t retiredNow = W::kAppendRetired ? dCnt[R] : 0u;
+                uint32_t retiredNow = 0u;
+                if (W::kAppendRetired) {
+                    for (int k = 0; k < K; ++k) retiredNow += dCnt[R + k];
+                    // (sRet is next read by the following round's ranking, after barriers)
+                    if (tid < K && dCnt[R + tid]) {
+                        sRet[tid] += dCnt[R + tid];
+                        if (c == 0) a.result[4 + tid] = round + 1u;  // the run's last round so far
+                    }
+                }
                 if (lr) a.roundLog[7 * round + 1] = a.roundLog[7 * round + 2] = globaltimer();
                 for (uint32_t slot = tid; slot < nValid; slot += kB) {
                     const uint32_t dst = slotDst[slot];
@@ -946,8 +980,10 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                     const uint32_t i = lo + 4u * (v0 + (uint32_t)u * kB + tid);
                     const int32_t e4[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        if (i + m < hi && (uint32_t)e4[m] < (uint32_t)D) atomicAdd(&wc[warp * D + e4[m]], 1u);
+                    for (int m = 0; m < 4; ++m) {
+                        const uint32_t dg = digit_of(e4[m]);
+                        if (i + m < hi && dg < (uint32_t)D) atomicAdd(&wc[warp * D + dg], 1u);
+                    }
                 }
             }
             __syncthreads();
@@ -1051,9 +1087,17 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                 __syncthreads();
             }
         }
-        const uint32_t retiredNow = W::kAppendRetired ? dStart[R] : 0u;
+        uint32_t retiredNow = 0u;
+        if (W::kAppendRetired)
+            for (int k = 0; k < K; ++k) retiredNow += dStart[R + k];
         const uint32_t nNext = rounds_block_scan<kB>(dStart, R, tmp);  // ranks only
-        if (W::kAppendRetired && tid == 0) dStart[R] = (uint32_t)retiredSoFar;
+        if (W::kAppendRetired && tid < K) {
+            // run tid's retirement digit: its sink base, then its running count
+            const uint32_t rn = dStart[R + tid];
+            dStart[R + tid] = (uint32_t)tid * a.runCap + sRet[tid];
+            sRet[tid] += rn;
+            if (c == 0 && rn) a.result[4 + tid] = round + 1u;  // the run's last round so far
+        }
         __syncthreads();
         for (int e = tid; e < D; e += kB) dBase[e] += dStart[e];
         // clear the count tables of iteration it + 2 (last read in phase 2 of
@@ -1117,10 +1161,11 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                     if (kFuse && fuse && part == 0u) {
                         const int32_t d2 = dts[src];
                         nxtDest[dst] = d2;
-                        if (push && (uint32_t)d2 < (uint32_t)D) {
+                        const uint32_t dg = digit_of(d2);
+                        if (push && dg < (uint32_t)D) {
                             const uint32_t oc = ((uint32_t)G * ((dst & ~15u) + 1u) - 1u) / nNext;
-                            atomicAdd(&totNext[(size_t)oc * Dp + d2], 1u);
-                            atomicAdd(&grpNext[(size_t)(oc / (uint32_t)grpSize) * Dp + d2], 1u);
+                            atomicAdd(&totNext[(size_t)oc * Dp + dg], 1u);
+                            atomicAdd(&grpNext[(size_t)(oc / (uint32_t)grpSize) * Dp + dg], 1u);
                         }
                     }
                 }
@@ -1162,6 +1207,7 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
         a.result[1] = forwarded;
         a.result[2] = failed ? RF_DEV_TIMEOUT : 0u;
         a.result[3] = retiredSoFar;
+        for (int k = 0; k < K; ++k) a.result[4 + kMaxRuns + k] = sRet[k];
         if (a.retiredCountOut) *a.retiredCountOut = retiredSoFar;
         *a.numActiveOut = failed ? 0ull : n;
     }
@@ -1171,11 +1217,17 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
 // queues, starting from its current incoming queue, or (seeded) from its
 // out-queue with the items' first ranks as destinations.  res (host)
 // receives {rounds, forwarded, status, retired}.  Waits for the stream.
+// numRuns > 1 (seeded, steps on arrival, policies with kAppendRetired): the
+// seeded items belong to that many independent runs, named by the high bits
+// of their destination words; run k retires into sink slots
+// [k runCap, (k + 1) runCap).  runOut (host, nullable, 2 kMaxRuns words)
+// receives each run's rounds, then each run's retired count.
 template <class W>
 rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStream_t s,
                         unsigned long long *roundLog, uint32_t roundLogCap, uint4 *retiredOut,
                         unsigned long long retiredCap, unsigned long long *retiredCountOut, unsigned long long res[4],
-                        bool stepOnArrival = false, bool seeded = false, const void *seedItems = nullptr)
+                        bool stepOnArrival = false, bool seeded = false, const void *seedItems = nullptr,
+                        uint32_t numRuns = 1, unsigned long long runCap = 0, unsigned long long *runOut = nullptr)
 {
     if ((seeded || stepOnArrival) && !W::kFuseStep) {
         set_error("persistent rounds: the policy does not step on arrival");
@@ -1185,6 +1237,13 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         set_error("persistent rounds: a seeded start needs steps on arrival");
         return RF_ERR_ARG;
     }
+    if (numRuns < 1 || numRuns > (uint32_t)kMaxRuns ||
+        (numRuns > 1 && (!W::kAppendRetired || !seeded || !retiredOut ||
+                         (unsigned long long)numRuns * runCap > retiredCap || numRuns * runCap >= (1ull << 31)))) {
+        set_error("persistent rounds: %u runs (at most %d, each with its own sink, seeded, steps on arrival)",
+                  numRuns, kMaxRuns);
+        return RF_ERR_ARG;
+    }
     const uint32_t itemBytes = 16u * W::V;
     if (ctx->itemBytes != itemBytes) {
         set_error("persistent rounds: the workload moves %u-byte items, the context %u", itemBytes,
@@ -1192,7 +1251,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
         return RF_ERR_ARG;
     }
     const int R = ctx->numRanks;
-    const int D = R + (W::kAppendRetired ? 1 : 0);
+    const int D = R + (W::kAppendRetired ? (int)numRuns : 0);
     if (D > 8 * W::kBlock) {
         set_error("persistent rounds: %d destinations exceed %d", D, 8 * W::kBlock);
         return RF_ERR_ARG;
@@ -1231,7 +1290,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     const size_t totBytes = (size_t)3 * G * rounds_row_stride(D) * sizeof(uint32_t);
     const size_t grpBytes = (size_t)3 * kSyncGroups * rounds_row_stride(D) * sizeof(uint32_t);
     const size_t smBytes = rounds_align_sz((size_t)G * sizeof(uint32_t), 16);
-    const size_t tailBytes = grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long) + smBytes;
+    const size_t tailBytes = grpBytes + sizeof(GridSync) + kResultWords * sizeof(unsigned long long) + smBytes;
     // second destination array (step on arrival), padded like ctx->dest
     const size_t dest2Bytes = W::kFuseStep ? rounds_align_sz((size_t)(ctx->capacity + 3) / 4 * 16 + 16, 256) : 0;
     if (rf_status st = ensure_rounds_scratch(ctx, rounds_align_sz(totBytes + tailBytes, 256) + dest2Bytes)) return st;
@@ -1245,7 +1304,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.grpTot = reinterpret_cast<uint32_t *>(base + totBytes);
     a.sync = reinterpret_cast<GridSync *>(base + totBytes + grpBytes);
     a.result = reinterpret_cast<unsigned long long *>(base + totBytes + grpBytes + sizeof(GridSync));
-    a.smOf = reinterpret_cast<uint32_t *>(base + totBytes + grpBytes + sizeof(GridSync) + 4 * sizeof(unsigned long long));
+    a.smOf = reinterpret_cast<uint32_t *>(base + totBytes + grpBytes + sizeof(GridSync) +
+                                          kResultWords * sizeof(unsigned long long));
     // the SM table is staged in the tile buffers: G + 3 words must fit
     a.skew = W::kFuseStep && ((size_t)G + 3) * 4 <= (size_t)2 * W::kBlock * W::kItemsPerThread * itemBytes
                  ? (ctx->rankSkew < 32u ? ctx->rankSkew : 32u)
@@ -1267,6 +1327,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.pushMax = W::kFuseStep && stepOnArrival ? (ctx->pushMax < pushCap ? ctx->pushMax : pushCap) : 0u;
     a.maxRounds = maxRounds;
     a.numRanks = R;
+    a.numRuns = numRuns;
+    a.runCap = numRuns > 1 ? (uint32_t)runCap : 0u;
     RF_CUDA(cudaMemsetAsync(base, 0, totBytes + tailBytes, s));
     W w = work;
     void *params[] = {&a, &w};
@@ -1276,12 +1338,14 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     count_launch();
     time_end(ctx, kTimeRounds, s);
     RF_CUDA(cudaMemcpyAsync(ctx->host, ctx->dev, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    unsigned long long r[4] = {0, 0, 0, 0};
+    unsigned long long r[kResultWords] = {};
     RF_CUDA(cudaMemcpyAsync(r, a.result, sizeof r, cudaMemcpyDeviceToHost, s));
     RF_CUDA(cudaStreamSynchronize(s));
     ctx->pending = false;
     time_collect(ctx);
     for (int i = 0; i < 4; ++i) res[i] = r[i];
+    if (runOut)
+        for (int i = 0; i < 2 * kMaxRuns; ++i) runOut[i] = r[4 + i];
     if (r[2] & RF_DEV_TIMEOUT) {
         set_error("persistent rounds: a bounded device-side wait gave up");
         return RF_ERR_TIMEOUT;

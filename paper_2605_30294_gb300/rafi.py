@@ -94,6 +94,8 @@ _SIGS = {
                   _PU64, _PU64],
     "rf_c1_run_batched": [_P, _P, _u64, _u32, _i32, _f64, _i32, _i32, _i32, _P, _PU64, _i32, _i32, _u32, _P,
                           _PU64, _PU64, _P, _u32],
+    "rf_c1_run_batched_runs": [_P, _P, _u64, _i32, _u32, _P, _f64, _i32, _i32, _i32, _P, _P, _i32, _u32, _P,
+                               _P, _PU64, _P, _u32],
     "rf_c0_make_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c2_make_bricks": [_P, _i32, _i32, _P, _P],
     "rf_c4_render": [_P, _P, _i32, _i32, ctypes.c_float, _i32, _P, _P, _i32, _u32, _P, _i32, _u32, _P, _PU64,
@@ -350,6 +352,29 @@ def rf_c1_run_batched(ctx: int, items, n: int, seed: int, mode: int, zipf_s: flo
                                  ctypes.byref(rounds), ctypes.byref(fwd), ptr(round_log), round_log_cap)
     _check("rf_c1_run_batched", st, allow)
     return st, cnt.value, rounds.value, fwd.value
+
+
+def rf_c1_run_batched_runs(ctx: int, items, n: int, seed: int, modes, zipf_s: float, grid, retired,
+                           host_memory: bool = False, max_rounds: int = 100000, stream=None, round_log=None,
+                           round_log_cap: int = 0, allow=()):
+    """Several independent microbenchmark runs (laws `modes`, n items each,
+    run k at items [k n, (k + 1) n)) in one persistent launch; returns
+    (status, retired counts per run, rounds per run, forwarded over all runs)."""
+    fn = "rf_c1_run_batched_runs"
+    k = len(modes)
+    _need(items, k * n * 64, fn, "items")
+    _need(retired, k * n * 64, fn, "retired")
+    gx, gy, gz = grid
+    m = (ctypes.c_int32 * max(k, 1))(*modes)
+    cnt = (ctypes.c_uint64 * max(k, 1))()
+    rounds = (ctypes.c_uint64 * max(k, 1))()
+    fwd = ctypes.c_uint64()
+    st = lib().rf_c1_run_batched_runs(ctx, ptr(items), n, k, seed, ctypes.cast(m, ctypes.c_void_p), zipf_s, gx, gy,
+                                      gz, ptr(retired), ctypes.cast(cnt, ctypes.c_void_p), int(host_memory),
+                                      max_rounds, stream_handle(stream), ctypes.cast(rounds, ctypes.c_void_p),
+                                      ctypes.byref(fwd), ptr(round_log), round_log_cap)
+    _check(fn, st, allow)
+    return st, [int(cnt[i]) for i in range(k)], [int(rounds[i]) for i in range(k)], fwd.value
 
 
 def c0_bricks_floats(n: int, brick: int) -> int:

@@ -110,3 +110,14 @@ def test_rank_skew_refuses_a_null_context():
     assert e.value.status == rafi.RF_ERR_ARG
     with pytest.raises(rafi.RafiError):
         rafi.rf_get_rank_skew(0)
+
+
+@pytest.mark.parametrize("short", ["items", "retired"])
+def test_c1_joint_runs_refuse_short_buffers(short):
+    # three runs of n items read 3 n items and retire into 3 n slots
+    n = 100
+    items = np.zeros((3 * n - (1 if short == "items" else 0), 16), np.uint32)
+    retired = np.zeros((3 * n - (1 if short == "retired" else 0), 16), np.uint32)
+    with pytest.raises(rafi.RafiError) as e:
+        rafi.rf_c1_run_batched_runs(0, items, n, 1, [0, 1, 2], 1.1, (4, 4, 4), retired)
+    assert e.value.status == rafi.RF_ERR_ARG and short in str(e.value)
