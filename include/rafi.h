@@ -407,7 +407,13 @@ rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t
  * order are exactly those of rf_c1_run_batched on it alone.  Each run has a
  * retirement destination of its own: run k's retired items land, stably, in
  * retired slots [k n, (k + 1) n) (numRuns x n x 64 bytes; page-locked host
- * memory receives them during the run, other host memory after it).
+ * memory receives them during the run, other host memory after it).  With
+ * hostMemory != 0 and a page-locked retired buffer the runs are launched one
+ * after another instead (each as rf_c1_run_batched, reading its items in
+ * place from a queue slot beyond the first n), and each run's items are
+ * copied in on a stream of the context's own while the run before it
+ * executes, so the two directions of the host link work at once; the
+ * results are the same, roundLog is not written.
  * Results (host): retiredCountsOut[k] and roundsOut[k] (nullable) per run,
  * *forwarded (nullable) the deliveries of all runs' work rounds.  The
  * context's capacity must hold numRuns x n items (below 2^31).  A launch that

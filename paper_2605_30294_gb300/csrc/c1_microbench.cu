@@ -692,6 +692,70 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
     return RF_OK;
 }
 
+// Several runs from page-locked host memory: one persistent launch per run,
+// each run's items copied in on the context's copy stream while the run
+// before it executes (the copy engine reads the host link in one direction,
+// the kernel writes the retired items over it in the other).  The items of
+// run k are staged in the queue slots [n, 2n) of `in` (k even) or of `out`
+// (k odd), beyond the [0, n) a run's kernel uses, and read there in place.
+// Each launch is rf_c1_run_batched's, so each run's results are those of its
+// own launch.
+static rf_status c1_runs_pipelined(rf_ctx *ctx, const void *items, uint64_t n, int32_t numRuns, uint32_t seed,
+                                   const int32_t *modes, int32_t gx, int32_t gy, int32_t gz, uint4 *devRetired,
+                                   uint64_t *retiredCountsOut, uint32_t maxRounds, cudaStream_t s,
+                                   uint64_t *roundsOut, uint64_t *forwarded, const rf_device_queues &q)
+{
+    using namespace rfi;
+    if (rf_status st = ensure_copy_stream(ctx)) return st;
+    cudaStream_t cs = ctx->copyStream;
+    const size_t runBytes = (size_t)n * 64u;
+    void *slot[2] = {static_cast<unsigned char *>(q.in) + runBytes, static_cast<unsigned char *>(q.out) + runBytes};
+    // the first copy waits for whatever the caller's stream still has in flight
+    RF_CUDA(cudaEventRecord(ctx->copyDone[1], s));
+    RF_CUDA(cudaStreamWaitEvent(cs, ctx->copyDone[1], 0));
+    RF_CUDA(cudaMemcpyAsync(slot[0], items, runBytes, cudaMemcpyHostToDevice, cs));
+    RF_CUDA(cudaEventRecord(ctx->copyDone[0], cs));
+    unsigned long long fwd = 0;
+    rf_status st = RF_OK;
+    for (int32_t k = 0; k < numRuns && st == RF_OK; ++k) {
+        const int b = k & 1;
+        // slot b ^ 1 was last read by run k - 1, whose launch has completed
+        if (k + 1 < numRuns) {
+            RF_CUDA(cudaMemcpyAsync(slot[b ^ 1], static_cast<const unsigned char *>(items) + (size_t)(k + 1) * runBytes,
+                                    runBytes, cudaMemcpyHostToDevice, cs));
+            RF_CUDA(cudaEventRecord(ctx->copyDone[b ^ 1], cs));
+        }
+        RF_CUDA(cudaStreamWaitEvent(s, ctx->copyDone[b], 0));
+        seed_dest_kernel<<<grid_for(ctx, n, 8), kBlock, 0, s>>>((uint32_t)n, q);
+        RF_LAUNCHED("seed_dest_kernel");
+        C1Work w;
+        w.zipfThr = ctx->zipfThr;
+        w.seed = seed;
+        w.mode = modes[k];
+        w.gx = gx;
+        w.gy = gy;
+        w.gz = gz;
+        w.R = ctx->numRanks;
+        unsigned long long res[4];
+        st = C1Shapes::launch(ctx->batchedShape[RF_POLICY_MICROBENCH], ctx, w, maxRounds, s, nullptr, 0u,
+                              devRetired + (size_t)k * n * 4u, (unsigned long long)n, ctx->stagingCount, res, true,
+                              true, slot[b]);
+        if (st != RF_OK) break;
+        retiredCountsOut[k] = res[3];
+        if (roundsOut) roundsOut[k] = res[0];
+        fwd += res[1];
+        if (ctx->host->numActive) {
+            set_error("rf_c1_run_batched_runs: run %d: %llu items still active after %u rounds", k,
+                      (unsigned long long)ctx->host->numActive, maxRounds);
+            st = RF_ERR_MAX_ROUNDS;
+        }
+    }
+    // no copy may still be writing into the queues when the call returns
+    RF_CUDA(cudaStreamSynchronize(cs));
+    if (forwarded) *forwarded = fwd;
+    return st;
+}
+
 // Several independent runs of the microbenchmark in one persistent launch.
 // Run k holds items [k n, (k + 1) n) of `items`, all of them starting at rank
 // i mod R as in a run of its own, and moves under its own destination law
@@ -757,6 +821,9 @@ extern "C" rf_status rf_c1_run_batched_runs(rf_ctx *ctx, const void *items, uint
     RF_CUDA(cudaMemsetAsync(ctx->stagingCount, 0, sizeof(unsigned long long), s));
     rf_device_queues q;
     rf_get_device_queues(ctx, &q);
+    if (direct && numRuns > 1)
+        return c1_runs_pipelined(ctx, items, n, numRuns, seed, modes, gx, gy, gz, static_cast<uint4 *>(devRetired),
+                                 retiredCountsOut, maxRounds, s, roundsOut, forwarded, q);
     // the seeded items are read where the caller keeps them when they are
     // 16-byte aligned device memory, else copied into the out-queue first
     const bool inPlace = !hostMemory && ((uintptr_t)items & 15u) == 0;

@@ -182,6 +182,14 @@ rf_status ensure_staging(rf_ctx *ctx)
     return RF_OK;
 }
 
+rf_status ensure_copy_stream(rf_ctx *ctx)
+{
+    if (ctx->copyStream) return RF_OK;
+    RF_CUDA(cudaStreamCreateWithFlags(&ctx->copyStream, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : ctx->copyDone) RF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return RF_OK;
+}
+
 }  // namespace rfi
 
 using namespace rfi;
@@ -307,6 +315,9 @@ rf_status rf_destroy(rf_ctx *ctx)
     cudaFree(ctx->roundsScratch);
     cudaFree(ctx->loopState);
     if (ctx->host) cudaFreeHost(ctx->host);
+    for (cudaEvent_t e : ctx->copyDone)
+        if (e) cudaEventDestroy(e);
+    if (ctx->copyStream) cudaStreamDestroy(ctx->copyStream);
     for (int i = 0; i < 2 * kTimeSlots; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     delete ctx;

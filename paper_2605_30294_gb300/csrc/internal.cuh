@@ -71,6 +71,8 @@ struct rf_ctx {
     rfi::DevState *host = nullptr;  // pinned mirror of *dev
     void *staging = nullptr;        // lazily allocated: capacity items (host-memory runs)
     unsigned long long *stagingCount = nullptr;
+    cudaStream_t copyStream = nullptr;  // lazily created: copies that overlap a run's kernel
+    cudaEvent_t copyDone[2] = {};
 
     cudaStream_t lastStream = nullptr;
     bool pending = false;  // an exchange's read-back has not been waited for
@@ -173,6 +175,9 @@ int c4_shapes(int32_t *out, int32_t cap);
 
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);
+
+// Create ctx->copyStream and its two events once.
+rf_status ensure_copy_stream(rf_ctx *ctx);
 
 // Allocate (or grow) ctx->roundsScratch to at least `bytes` (zeroed).
 rf_status ensure_rounds_scratch(rf_ctx *ctx, size_t bytes);

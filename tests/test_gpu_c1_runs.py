@@ -32,13 +32,21 @@ def _items(n, seeds):
 
 
 def _runs(items, n, seed, modes, ctx=None, host=False, round_log=None):
-    """One joint launch; returns (per-run retired rows, counts, rounds, forwarded)."""
+    """One call; returns (per-run retired rows, counts, rounds, forwarded).  host:
+    False (device buffers), True (page-locked host buffers: runs launched one by
+    one, copies overlapped) or "pageable" (plain host memory: one joint launch)."""
     k = len(modes)
     s = stream()
     own = ctx is None
     ctx = ctx or rafi.Context(R, 64, max(k * n, 1))
     try:
-        if host:
+        if host == "pageable":
+            h_items = np.ascontiguousarray(items).reshape(-1, 16)
+            h_ret = np.zeros((max(k * n, 1), 16), np.uint32)
+            st, cnt, rounds, fwd = rafi.rf_c1_run_batched_runs(ctx.handle, h_items, n, seed, modes, 1.1, GRID,
+                                                               h_ret, host_memory=True, stream=s)
+            got = h_ret
+        elif host:
             h_items = torch.from_numpy(np.ascontiguousarray(items).view(np.int32).reshape(-1, 16)).pin_memory()
             h_ret = torch.zeros((max(k * n, 1), 16), dtype=torch.int32).pin_memory()
             st, cnt, rounds, fwd = rafi.rf_c1_run_batched_runs(ctx.handle, h_items.data_ptr(), n, seed, modes, 1.1,
@@ -108,10 +116,11 @@ def test_every_persistent_shape(shape):
     _check_against_oracle(items, n, seed, modes, got, cnt, rounds, fwd)
 
 
-def test_joint_launch_equals_separate_launches_and_pinned_host_buffers():
+def test_joint_launch_equals_separate_launches_and_host_buffers():
     # the same runs launched one by one (rf_c1_run_batched), jointly from
-    # device buffers, and jointly from page-locked host buffers: identical
-    # retirement buffers, rounds and forwards
+    # device buffers, from page-locked host buffers (one launch per run, copies
+    # overlapped) and from pageable host buffers (joint launch, staged sink):
+    # identical retirement buffers, rounds and forwards
     n, seed, modes = 300007, 59, [T, U, Z]
     items = _items(n, (31, 32, 33))
     s = stream()
@@ -125,7 +134,7 @@ def test_joint_launch_equals_separate_launches_and_pinned_host_buffers():
             sep.append(ret.cpu().numpy().view(np.uint32))
             sep_rounds.append(rounds)
             sep_fwd += fwd
-        for host in (False, True):
+        for host in (False, True, "pageable"):
             got, cnt, rounds, fwd = _runs(items, n, seed, modes, ctx=ctx, host=host)
             assert cnt == [n] * 3 and rounds == sep_rounds and fwd == sep_fwd
             for j in range(3):
