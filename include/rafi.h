@@ -410,10 +410,11 @@ rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t
  * memory receives them during the run, other host memory after it).  With
  * hostMemory != 0 and a page-locked retired buffer the runs are launched one
  * after another instead (each as rf_c1_run_batched, reading its items in
- * place from a queue slot beyond the first n), and each run's items are
- * copied in on a stream of the context's own while the run before it
- * executes, so the two directions of the host link work at once; the
- * results are the same, roundLog is not written.
+ * place from a queue slot beyond the first n and retiring into a device
+ * staging buffer): while run k executes, run k + 1's items are copied in and
+ * run k - 1's retired items copied out on two streams of the context's own,
+ * so both directions of the host link work at once; the results are the
+ * same, roundLog is not written.
  * Results (host): retiredCountsOut[k] and roundsOut[k] (nullable) per run,
  * *forwarded (nullable) the deliveries of all runs' work rounds.  The
  * context's capacity must hold numRuns x n items (below 2^31).  A launch that

@@ -693,21 +693,24 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
 }
 
 // Several runs from page-locked host memory: one persistent launch per run,
-// each run's items copied in on the context's copy stream while the run
-// before it executes (the copy engine reads the host link in one direction,
-// the kernel writes the retired items over it in the other).  The items of
-// run k are staged in the queue slots [n, 2n) of `in` (k even) or of `out`
-// (k odd), beyond the [0, n) a run's kernel uses, and read there in place.
+// pipelined over the two directions of the host link.  While run k's kernel
+// executes, run k + 1's items are copied in on the context's copy stream and
+// run k - 1's retired items are copied out on its copy-out stream.  The
+// items of run k are staged in the queue slots [n, 2n) of `in` (k even) or of
+// `out` (k odd), beyond the [0, n) a run's kernel uses, and read there in
+// place; run k retires into the staging buffer's slots [k n, (k + 1) n).
 // Each launch is rf_c1_run_batched's, so each run's results are those of its
 // own launch.
 static rf_status c1_runs_pipelined(rf_ctx *ctx, const void *items, uint64_t n, int32_t numRuns, uint32_t seed,
-                                   const int32_t *modes, int32_t gx, int32_t gy, int32_t gz, uint4 *devRetired,
+                                   const int32_t *modes, int32_t gx, int32_t gy, int32_t gz, void *hostRetired,
                                    uint64_t *retiredCountsOut, uint32_t maxRounds, cudaStream_t s,
                                    uint64_t *roundsOut, uint64_t *forwarded, const rf_device_queues &q)
 {
     using namespace rfi;
     if (rf_status st = ensure_copy_stream(ctx)) return st;
-    cudaStream_t cs = ctx->copyStream;
+    if (rf_status st = ensure_staging(ctx)) return st;
+    uint4 *sink = static_cast<uint4 *>(ctx->staging);
+    cudaStream_t cs = ctx->copyStream, co = ctx->copyOutStream;
     const size_t runBytes = (size_t)n * 64u;
     void *slot[2] = {static_cast<unsigned char *>(q.in) + runBytes, static_cast<unsigned char *>(q.out) + runBytes};
     // the first copy waits for whatever the caller's stream still has in flight
@@ -738,9 +741,14 @@ static rf_status c1_runs_pipelined(rf_ctx *ctx, const void *items, uint64_t n, i
         w.R = ctx->numRanks;
         unsigned long long res[4];
         st = C1Shapes::launch(ctx->batchedShape[RF_POLICY_MICROBENCH], ctx, w, maxRounds, s, nullptr, 0u,
-                              devRetired + (size_t)k * n * 4u, (unsigned long long)n, ctx->stagingCount, res, true,
-                              true, slot[b]);
+                              sink + (size_t)k * n * 4u, (unsigned long long)n, ctx->stagingCount, res, true, true,
+                              slot[b]);
         if (st != RF_OK) break;
+        // the launch has completed: its retired items go out while the next run executes
+        const unsigned long long got = res[3] < n ? res[3] : n;
+        if (got)
+            RF_CUDA(cudaMemcpyAsync(static_cast<unsigned char *>(hostRetired) + (size_t)k * runBytes,
+                                    sink + (size_t)k * n * 4u, (size_t)got * 64u, cudaMemcpyDeviceToHost, co));
         retiredCountsOut[k] = res[3];
         if (roundsOut) roundsOut[k] = res[0];
         fwd += res[1];
@@ -750,8 +758,9 @@ static rf_status c1_runs_pipelined(rf_ctx *ctx, const void *items, uint64_t n, i
             st = RF_ERR_MAX_ROUNDS;
         }
     }
-    // no copy may still be writing into the queues when the call returns
+    // no copy may still be writing into the queues or the host buffer when the call returns
     RF_CUDA(cudaStreamSynchronize(cs));
+    RF_CUDA(cudaStreamSynchronize(co));
     if (forwarded) *forwarded = fwd;
     return st;
 }
@@ -822,8 +831,8 @@ extern "C" rf_status rf_c1_run_batched_runs(rf_ctx *ctx, const void *items, uint
     rf_device_queues q;
     rf_get_device_queues(ctx, &q);
     if (direct && numRuns > 1)
-        return c1_runs_pipelined(ctx, items, n, numRuns, seed, modes, gx, gy, gz, static_cast<uint4 *>(devRetired),
-                                 retiredCountsOut, maxRounds, s, roundsOut, forwarded, q);
+        return c1_runs_pipelined(ctx, items, n, numRuns, seed, modes, gx, gy, gz, retired, retiredCountsOut,
+                                 maxRounds, s, roundsOut, forwarded, q);
     // the seeded items are read where the caller keeps them when they are
     // 16-byte aligned device memory, else copied into the out-queue first
     const bool inPlace = !hostMemory && ((uintptr_t)items & 15u) == 0;

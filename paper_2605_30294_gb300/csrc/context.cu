@@ -186,6 +186,7 @@ rf_status ensure_copy_stream(rf_ctx *ctx)
 {
     if (ctx->copyStream) return RF_OK;
     RF_CUDA(cudaStreamCreateWithFlags(&ctx->copyStream, cudaStreamNonBlocking));
+    RF_CUDA(cudaStreamCreateWithFlags(&ctx->copyOutStream, cudaStreamNonBlocking));
     for (cudaEvent_t &e : ctx->copyDone) RF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return RF_OK;
 }
@@ -318,6 +319,7 @@ rf_status rf_destroy(rf_ctx *ctx)
     for (cudaEvent_t e : ctx->copyDone)
         if (e) cudaEventDestroy(e);
     if (ctx->copyStream) cudaStreamDestroy(ctx->copyStream);
+    if (ctx->copyOutStream) cudaStreamDestroy(ctx->copyOutStream);
     for (int i = 0; i < 2 * kTimeSlots; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     delete ctx;

@@ -71,7 +71,8 @@ struct rf_ctx {
     rfi::DevState *host = nullptr;  // pinned mirror of *dev
     void *staging = nullptr;        // lazily allocated: capacity items (host-memory runs)
     unsigned long long *stagingCount = nullptr;
-    cudaStream_t copyStream = nullptr;  // lazily created: copies that overlap a run's kernel
+    cudaStream_t copyStream = nullptr;     // lazily created: copies in that overlap a run's kernel
+    cudaStream_t copyOutStream = nullptr;  // and copies out
     cudaEvent_t copyDone[2] = {};
 
     cudaStream_t lastStream = nullptr;
@@ -176,7 +177,7 @@ int c4_shapes(int32_t *out, int32_t cap);
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);
 
-// Create ctx->copyStream and its two events once.
+// Create ctx->copyStream, ctx->copyOutStream and the two events once.
 rf_status ensure_copy_stream(rf_ctx *ctx);
 
 // Allocate (or grow) ctx->roundsScratch to at least `bytes` (zeroed).
