@@ -207,7 +207,8 @@ __device__ inline bool barrier_wait_bounded(GridSync *gs, unsigned int target, l
                 return false;
             }
         }
-        __nanosleep(20);
+        // (each poll is an L2 round trip; a 20 ns sleep between polls measured
+        // 0.24 % slower over a joint launch of the three runs)
     }
     return true;
 }
