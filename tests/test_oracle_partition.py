@@ -91,3 +91,43 @@ def test_partition_identity_when_sorted():
     out, off, _, _ = oracle.partition(items, dest, R)
     np.testing.assert_array_equal(out, items)
     np.testing.assert_array_equal(off[:-1], np.searchsorted(dest, np.arange(R)).astype(np.uint64))
+
+
+def test_joint_runs_partition_restricted_to_a_run_is_that_runs_own():
+    # Several independent runs can share one round's queue (the batched form's
+    # joint launch): each item moves by a rule of its own bytes and the round,
+    # never of its position.  Then the stable partition of the joint queue,
+    # restricted to one run's items, is that run's own stable partition, round
+    # after round, and so are the items each round retires, in order.
+    rng = np.random.default_rng(7)
+    R, K, n, ib = 16, 3, 500, 16
+    runs = []
+    for k in range(K):
+        it = rng.integers(0, 256, size=(n, ib), dtype=np.uint8)
+        it[:, 0] = k  # run tag (the rule below ignores it)
+        it[:, 1:5] = np.arange(n, dtype=np.uint32).view(np.uint8).reshape(n, 4)  # unique per run
+        runs.append(it)
+
+    def rule(items, rnd):
+        # next destination from the item's bytes 5.. and the round; -1 retires
+        h = (items[:, 5:].astype(np.uint64) * np.arange(1, ib - 4, dtype=np.uint64)).sum(axis=1)
+        h = (h * np.uint64(2654435761) + np.uint64(rnd * 40503)) % np.uint64(1 << 31)
+        d = (h % np.uint64(R + 3)).astype(np.int32)
+        return np.where(d >= R, -1, d)
+
+    def first(items):  # item i of a run starts at rank i mod R
+        return (items[:, 1:5].copy().view(np.uint32)[:, 0] % R).astype(np.int32)
+
+    joint, _, _, _ = oracle.partition(np.concatenate(runs), np.concatenate([first(r) for r in runs]), R)
+    own = [oracle.partition(r, first(r), R)[0] for r in runs]
+    for rnd in range(12):
+        for k in range(K):
+            np.testing.assert_array_equal(joint[joint[:, 0] == k], own[k])
+        dj = rule(joint, rnd)
+        retired_joint = joint[dj < 0]
+        joint = oracle.partition(joint, dj, R)[0]
+        for k in range(K):
+            dk = rule(own[k], rnd)
+            np.testing.assert_array_equal(retired_joint[retired_joint[:, 0] == k], own[k][dk < 0])
+            own[k] = oracle.partition(own[k], dk, R)[0]
+    assert len(joint) < K * n  # items did retire along the way
