@@ -14,6 +14,10 @@
 #include <cmath>
 #include <vector>
 
+#include <chrono>
+#include <functional>
+#include <thread>
+
 #include "internal.cuh"
 #include "philox.cuh"
 #include "rafi_device.cuh"
@@ -304,6 +308,17 @@ struct C1Work {
 // stores), one shape per SM-occupancy that fits the tile's shared memory.
 using C1Shapes = ShapeList<C1Work, Shape<C1Work, 2, 3, 256>, Shape<C1Work, 3, 2, 256>, Shape<C1Work, 4, 1, 256>,
                            Shape<C1Work, 2, 1, 512>>;
+
+// The same policy publishing its retired count after every round, for the
+// runs whose retired items leave for the host while the launch still runs.
+struct C1WorkProgress : C1Work {
+    static constexpr bool kProgress = true;
+    C1WorkProgress() = default;
+    __host__ __device__ explicit C1WorkProgress(const C1Work &w) : C1Work(w) {}
+};
+using C1ProgressShapes =
+    ShapeList<C1WorkProgress, Shape<C1WorkProgress, 2, 3, 256>, Shape<C1WorkProgress, 3, 2, 256>,
+              Shape<C1WorkProgress, 4, 1, 256>, Shape<C1WorkProgress, 2, 1, 512>>;
 
 // Seed: emit item i to rank i mod R at out slot base + i, where base was
 // reserved on the append counter by reserve_kernel.
@@ -694,8 +709,11 @@ extern "C" rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t 
 
 // Several runs from page-locked host memory: one persistent launch per run,
 // pipelined over the two directions of the host link.  While run k's kernel
-// executes, run k + 1's items are copied in on the context's copy stream and
-// run k - 1's retired items are copied out on its copy-out stream.  The
+// executes, run k + 1's items are copied in on the context's copy stream,
+// and run k's retired items are copied out on its copy-out stream as soon
+// as their sink slots are final (the kernel publishes that count in mapped
+// host memory after every round; the host copies it out in chunks of at
+// least 2^20 items while it waits for the launch).  The
 // items of run k are staged in the queue slots [n, 2n) of `in` (k even) or of
 // `out` (k odd), beyond the [0, n) a run's kernel uses, and read there in
 // place; run k retires into the staging buffer's slots [k n, (k + 1) n).
@@ -740,15 +758,36 @@ static rf_status c1_runs_pipelined(rf_ctx *ctx, const void *items, uint64_t n, i
         w.gz = gz;
         w.R = ctx->numRanks;
         unsigned long long res[4];
-        st = C1Shapes::launch(ctx->batchedShape[RF_POLICY_MICROBENCH], ctx, w, maxRounds, s, nullptr, 0u,
-                              sink + (size_t)k * n * 4u, (unsigned long long)n, ctx->stagingCount, res, true, true,
-                              slot[b]);
+        volatile unsigned long long *prog = ctx->progressHost;
+        *prog = 0ull;
+        unsigned long long copied = 0;  // retired items of run k already on their way out
+        unsigned char *hostRun = static_cast<unsigned char *>(hostRetired) + (size_t)k * runBytes;
+        const uint4 *sinkRun = sink + (size_t)k * n * 4u;
+        cudaError_t copyErr = cudaSuccess;
+        const std::function<void()> poll = [&]() {
+            const unsigned long long p = *prog;  // final sink slots so far (never more than n)
+            if (p >= copied + (1ull << 20) && p <= n && copyErr == cudaSuccess) {
+                copyErr = cudaMemcpyAsync(hostRun + (size_t)copied * 64u, sinkRun + (size_t)copied * 4u,
+                                          (size_t)(p - copied) * 64u, cudaMemcpyDeviceToHost, co);
+                copied = p;
+            } else {
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+        };
+        st = C1ProgressShapes::launch(ctx->batchedShape[RF_POLICY_MICROBENCH], ctx, C1WorkProgress(w), maxRounds, s,
+                                      nullptr, 0u, sink + (size_t)k * n * 4u, (unsigned long long)n,
+                                      ctx->stagingCount, res, true, true, slot[b], 1u, 0ull, nullptr,
+                                      ctx->progressDev, &poll);
+        if (copyErr != cudaSuccess) {
+            cuda_fail(copyErr, "cudaMemcpyAsync of retired items");
+            st = RF_ERR_CUDA;
+        }
         if (st != RF_OK) break;
-        // the launch has completed: its retired items go out while the next run executes
+        // the launch has completed: the rest of its retired items go out while the next run executes
         const unsigned long long got = res[3] < n ? res[3] : n;
-        if (got)
-            RF_CUDA(cudaMemcpyAsync(static_cast<unsigned char *>(hostRetired) + (size_t)k * runBytes,
-                                    sink + (size_t)k * n * 4u, (size_t)got * 64u, cudaMemcpyDeviceToHost, co));
+        if (got > copied)
+            RF_CUDA(cudaMemcpyAsync(hostRun + (size_t)copied * 64u, sinkRun + (size_t)copied * 4u,
+                                    (size_t)(got - copied) * 64u, cudaMemcpyDeviceToHost, co));
         retiredCountsOut[k] = res[3];
         if (roundsOut) roundsOut[k] = res[0];
         fwd += res[1];

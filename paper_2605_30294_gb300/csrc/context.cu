@@ -184,10 +184,14 @@ rf_status ensure_staging(rf_ctx *ctx)
 
 rf_status ensure_copy_stream(rf_ctx *ctx)
 {
-    if (ctx->copyStream) return RF_OK;
-    RF_CUDA(cudaStreamCreateWithFlags(&ctx->copyStream, cudaStreamNonBlocking));
-    RF_CUDA(cudaStreamCreateWithFlags(&ctx->copyOutStream, cudaStreamNonBlocking));
-    for (cudaEvent_t &e : ctx->copyDone) RF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!ctx->copyStream) RF_CUDA(cudaStreamCreateWithFlags(&ctx->copyStream, cudaStreamNonBlocking));
+    if (!ctx->copyOutStream) RF_CUDA(cudaStreamCreateWithFlags(&ctx->copyOutStream, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : ctx->copyDone)
+        if (!e) RF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (!ctx->progressHost) {
+        RF_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&ctx->progressHost), 64, cudaHostAllocMapped));
+        RF_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void **>(&ctx->progressDev), ctx->progressHost, 0));
+    }
     return RF_OK;
 }
 
@@ -320,6 +324,7 @@ rf_status rf_destroy(rf_ctx *ctx)
         if (e) cudaEventDestroy(e);
     if (ctx->copyStream) cudaStreamDestroy(ctx->copyStream);
     if (ctx->copyOutStream) cudaStreamDestroy(ctx->copyOutStream);
+    if (ctx->progressHost) cudaFreeHost(ctx->progressHost);
     for (int i = 0; i < 2 * kTimeSlots; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     delete ctx;

@@ -74,6 +74,8 @@ struct rf_ctx {
     cudaStream_t copyStream = nullptr;     // lazily created: copies in that overlap a run's kernel
     cudaStream_t copyOutStream = nullptr;  // and copies out
     cudaEvent_t copyDone[2] = {};
+    unsigned long long *progressHost = nullptr;  // page-locked, mapped: a running launch's retired count
+    unsigned long long *progressDev = nullptr;   // its device address
 
     cudaStream_t lastStream = nullptr;
     bool pending = false;  // an exchange's read-back has not been waited for
@@ -177,7 +179,8 @@ int c4_shapes(int32_t *out, int32_t cap);
 // Allocate ctx->staging (capacity items) on first use.
 rf_status ensure_staging(rf_ctx *ctx);
 
-// Create ctx->copyStream, ctx->copyOutStream and the two events once.
+// Create ctx->copyStream, ctx->copyOutStream, the two events and the mapped
+// progress word once.
 rf_status ensure_copy_stream(rf_ctx *ctx);
 
 // Allocate (or grow) ctx->roundsScratch to at least `bytes` (zeroed).

@@ -37,6 +37,8 @@
 // CTAs check at the next barrier, and the kernel returns with a timeout status.
 #pragma once
 
+#include <functional>
+#include <type_traits>
 #include <utility>
 
 #include "internal.cuh"
@@ -95,9 +97,18 @@ struct RoundsArgs {
     int32_t numRanks;
     uint32_t numRuns;   // independent runs (1..kMaxRuns); retirement digit R + k is run k's
     uint32_t runCap;    // sink slots per run: run k retires into [k runCap, (k + 1) runCap)
+    volatile unsigned long long *progress;  // nullable, host-mapped (policies with kProgress): the
+                                            // retired items whose sink slots are final, after every round
 };
 
 constexpr int kRoundsBlock = 256;  // threads per CTA of a policy's default shape
+
+// Policies that publish their retired count after every round (W::kProgress
+// true) compile the store; the others carry no trace of it.
+template <class W, class = void>
+struct HasProgress : std::false_type {};
+template <class W>
+struct HasProgress<W, std::void_t<decltype(W::kProgress)>> : std::bool_constant<W::kProgress> {};
 
 // A workload policy W (described at rounds_kernel) launched in another shape:
 // K items per thread per tile, CTAS resident CTAs per SM to compile for,
@@ -805,6 +816,12 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
                     a.roundLog[7 * round + 6] = nNext;
                 }
                 retiredSoFar += retiredNow;
+                if constexpr (HasProgress<W>::value) {
+                    if (a.progress && tid == 0) {
+                        __threadfence_system();
+                        *a.progress = retiredSoFar;
+                    }
+                }
                 forwarded += nNext;
                 n = nNext;
                 A ^= 1u;
@@ -1184,6 +1201,13 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
             break;
         }
         if (logRound) a.roundLog[7 * round + 4] = globaltimer();
+        if constexpr (HasProgress<W>::value) {
+            if (a.progress && c == 0 && tid == 0) {
+                // every CTA's sink writes of this round precede the barrier just passed
+                __threadfence_system();
+                *a.progress = retiredSoFar;
+            }
+        }
         n = nNext;
         pushed = push;
         fresh = !fuse;
@@ -1222,13 +1246,17 @@ __global__ void __launch_bounds__(W::kBlock, W::kMinBlocksPerSM) rounds_kernel(R
 // seeded items belong to that many independent runs, named by the high bits
 // of their destination words; run k retires into sink slots
 // [k runCap, (k + 1) runCap).  runOut (host, nullable, 2 kMaxRuns words)
-// receives each run's rounds, then each run's retired count.
+// receives each run's rounds, then each run's retired count.  progress
+// (nullable, device address of host-mapped memory) receives, after every
+// round, how many retired items' sink slots are final; poll (nullable) is
+// called over and over while the launch runs.
 template <class W>
 rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStream_t s,
                         unsigned long long *roundLog, uint32_t roundLogCap, uint4 *retiredOut,
                         unsigned long long retiredCap, unsigned long long *retiredCountOut, unsigned long long res[4],
                         bool stepOnArrival = false, bool seeded = false, const void *seedItems = nullptr,
-                        uint32_t numRuns = 1, unsigned long long runCap = 0, unsigned long long *runOut = nullptr)
+                        uint32_t numRuns = 1, unsigned long long runCap = 0, unsigned long long *runOut = nullptr,
+                        unsigned long long *progress = nullptr, const std::function<void()> *poll = nullptr)
 {
     if ((seeded || stepOnArrival) && !W::kFuseStep) {
         set_error("persistent rounds: the policy does not step on arrival");
@@ -1330,6 +1358,7 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
     a.numRanks = R;
     a.numRuns = numRuns;
     a.runCap = numRuns > 1 ? (uint32_t)runCap : 0u;
+    a.progress = progress;
     RF_CUDA(cudaMemsetAsync(base, 0, totBytes + tailBytes, s));
     W w = work;
     void *params[] = {&a, &w};
@@ -1338,6 +1367,8 @@ rf_status launch_rounds(rf_ctx *ctx, const W &work, uint32_t maxRounds, cudaStre
                                         L.total, s));
     count_launch();
     time_end(ctx, kTimeRounds, s);
+    if (poll)  // the caller's work while the launch runs (stream order stays as it is)
+        while (cudaStreamQuery(s) == cudaErrorNotReady) (*poll)();
     RF_CUDA(cudaMemcpyAsync(ctx->host, ctx->dev, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     unsigned long long r[kResultWords] = {};
     RF_CUDA(cudaMemcpyAsync(r, a.result, sizeof r, cudaMemcpyDeviceToHost, s));
