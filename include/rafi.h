@@ -412,9 +412,9 @@ rf_status rf_c1_run_batched(rf_ctx *ctx, const void *items, uint64_t n, uint32_t
  * after another instead (each as rf_c1_run_batched, reading its items in
  * place from a queue slot beyond the first n and retiring into a device
  * staging buffer): while run k executes, run k + 1's items are copied in and
- * run k - 1's retired items copied out on two streams of the context's own,
- * so both directions of the host link work at once; the results are the
- * same, roundLog is not written.
+ * run k's retired items copied out, as their slots become final, on two
+ * streams of the context's own, so both directions of the host link work at
+ * once; the results are the same, roundLog is not written.
  * Results (host): retiredCountsOut[k] and roundsOut[k] (nullable) per run,
  * *forwarded (nullable) the deliveries of all runs' work rounds.  The
  * context's capacity must hold numRuns x n items (below 2^31).  A launch that
