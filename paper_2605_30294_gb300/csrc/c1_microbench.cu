@@ -11,6 +11,12 @@
 // picks the destination d (uniform, Zipf table, or one of the 6 torus
 // neighbours of the item's rank) and the item becomes w14 = d, w13 ^= r2,
 // w15 += 1.  Philox4x32-10 follows Salmon et al., SC'11.
+//
+// Forms: the host loop (rf_c1_run), its kernels in a CUDA graph
+// (rf_c1_run_graph), one persistent launch per run (rf_c1_run_batched) and
+// several independent runs, each with its own law, in one persistent launch
+// (rf_c1_run_batched_runs; from page-locked host buffers, one launch per run
+// with the host link's two directions pipelined).
 #include <cmath>
 #include <vector>
 
